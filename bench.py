@@ -1,0 +1,363 @@
+"""Benchmark: events/s of VELO-like pixel tracking on B300.
+
+Workload: 10,000 synthetic pile-up-5.5 events (n_PV ~ Poisson(5.5), tracks
+per PV ~ Poisson(40), 0.5 mrad scattering per module, 99 % hit efficiency,
+1e-4 noise per cell per module) -- the stand-in for the paper's pp
+collisions at mu ~ 5 (Sec. "Introduction").  One step reconstructs the whole
+batch (clustering, seeding + extension, fit + cut, output compaction) with
+the inputs resident in HBM; the 0.5 GB of pixel words per step exceed the
+126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank with its own 10k
+events (weak scaling, no collective on the data path: the events are
+independent; the barrier and the max over ranks are timing only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s (1 B300) for VELO-like tracking at pileup 5.5; p99 batch latency"
+UNIT = "events/s"
+WORKLOAD = "C2: 10k events, pileup 5.5 (n_PV~Poisson(5.5), 40 tracks/PV), 26 modules, MS 0.5 mrad, eff 0.99, noise 1e-4"
+STAGES = ("k_cluster", "k_track", "k_scan", "k_output")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--events", type=int, default=10_000, help="events per GPU per step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def params_values(ms_theta):
+    return dict(win_seed=0.04, win_fwd=0.04, max_slope=0.3, max_scatter_seed=0.01, max_scatter_fwd=0.02,
+                max_skipped=1, sigma_meas=0.0159, ms_theta=ms_theta, chi2ndf_max=10.0, chi2ndf_max_3hit=2.0)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the GPU this process runs on, while running."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str):
+        self.bus = bus_id.lower()
+        self.p = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        rows = []
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 10:
+                continue
+            bus = f[1].lower()
+            if self.bus and not (bus.endswith(self.bus[-12:]) or self.bus.endswith(bus[-12:])):
+                continue
+            try:
+                rows.append((float(f[2]), float(f[3]), float(f[4]) if f[4] not in ("[N/A]", "N/A") else 0.0, f[5:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        maxsm = max(r[1] for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[3][1:]) if v.strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": maxsm, "samples": len(rows),
+                "power_w_max": max(r[2] for r in rows), "reasons": reasons}
+
+
+def bus_id_of(dev):
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+    except AttributeError:
+        return ""
+
+
+# ------------------------------------------------------------------ roofline inputs
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2412_05041_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per event of `kernel` from the committed ncu summary, if it was
+    taken from the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_c2.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_event:\s*([0-9.eE+]+)", txt)
+    if not m_src or not m_b or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    """The CPU oracle as the reference arm: every step is a bounded sample of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import velogen
+    cfg = velogen.C2
+    cores = os.cpu_count() or 1
+    n = max(32, min(2000, 24 * cores))
+    batches = [velogen.generate(cfg, n_events=n, first_event=(i * n) % cfg.n_events)
+               for i in range(max(args.steps, 1) + args.warmup)]
+    op = oracle.Params(**params_values(cfg.ms_theta))
+    for i in range(args.warmup):
+        b = batches[i]
+        oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    t = []
+    for i in range(args.steps):
+        b = batches[args.warmup + i]
+        t0 = time.perf_counter()
+        oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+        t.append(time.perf_counter() - t0)
+    sec = float(np.sum(t))
+    value = args.steps * n / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_events_per_step": n, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} events of the C2 workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(cfg):
+    import oracle
+    import velogen
+    cores = os.cpu_count() or 1
+    op = oracle.Params(**params_values(cfg.ms_theta))
+    n_done, t_total, first = 0, 0.0, 0
+    per = max(32, 8 * cores)
+    while t_total < 4.0 and n_done < cfg.n_events:
+        b = velogen.generate(cfg, n_events=per, first_event=first)
+        t0 = time.perf_counter()
+        oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+        t_total += time.perf_counter() - t0
+        n_done += per
+        first += per
+    return {"value": n_done / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_done} of the 10k C2 events, all {cores} host threads, {t_total:.1f} s wall"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2412_05041_b300 as velo
+    import velogen
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    velo.build()
+    cfg = velogen.C2
+    n_ev = args.events
+    b = velogen.generate(cfg, n_events=n_ev, first_event=rank * n_ev)
+    vp = velo.default_params(**params_values(cfg.ms_theta))
+    off_h = torch.from_numpy(b.offsets.view(np.int64)).pin_memory()
+    pix_h = torch.from_numpy(b.pixels.view(np.int32)).pin_memory()
+    off = off_h.to(dev)
+    pix = pix_h.to(dev)
+    P = pix.numel()
+    R = velo.Reconstructor(b.geometry, vp, max_events=n_ev, max_pixels=P, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        R.run(off, pix, stream)
+    torch.cuda.synchronize(dev)
+    res = R.result()
+    tot = [int(res["cluster_offsets"][-1]), int(res["track_offsets"][-1]), len(res["track_hits"]), int(res["n_failed"])]
+
+    K = args.steps
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    for mk in marks:  # create the handles before the timed region
+        for m in mk:
+            m.record(stream)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(bus_id_of(dev)) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0.record(stream)
+        for k in range(K):
+            R.run(off, pix, stream, marks=marks[k])
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = t0.elapsed_time(t1) / K
+    stage_ms = {s: float(np.mean([marks[k][i].elapsed_time(marks[k][i + 1]) for k in range(K)]))
+                for i, s in enumerate(STAGES)}
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_ev / (ms / 1000.0)
+
+    # batch latency percentiles: 1k-event batches, one at a time
+    lat = []
+    nb = min(1000, n_ev)
+    off_b = torch.from_numpy(b.offsets[: nb + 1].view(np.int64)).to(dev)
+    Rb = velo.Reconstructor(b.geometry, vp, max_events=nb, max_pixels=int(b.offsets[nb]), device=dev)
+    for _ in range(3):
+        Rb.run(off_b, pix[: int(b.offsets[nb])], stream)
+    for _ in range(30):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Rb.run(off_b, pix[: int(b.offsets[nb])], stream)
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+
+    # end to end through the host-buffer entry point (H2D + kernels + D2H inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        H = velo.HostReconstructor(b.geometry, vp, max_events=n_ev, max_pixels=P)
+        for _ in range(2):
+            H.run(off_h, pix_h, stream)
+        barrier()
+        tt = time.perf_counter()
+        ke = max(3, min(K, 10))
+        for _ in range(ke):
+            H.run(off_h, pix_h, stream)
+        el = (time.perf_counter() - tt) / ke
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * n_ev / el, "unit": UNIT, "h2d_bytes_per_step": int(8 * (n_ev + 1) + 4 * P),
+               "d2h_bytes_per_step": int(H.bytes_out()), "ms_per_step": 1000 * el}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = measured_peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    n_cl, n_tr, n_hits = tot[0], tot[1], tot[2]
+    # algorithmic bytes of the whole path per step: read the words, write clusters
+    # (x, y, z) and tracks (hit ids, 20-float state, offsets); per-kernel in DESIGN
+    alg = {
+        "k_cluster": 4 * P + 8 * (n_ev + 1) + 12 * n_cl + 4 * n_cl,
+        "k_track": 16 * n_cl,
+        "k_scan": 24 * n_ev,
+        "k_output": 8 * n_cl + 12 * n_cl + n_tr * (4 * 20 + 8) + 4 * n_hits,
+    }
+    achieved = alg[dom] / (stage_ms[dom] / 1000.0) / 1e9
+    traffic = profiled_traffic(dom)
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None if traffic is None else traffic * n_ev,
+            "peak_source": f"{peak_kind} hbm_gbs (copy)", "stage_ms": stage_ms}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_gpu": n_ev, "pixels_per_gpu": P, "clusters": n_cl,
+                   "tracks": n_tr, "failed_events": tot[3], "l2": "inputs larger than L2 (0.5 GB words)",
+                   "parallelism": f"replicas x{world} (event sharding)"},
+        "p50_batch_latency_ms": float(np.percentile(lat, 50)), "p99_batch_latency_ms": float(np.percentile(lat, 99)),
+        "latency_batch_events": nb,
+        "gpu_launches": 5 * K,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: --warmup raised to 3", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/* velo.h -- C ABI of the B300 (sm_103a) event-batched VELO-like pixel tracking library.
+ *
+ * What it computes.  The paper's first trigger stage reconstructs every
+ * collision event on GPUs at the full input rate (Sec. "Introduction",
+ * Sec. "Data flow overview"), with a simplified pattern recognition and a
+ * parameterised Kalman filter applied only to the pixel-tracker (VELO)
+ * segment of each track (Sec. "HLT1 details and results").  The paper gives
+ * no algorithm; this library implements one concrete definition of it:
+ *   pixel words -> 8-connected clusters per module (hits)
+ *   -> search by triplet seeding + forward extension across modules
+ *   -> straight-line least-squares fit + simplified Kalman filter
+ *   -> chi2/ndf cut -> tracks in canonical order.
+ * Every floating-point decision is binary32 with one rounding per operation
+ * in a fixed order and no fused multiply-add, so results are reproducible
+ * bit for bit on any IEEE-754 machine that runs the same steps.
+ *
+ * Conventions.
+ *   - All functions return VELO_OK (0) or a positive VELO_E* code; no function
+ *     aborts, traps or prints.  velo_strerror() names a code.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary (preferably pinned) host memory.
+ *   - Every buffer is caller-owned unless a function says it allocates.
+ *   - Asynchronous functions enqueue work on the given cudaStream_t (passed
+ *     as void*; NULL = the legacy default stream) and return without waiting;
+ *     results are valid once the stream has reached that point.
+ *   - The library keeps no global state and never synchronises a stream it
+ *     was not asked to (the *_host entry points synchronise their own
+ *     stream before returning).
+ */
+#ifndef VELO_H
+#define VELO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VELO_STATE_STRIDE 20          /* floats per track state, layout below */
+#define VELO_MAX_MODULES 32u          /* geometry limit (5-bit module field) */
+#define VELO_MAX_MODULE_CLUSTERS 65535u /* per module per event; beyond it the event fails */
+
+/* Return codes. */
+enum {
+  VELO_OK = 0,
+  VELO_EINVAL = 1,     /* bad argument: NULL where a pointer is required, bad geometry or params */
+  VELO_ECAPACITY = 2,  /* a caller buffer or workspace is smaller than velo_query_sizes asked for */
+  VELO_ECUDA = 3,      /* a CUDA runtime call failed (the CUDA error is not cleared) */
+  VELO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+  VELO_ENOMEM = 5      /* a library allocation failed (only the allocating entry points) */
+};
+
+/* Per-event status codes written to velo_output_t.status. */
+enum {
+  VELO_EVT_OK = 0,
+  VELO_EVT_BADWORD = 1,  /* a pixel word has bit 31 set, q = 0, or module/row/col outside the geometry */
+  VELO_EVT_OVERFLOW = 2  /* a module has more than VELO_MAX_MODULE_CLUSTERS clusters */
+};
+/* A failed event contributes no cluster and no track; the other events are unaffected. */
+
+/* Detector geometry: planar pixel modules perpendicular to the beam (z). */
+typedef struct velo_geometry {
+  uint32_t n_modules;     /* 3 .. VELO_MAX_MODULES */
+  const float* module_z;  /* host [n_modules], strictly ascending, mm */
+  float pitch_mm;         /* square pixel pitch */
+  uint32_t n_rows, n_cols;/* pixel grid per module, each <= 2048 */
+  float x0_mm, y0_mm;     /* lower edge of the grid: pixel (row, col) spans
+                             x in [x0 + pitch*col, x0 + pitch*(col+1)) */
+} velo_geometry_t;
+
+/* Reconstruction parameters (velo_params_default fills the standard values). */
+typedef struct velo_params {
+  float win_seed;          /* pseudo-angle half window for seeding, in [0, 1] (full turn = 4) */
+  float win_fwd;           /* pseudo-angle half window for extension, in [0, 1] */
+  float max_slope;         /* seeds need |tx|, |ty| <= max_slope */
+  float max_scatter_seed;  /* mm^2: squared 2D distance of the middle hit to the outer-hit line */
+  float max_scatter_fwd;   /* mm^2: squared 2D distance of a hit to the extrapolated track */
+  uint32_t max_skipped;    /* modules a track may miss in a row before it terminates */
+  float sigma_meas;        /* mm, hit resolution used by both fits */
+  float ms_theta;          /* rad per module; 0 -> the cut uses the straight-line chi2,
+                              > 0 -> the Kalman chi2 with slope noise ms_theta^2 per module */
+  float chi2ndf_max;       /* keep a track if chi2/ndf <= chi2ndf_max */
+  float chi2ndf_max_3hit;  /* ... and a 3-hit track only if also <= chi2ndf_max_3hit */
+} velo_params_t;
+
+/* A batch of events in CSR form.  Pixel word layout (any order inside an event):
+ *   bit 31 = 0 | q (4 bits, 1..15) << 27 | module (5) << 22 | row (11) << 11 | col (11) */
+typedef struct velo_events {
+  uint64_t n_events;
+  uint64_t n_pixels;              /* == event_offsets[n_events] */
+  const uint64_t* event_offsets;  /* [n_events + 1], event_offsets[0] == 0, non-decreasing */
+  const uint32_t* pixels;         /* [n_pixels] */
+} velo_events_t;
+
+/* Output buffers (all caller-owned; capacities from velo_query_sizes).
+ * Cluster ids are event-local: the rank of a cluster in the event when the
+ * clusters are ordered by (module, smallest row*2048+col of their pixels).
+ * Tracks of an event are ordered by their smallest cluster id; a track's hit
+ * list holds its cluster ids ascending (= upstream to downstream).
+ * Track state layout (VELO_STATE_STRIDE floats per track):
+ *   0 x, 1 y, 2 tx, 3 ty   straight-line least squares, at the first hit's z
+ *   4 z_first              z of the first (most upstream) hit
+ *   5 z_beam               z of the fitted line's closest approach to the z axis
+ *   6 chi2_lsq, 7 chi2_kf  straight-line chi2 and Kalman chi2 (sum of r^2/S)
+ *   8 kf_x, 9 kf_y, 10 kf_tx, 11 kf_ty   Kalman state at the first hit
+ *  12 C_xx, 13 C_xtx, 14 C_txtx          Kalman covariance, x projection
+ *  15 C_yy, 16 C_yty, 17 C_tyty          Kalman covariance, y projection
+ *  18 ndf = 2 n_hits - 4, 19 reserved (0) */
+typedef struct velo_output {
+  int32_t* status;              /* [n_events] VELO_EVT_* */
+  uint64_t* cluster_offsets;    /* [n_events + 1] into cluster_x/y/z */
+  float* cluster_x;             /* [cap_clusters] mm */
+  float* cluster_y;             /* [cap_clusters] mm */
+  float* cluster_z;             /* [cap_clusters] mm */
+  uint32_t* pixel_cluster;      /* optional (NULL = not written) [n_pixels]: event-local cluster id
+                                   of every input word, 0xFFFFFFFF in failed events */
+  uint64_t* track_offsets;      /* [n_events + 1] into the track arrays */
+  uint64_t* track_hit_offsets;  /* [cap_tracks + 1] into track_hits (global positions) */
+  uint32_t* track_hits;         /* [cap_track_hits] event-local cluster ids */
+  float* track_states;          /* [cap_tracks * VELO_STATE_STRIDE] */
+  uint64_t* totals;             /* [4]: n_clusters, n_tracks, n_track_hits, n_failed_events */
+} velo_output_t;
+
+/* Capacities that always suffice for a batch of n_events events holding
+ * n_pixels pixel words, and the device workspace velo_reconstruct_into needs. */
+typedef struct velo_sizes {
+  uint64_t cap_clusters;     /* = n_pixels (a cluster has >= 1 pixel) */
+  uint64_t cap_tracks;       /* = n_pixels / 3 (disjoint tracks of >= 3 hits) */
+  uint64_t cap_track_hits;   /* = n_pixels */
+  uint64_t workspace_bytes;  /* device scratch, 256-byte aligned start required */
+} velo_sizes_t;
+
+/* Fill *p with the standard parameters (win 0.04, slope 0.3, scatter 0.01 /
+ * 0.02 mm^2, 1 skipped module, sigma 0.0159 mm, 0.5 mrad, cuts 10 and 2). */
+int velo_params_default(velo_params_t* p);
+
+/* Sizes for a batch (host arithmetic only; no device call). */
+int velo_query_sizes(uint64_t n_events, uint64_t n_pixels, velo_sizes_t* out);
+
+/* Reconstruct a device-resident batch into caller-owned device buffers.
+ * events->event_offsets/pixels and every output pointer are device pointers;
+ * geometry->module_z is a host pointer (copied into the launch arguments).
+ * workspace: device, >= sizes.workspace_bytes, 256-byte aligned, contents
+ * ignored on entry and undefined on exit.  Allocates nothing and never
+ * synchronises: everything runs on `stream` (a cudaStream_t).  Offsets that
+ * are not monotone or do not end at n_pixels are detected on the device and
+ * make every event fail with VELO_EVT_BADWORD. */
+int velo_reconstruct_into(const velo_events_t* events, const velo_geometry_t* geometry,
+                          const velo_params_t* params, const velo_output_t* out, void* workspace,
+                          uint64_t workspace_bytes, void* stream);
+
+/* velo_reconstruct_into plus timing marks: stage_events holds 5 cudaEvent_t
+ * handles created by the caller (cast to void*), recorded on `stream` before
+ * the clustering kernel, after it, after the tracking kernel, after the
+ * offsets scan and after the output kernel.  NULL records nothing.  The
+ * marks add no work and no synchronisation. */
+int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometry_t* geometry,
+                                 const velo_params_t* params, const velo_output_t* out, void* workspace,
+                                 uint64_t workspace_bytes, void* stream, void* const* stage_events);
+
+/* The same with library-owned results (the form of the call that returns
+ * "tracks"): allocates the output buffers and the workspace on `stream`
+ * with cudaMallocAsync and returns an opaque handle in *result.  The handle
+ * is valid immediately; its contents once `stream` reaches this point. */
+typedef struct velo_result velo_result_t;
+typedef struct velo_result_view {
+  uint64_t n_events, n_pixels;
+  uint64_t cap_clusters, cap_tracks, cap_track_hits;
+  velo_output_t out;  /* device pointers owned by the result */
+} velo_result_view_t;
+int velo_reconstruct(const velo_events_t* events, const velo_geometry_t* geometry,
+                     const velo_params_t* params, velo_result_t** result, void* stream);
+int velo_result_view(const velo_result_t* result, velo_result_view_t* view);
+/* Frees the result's buffers on its stream (stream-ordered; no host wait). */
+void velo_result_free(velo_result_t* result);
+
+/* Host-buffer form, for callers whose events sit in host memory: a context
+ * owns device buffers for up to max_events / max_pixels (allocated once, by
+ * velo_context_create).  velo_reconstruct_host copies the batch in, runs
+ * velo_reconstruct_into, copies the results out into caller-owned HOST
+ * buffers of capacities from velo_query_sizes, and synchronises `stream`
+ * before it returns.  Only the used part of each output is copied back. */
+typedef struct velo_context velo_context_t;
+int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t** ctx);
+void velo_context_destroy(velo_context_t* ctx);
+int velo_reconstruct_host(velo_context_t* ctx, const velo_events_t* host_events,
+                          const velo_geometry_t* geometry, const velo_params_t* params,
+                          const velo_output_t* host_out, void* stream);
+
+/* Name of a VELO_* return code. */
+const char* velo_strerror(int code);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int velo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VELO_H */

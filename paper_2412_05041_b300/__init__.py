@@ -1,0 +1,138 @@
+"""B300-native event-batched VELO-like pixel tracking (sm_103a CUDA kernels behind a C ABI).
+
+The paper's first trigger stage reconstructs every collision event on GPUs at
+the full input rate, with a simplified pattern recognition and a
+parameterised Kalman filter on the pixel-tracker segment of each track
+(Sec. "Introduction", Sec. "HLT1 details and results").  This package is the
+thin Python layer over ``libvelo.so`` (``include/velo.h``): it marshals torch
+tensors (device memory, streams) into the C structs and calls the library.
+Every step of the reconstruction runs in the library's CUDA kernels; there is
+no CPU fallback -- without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._build import LIB_PATH, build  # noqa: F401
+
+STATE_STRIDE = 20
+MAX_MODULES = 32
+EVT_OK, EVT_BADWORD, EVT_OVERFLOW = 0, 1, 2
+OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOMEM = range(6)
+STATE_FIELDS = ("x", "y", "tx", "ty", "z_first", "z_beam", "chi2_lsq", "chi2_kf", "kf_x", "kf_y", "kf_tx",
+                "kf_ty", "kf_cxx", "kf_cxtx", "kf_ctxtx", "kf_cyy", "kf_cyty", "kf_ctyty", "ndf", "reserved")
+
+_P = ctypes.c_void_p
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_modules", ctypes.c_uint32), ("module_z", ctypes.POINTER(ctypes.c_float)),
+                ("pitch_mm", ctypes.c_float), ("n_rows", ctypes.c_uint32), ("n_cols", ctypes.c_uint32),
+                ("x0_mm", ctypes.c_float), ("y0_mm", ctypes.c_float)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("win_seed", ctypes.c_float), ("win_fwd", ctypes.c_float), ("max_slope", ctypes.c_float),
+                ("max_scatter_seed", ctypes.c_float), ("max_scatter_fwd", ctypes.c_float),
+                ("max_skipped", ctypes.c_uint32), ("sigma_meas", ctypes.c_float), ("ms_theta", ctypes.c_float),
+                ("chi2ndf_max", ctypes.c_float), ("chi2ndf_max_3hit", ctypes.c_float)]
+
+
+class Events(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint64), ("n_pixels", ctypes.c_uint64), ("event_offsets", _P),
+                ("pixels", _P)]
+
+
+class Output(ctypes.Structure):
+    _fields_ = [("status", _P), ("cluster_offsets", _P), ("cluster_x", _P), ("cluster_y", _P), ("cluster_z", _P),
+                ("pixel_cluster", _P), ("track_offsets", _P), ("track_hit_offsets", _P), ("track_hits", _P),
+                ("track_states", _P), ("totals", _P)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("cap_clusters", ctypes.c_uint64), ("cap_tracks", ctypes.c_uint64),
+                ("cap_track_hits", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+
+
+class ResultView(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint64), ("n_pixels", ctypes.c_uint64), ("cap_clusters", ctypes.c_uint64),
+                ("cap_tracks", ctypes.c_uint64), ("cap_track_hits", ctypes.c_uint64), ("out", Output)]
+
+
+class VeloError(RuntimeError):
+    pass
+
+
+_lib = None
+
+# every entry point declared in include/velo.h
+EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "velo_reconstruct_into_marked",
+           "velo_reconstruct",
+           "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
+           "velo_reconstruct_host", "velo_strerror", "velo_version")
+
+
+def lib():
+    """The loaded ``libvelo.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise VeloError(f"{LIB_PATH} is missing: run paper_2412_05041_b300.build() (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.velo_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.velo_query_sizes.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Sizes)]
+        L.velo_reconstruct_into.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry), ctypes.POINTER(Params),
+                                            ctypes.POINTER(Output), _P, ctypes.c_uint64, _P]
+        L.velo_reconstruct_into_marked.argtypes = L.velo_reconstruct_into.argtypes + [ctypes.POINTER(_P)]
+        L.velo_reconstruct.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry), ctypes.POINTER(Params),
+                                       ctypes.POINTER(_P), _P]
+        L.velo_result_view.argtypes = [_P, ctypes.POINTER(ResultView)]
+        L.velo_result_free.argtypes = [_P]
+        L.velo_result_free.restype = None
+        L.velo_context_create.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(_P)]
+        L.velo_context_destroy.argtypes = [_P]
+        L.velo_context_destroy.restype = None
+        L.velo_reconstruct_host.argtypes = [_P, ctypes.POINTER(Events), ctypes.POINTER(Geometry),
+                                            ctypes.POINTER(Params), ctypes.POINTER(Output), _P]
+        L.velo_strerror.restype = ctypes.c_char_p
+        L.velo_strerror.argtypes = [ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def check(rc: int, what: str = "velo call"):
+    if rc != OK:
+        raise VeloError(f"{what} failed: {lib().velo_strerror(rc).decode()} ({rc})")
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    check(lib().velo_params_default(ctypes.byref(p)), "velo_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class _GeometryHolder:
+    """Keeps the module_z array alive while a Geometry struct points at it."""
+
+    def __init__(self, g):
+        n = int(g.n_modules)
+        self.z = (ctypes.c_float * n)(*[float(z) for z in g.module_z])
+        self.s = Geometry(n, ctypes.cast(self.z, ctypes.POINTER(ctypes.c_float)), float(g.pitch), int(g.n_rows),
+                          int(g.n_cols), float(g.x0), float(g.y0))
+
+
+def geometry_struct(g) -> _GeometryHolder:
+    """From any object with n_modules, module_z, pitch, n_rows, n_cols, x0, y0."""
+    return _GeometryHolder(g)
+
+
+def query_sizes(n_events: int, n_pixels: int) -> Sizes:
+    s = Sizes()
+    check(lib().velo_query_sizes(n_events, n_pixels, ctypes.byref(s)), "velo_query_sizes")
+    return s
+
+
+from .api import Reconstructor, HostReconstructor, reconstruct  # noqa: E402,F401

@@ -1,0 +1,391 @@
+// Host side of the C ABI declared in include/velo.h: argument validation,
+// workspace layout, the launch sequence, and the allocating conveniences.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "velo_internal.cuh"
+
+namespace velo {
+
+namespace {
+
+struct Carver {
+  uint8_t* base;
+  uint64_t off = 0;
+  template <class T>
+  T* take(uint64_t count) {
+    off = (off + 255ull) & ~255ull;
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
+  const uint64_t T = P / 3 + 1;
+  ws->flag = c.take<uint32_t>(4);
+  ws->ev_nclusters = c.take<uint32_t>(E);
+  ws->ev_modoff = c.take<uint32_t>(E * kModOffStride);
+  ws->ev_ntracks_all = c.take<uint32_t>(E);
+  ws->ev_ntracks = c.take<uint32_t>(E);
+  ws->ev_nhits = c.take<uint32_t>(E);
+  ws->ev_hitbase = c.take<uint64_t>(E);
+  ws->sa = c.take<uint32_t>(P);
+  ws->sb = c.take<uint32_t>(P);
+  ws->sc = c.take<uint32_t>(P);
+  ws->sd = c.take<uint32_t>(P);
+  ws->acc = c.take<unsigned long long>(3 * P);
+  ws->cl_x = c.take<float>(P);
+  ws->cl_y = c.take<float>(P);
+  ws->h_x = c.take<float>(P);
+  ws->h_y = c.take<float>(P);
+  ws->h_key = c.take<float>(P);
+  ws->h_id = c.take<uint32_t>(P);
+  ws->used = c.take<uint8_t>(P);
+  ws->trk_meta = c.take<uint32_t>(T);
+  ws->trk_a = c.take<uint32_t>(T);
+  ws->trk_b = c.take<uint32_t>(T);
+  ws->trk_pick = c.take<uint32_t>(T);
+  ws->trk_pick_key = c.take<unsigned long long>(T);
+  ws->trk_rank = c.take<uint32_t>(T);
+  ws->trk_hoff = c.take<uint32_t>(T);
+}
+
+bool geometry_ok(const velo_geometry_t* g) {
+  if (!g || !g->module_z) return false;
+  if (g->n_modules < 3 || g->n_modules > VELO_MAX_MODULES) return false;
+  if (g->n_rows < 1 || g->n_rows > 2048 || g->n_cols < 1 || g->n_cols > 2048) return false;
+  if (!(g->pitch_mm > 0.0f) || !std::isfinite(g->pitch_mm) || !std::isfinite(g->x0_mm) || !std::isfinite(g->y0_mm))
+    return false;
+  for (uint32_t m = 0; m < g->n_modules; ++m) {
+    if (!std::isfinite(g->module_z[m])) return false;
+    if (m && !(g->module_z[m] > g->module_z[m - 1])) return false;
+  }
+  return true;
+}
+
+bool params_ok(const velo_params_t* p) {
+  if (!p) return false;
+  auto fin = [](float v) { return std::isfinite(v); };
+  if (!fin(p->win_seed) || p->win_seed < 0.0f || p->win_seed > 1.0f) return false;
+  if (!fin(p->win_fwd) || p->win_fwd < 0.0f || p->win_fwd > 1.0f) return false;
+  if (!fin(p->max_slope) || p->max_slope < 0.0f) return false;
+  if (!fin(p->max_scatter_seed) || p->max_scatter_seed < 0.0f) return false;
+  if (!fin(p->max_scatter_fwd) || p->max_scatter_fwd < 0.0f) return false;
+  if (p->max_skipped >= VELO_MAX_MODULES) return false;
+  if (!fin(p->sigma_meas) || !(p->sigma_meas > 0.0f)) return false;
+  if (!fin(p->ms_theta) || p->ms_theta < 0.0f) return false;
+  if (!fin(p->chi2ndf_max) || !fin(p->chi2ndf_max_3hit)) return false;
+  return true;
+}
+
+bool output_ok(const velo_output_t* o) {
+  return o && o->status && o->cluster_offsets && o->cluster_x && o->cluster_y && o->cluster_z && o->track_offsets &&
+         o->track_hit_offsets && o->track_hits && o->track_states && o->totals;
+}
+
+Geo make_geo(const velo_geometry_t* g) {
+  Geo G;
+  std::memset(&G, 0, sizeof(G));
+  G.n_modules = g->n_modules;
+  G.n_rows = g->n_rows;
+  G.n_cols = g->n_cols;
+  G.pitch = g->pitch_mm;
+  G.x0 = g->x0_mm;
+  G.y0 = g->y0_mm;
+  for (uint32_t m = 0; m < g->n_modules; ++m) G.z[m] = g->module_z[m];
+  return G;
+}
+
+Par make_par(const velo_params_t* p) {
+  Par P;
+  P.win_seed = p->win_seed;
+  P.win_fwd = p->win_fwd;
+  P.max_slope = p->max_slope;
+  P.max_scatter_seed = p->max_scatter_seed;
+  P.max_scatter_fwd = p->max_scatter_fwd;
+  P.max_skipped = p->max_skipped;
+  P.sigma = p->sigma_meas;
+  P.ms_theta = p->ms_theta;
+  P.chi2ndf_max = p->chi2ndf_max;
+  P.chi2ndf_max_3hit = p->chi2ndf_max_3hit;
+  return P;
+}
+
+}  // namespace
+
+uint64_t workspace_bytes(uint64_t E, uint64_t P) {
+  Carver c{nullptr};
+  Workspace ws;
+  carve(c, E, P, &ws);
+  return (c.off + 255ull) & ~255ull;
+}
+
+bool carve_workspace(void* base, uint64_t bytes, uint64_t E, uint64_t P, Workspace* ws) {
+  if (workspace_bytes(E, P) > bytes) return false;
+  Carver c{reinterpret_cast<uint8_t*>(base)};
+  carve(c, E, P, ws);
+  return true;
+}
+
+}  // namespace velo
+
+using namespace velo;
+
+struct velo_result {
+  uint64_t n_events, n_pixels;
+  velo_sizes_t sizes;
+  velo_output_t out;
+  void* workspace;
+  cudaStream_t stream;
+};
+
+struct velo_context {
+  uint64_t max_events, max_pixels;
+  velo_sizes_t sizes;
+  uint64_t* d_off;
+  uint32_t* d_pix;
+  velo_output_t d_out;
+  void* workspace;
+};
+
+extern "C" {
+
+int velo_version(void) { return 100; }
+
+const char* velo_strerror(int code) {
+  switch (code) {
+    case VELO_OK: return "ok";
+    case VELO_EINVAL: return "invalid argument";
+    case VELO_ECAPACITY: return "buffer or workspace too small";
+    case VELO_ECUDA: return "CUDA runtime error";
+    case VELO_ETIMEOUT: return "bounded device wait timed out";
+    case VELO_ENOMEM: return "allocation failed";
+    default: return "unknown error";
+  }
+}
+
+int velo_params_default(velo_params_t* p) {
+  if (!p) return VELO_EINVAL;
+  p->win_seed = 0.04f;
+  p->win_fwd = 0.04f;
+  p->max_slope = 0.3f;
+  p->max_scatter_seed = 0.01f;
+  p->max_scatter_fwd = 0.02f;
+  p->max_skipped = 1;
+  p->sigma_meas = 0.0159f;
+  p->ms_theta = 5e-4f;
+  p->chi2ndf_max = 10.0f;
+  p->chi2ndf_max_3hit = 2.0f;
+  return VELO_OK;
+}
+
+int velo_query_sizes(uint64_t n_events, uint64_t n_pixels, velo_sizes_t* out) {
+  if (!out || n_events >= (1ull << 31) || n_pixels >= (1ull << 40)) return VELO_EINVAL;
+  out->cap_clusters = n_pixels;
+  out->cap_tracks = n_pixels / 3;
+  out->cap_track_hits = n_pixels;
+  out->workspace_bytes = workspace_bytes(n_events, n_pixels);
+  return VELO_OK;
+}
+
+int velo_reconstruct_into(const velo_events_t* events, const velo_geometry_t* geometry, const velo_params_t* params,
+                          const velo_output_t* out, void* workspace, uint64_t workspace_bytes_, void* stream) {
+  return velo_reconstruct_into_marked(events, geometry, params, out, workspace, workspace_bytes_, stream, nullptr);
+}
+
+int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometry_t* geometry,
+                                 const velo_params_t* params, const velo_output_t* out, void* workspace,
+                                 uint64_t workspace_bytes_, void* stream, void* const* marks) {
+  if (!events || !events->event_offsets || (events->n_pixels && !events->pixels)) return VELO_EINVAL;
+  if (events->n_events >= (1ull << 31) || events->n_pixels >= (1ull << 40)) return VELO_EINVAL;
+  if (!geometry_ok(geometry) || !params_ok(params) || !output_ok(out)) return VELO_EINVAL;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return VELO_EINVAL;
+  Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_events = events->n_events;
+  L.n_pixels = events->n_pixels;
+  L.off = events->event_offsets;
+  L.pix = events->pixels;
+  L.geo = make_geo(geometry);
+  L.par = make_par(params);
+  L.out = *out;
+  if (!carve_workspace(workspace, workspace_bytes_, L.n_events, L.n_pixels, &L.ws)) return VELO_ECAPACITY;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const unsigned E = (unsigned)L.n_events;
+  auto mark = [&](int i) {
+    if (marks && marks[i]) cudaEventRecord(reinterpret_cast<cudaEvent_t>(marks[i]), s);
+  };
+  k_validate_offsets<<<1, kScanThreads, 0, s>>>(L);
+  mark(0);
+  if (E) {
+    const uint32_t smem = cluster_smem_bytes();
+    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return VELO_ECUDA;
+    k_cluster<<<E, kClusterThreads, smem, s>>>(L);
+  }
+  mark(1);
+  if (E) k_track<<<E, kTrackThreads, 0, s>>>(L);
+  mark(2);
+  k_scan<<<1, kScanThreads, 0, s>>>(L);
+  mark(3);
+  if (E) k_output<<<E, kOutputThreads, 0, s>>>(L);
+  mark(4);
+  return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;
+}
+
+int velo_reconstruct(const velo_events_t* events, const velo_geometry_t* geometry, const velo_params_t* params,
+                     velo_result_t** result, void* stream) {
+  if (!result || !events) return VELO_EINVAL;
+  *result = nullptr;
+  velo_sizes_t sz;
+  if (velo_query_sizes(events->n_events, events->n_pixels, &sz) != VELO_OK) return VELO_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  velo_result* r = new velo_result;
+  std::memset(r, 0, sizeof(*r));
+  r->n_events = events->n_events;
+  r->n_pixels = events->n_pixels;
+  r->sizes = sz;
+  r->stream = s;
+  const uint64_t E = events->n_events;
+  bool ok = true;
+  auto alloc = [&](void** p, uint64_t bytes) {
+    if (cudaMallocAsync(p, bytes ? bytes : 256, s) != cudaSuccess) ok = false;
+  };
+  alloc((void**)&r->out.status, 4 * E);
+  alloc((void**)&r->out.cluster_offsets, 8 * (E + 1));
+  alloc((void**)&r->out.cluster_x, 4 * sz.cap_clusters);
+  alloc((void**)&r->out.cluster_y, 4 * sz.cap_clusters);
+  alloc((void**)&r->out.cluster_z, 4 * sz.cap_clusters);
+  alloc((void**)&r->out.pixel_cluster, 4 * events->n_pixels);
+  alloc((void**)&r->out.track_offsets, 8 * (E + 1));
+  alloc((void**)&r->out.track_hit_offsets, 8 * (sz.cap_tracks + 1));
+  alloc((void**)&r->out.track_hits, 4 * sz.cap_track_hits);
+  alloc((void**)&r->out.track_states, 4ull * VELO_STATE_STRIDE * (sz.cap_tracks ? sz.cap_tracks : 1));
+  alloc((void**)&r->out.totals, 8 * 4);
+  alloc(&r->workspace, sz.workspace_bytes);
+  if (!ok) {
+    velo_result_free(r);
+    cudaGetLastError();
+    return VELO_ENOMEM;
+  }
+  const int rc = velo_reconstruct_into(events, geometry, params, &r->out, r->workspace, sz.workspace_bytes, stream);
+  if (rc != VELO_OK) {
+    velo_result_free(r);
+    return rc;
+  }
+  *result = r;
+  return VELO_OK;
+}
+
+int velo_result_view(const velo_result_t* r, velo_result_view_t* v) {
+  if (!r || !v) return VELO_EINVAL;
+  v->n_events = r->n_events;
+  v->n_pixels = r->n_pixels;
+  v->cap_clusters = r->sizes.cap_clusters;
+  v->cap_tracks = r->sizes.cap_tracks;
+  v->cap_track_hits = r->sizes.cap_track_hits;
+  v->out = r->out;
+  return VELO_OK;
+}
+
+void velo_result_free(velo_result_t* r) {
+  if (!r) return;
+  void* ptrs[] = {r->out.status,    r->out.cluster_offsets, r->out.cluster_x,         r->out.cluster_y,
+                  r->out.cluster_z, r->out.pixel_cluster,   r->out.track_offsets,     r->out.track_hit_offsets,
+                  r->out.track_hits, r->out.track_states,   r->out.totals,            r->workspace};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, r->stream);
+  delete r;
+}
+
+int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t** ctx) {
+  if (!ctx) return VELO_EINVAL;
+  *ctx = nullptr;
+  velo_sizes_t sz;
+  if (velo_query_sizes(max_events, max_pixels, &sz) != VELO_OK) return VELO_EINVAL;
+  velo_context* c = new velo_context;
+  std::memset(c, 0, sizeof(*c));
+  c->max_events = max_events;
+  c->max_pixels = max_pixels;
+  c->sizes = sz;
+  bool ok = true;
+  auto alloc = [&](void** p, uint64_t bytes) {
+    if (cudaMalloc(p, bytes ? bytes : 256) != cudaSuccess) ok = false;
+  };
+  const uint64_t E = max_events;
+  alloc((void**)&c->d_off, 8 * (E + 1));
+  alloc((void**)&c->d_pix, 4 * max_pixels);
+  alloc((void**)&c->d_out.status, 4 * E);
+  alloc((void**)&c->d_out.cluster_offsets, 8 * (E + 1));
+  alloc((void**)&c->d_out.cluster_x, 4 * sz.cap_clusters);
+  alloc((void**)&c->d_out.cluster_y, 4 * sz.cap_clusters);
+  alloc((void**)&c->d_out.cluster_z, 4 * sz.cap_clusters);
+  alloc((void**)&c->d_out.pixel_cluster, 4 * max_pixels);
+  alloc((void**)&c->d_out.track_offsets, 8 * (E + 1));
+  alloc((void**)&c->d_out.track_hit_offsets, 8 * (sz.cap_tracks + 1));
+  alloc((void**)&c->d_out.track_hits, 4 * sz.cap_track_hits);
+  alloc((void**)&c->d_out.track_states, 4ull * VELO_STATE_STRIDE * (sz.cap_tracks ? sz.cap_tracks : 1));
+  alloc((void**)&c->d_out.totals, 8 * 4);
+  alloc(&c->workspace, sz.workspace_bytes);
+  if (!ok) {
+    velo_context_destroy(c);
+    cudaGetLastError();
+    return VELO_ENOMEM;
+  }
+  *ctx = c;
+  return VELO_OK;
+}
+
+void velo_context_destroy(velo_context_t* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_off,           c->d_pix,           c->d_out.status,           c->d_out.cluster_offsets,
+                  c->d_out.cluster_x, c->d_out.cluster_y, c->d_out.cluster_z,        c->d_out.pixel_cluster,
+                  c->d_out.track_offsets, c->d_out.track_hit_offsets, c->d_out.track_hits, c->d_out.track_states,
+                  c->d_out.totals,    c->workspace};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo_geometry_t* geometry,
+                          const velo_params_t* params, const velo_output_t* ho, void* stream) {
+  if (!c || !ev || !ev->event_offsets || (ev->n_pixels && !ev->pixels)) return VELO_EINVAL;
+  if (!ho || !ho->status || !ho->cluster_offsets || !ho->track_offsets || !ho->track_hit_offsets || !ho->track_hits ||
+      !ho->track_states || !ho->totals)
+    return VELO_EINVAL;
+  if (ev->n_events > c->max_events || ev->n_pixels > c->max_pixels) return VELO_ECAPACITY;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t E = ev->n_events, P = ev->n_pixels;
+  if (cudaMemcpyAsync(c->d_off, ev->event_offsets, 8 * (E + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return VELO_ECUDA;
+  if (P && cudaMemcpyAsync(c->d_pix, ev->pixels, 4 * P, cudaMemcpyHostToDevice, s) != cudaSuccess) return VELO_ECUDA;
+  velo_events_t dev = {E, P, c->d_off, c->d_pix};
+  velo_output_t dout = c->d_out;
+  if (!ho->pixel_cluster) dout.pixel_cluster = nullptr;
+  int rc = velo_reconstruct_into(&dev, geometry, params, &dout, c->workspace, c->sizes.workspace_bytes, stream);
+  if (rc != VELO_OK) return rc;
+  bool ok = true;
+  auto d2h = [&](void* dst, const void* src, uint64_t bytes) {
+    if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ok = false;
+  };
+  d2h(ho->totals, dout.totals, 32);
+  d2h(ho->status, dout.status, 4 * E);
+  d2h(ho->cluster_offsets, dout.cluster_offsets, 8 * (E + 1));
+  d2h(ho->track_offsets, dout.track_offsets, 8 * (E + 1));
+  if (ho->pixel_cluster) d2h(ho->pixel_cluster, dout.pixel_cluster, 4 * P);
+  if (!ok || cudaStreamSynchronize(s) != cudaSuccess) return VELO_ECUDA;
+  const uint64_t nc = ho->totals[0], nt = ho->totals[1], nh = ho->totals[2];
+  if (ho->cluster_x) d2h(ho->cluster_x, dout.cluster_x, 4 * nc);
+  if (ho->cluster_y) d2h(ho->cluster_y, dout.cluster_y, 4 * nc);
+  if (ho->cluster_z) d2h(ho->cluster_z, dout.cluster_z, 4 * nc);
+  d2h(ho->track_hit_offsets, dout.track_hit_offsets, 8 * (nt + 1));
+  d2h(ho->track_hits, dout.track_hits, 4 * nh);
+  d2h(ho->track_states, dout.track_states, 4ull * VELO_STATE_STRIDE * nt);
+  if (!ok || cudaStreamSynchronize(s) != cudaSuccess) return VELO_ECUDA;
+  return VELO_OK;
+}
+
+}  // extern "C"

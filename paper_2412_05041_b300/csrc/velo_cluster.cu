@@ -1,0 +1,277 @@
+// Clustering kernel: pixel words of one event -> clusters (hits).
+//
+// The first stage reconstructs every event from the raw detector data
+// (Sec. "Data flow overview"); for the pixel tracker this starts with
+// clustering.  One CTA per event (1024 threads, one CTA per SM):
+//   1. load and validate the event's words (coalesced, 4 B per thread);
+//   2. stable block radix sort by the 27-bit (module, row, col) key
+//      (4 passes of 8 bits) in shared memory;
+//   3. union-find over 8-connected neighbours found in the sorted array
+//      (the left neighbour and duplicates sit just before a word, the
+//      previous row by binary search); a union links the larger root under
+//      the smaller with atomicMin, so every root ends as the smallest sorted
+//      position of its component, i.e. its smallest (module, row, col);
+//   4. cluster id = exclusive scan of root flags (canonical, order-free);
+//   5. integer charge sums per cluster with 64-bit atomics (exact, so the
+//      order of the additions does not matter) and the binary32 centroid;
+//   6. pseudo-angle key and a stable block radix sort of the hits by
+//      (module, key, id): 4 passes over the key bits + 1 over the module.
+// Events larger than the shared-memory tier run the same code on their
+// slice of the global workspace (generic pointers).
+#include "velo_device.cuh"
+#include "velo_internal.cuh"
+
+namespace velo {
+
+namespace {
+
+struct ClusterSmem {
+  uint32_t cnt[kRadixCounters];
+  uint32_t tmp[64];
+  uint32_t mod_count[VELO_MAX_MODULES];
+  uint32_t mod_off[kModOffStride];
+  uint32_t flag;
+  uint32_t pad[2];
+};
+
+constexpr uint32_t kRootFlag = 0x80000000u;
+
+__device__ __forceinline__ uint32_t vload(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+__device__ __forceinline__ uint32_t uf_find(const uint32_t* parent, uint32_t a) {
+  for (;;) {  // parent[x] < x for every non-root: at most a steps
+    const uint32_t p = vload(parent + a);
+    if (p == a) return a;
+    a = p;
+  }
+}
+
+// Link the larger root under the smaller.  Returns false if the retry bound
+// was hit (never expected; the event is then failed instead of looping).
+__device__ __forceinline__ bool uf_unite(uint32_t* parent, uint32_t a, uint32_t b) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return true;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicMin(parent + a, b);
+    if (old == a) return true;
+    a = old;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool word_valid(uint32_t w, const Geo& g) {
+  return (w >> 31) == 0u && ((w >> 27) & 15u) != 0u && ((w >> 22) & 31u) < g.n_modules &&
+         ((w >> 11) & 2047u) < g.n_rows && (w & 2047u) < g.n_cols;
+}
+
+__device__ __forceinline__ uint32_t module_of(const uint32_t* mod_off, uint32_t n_modules, uint32_t id) {
+  // largest m with mod_off[m] <= id
+  uint32_t lo = 0, hi = n_modules;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (mod_off[mid] <= id) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offsets_ok, uint64_t p0, uint32_t n) {
+  if (threadIdx.x == 0) {
+    L.out.status[e] = code;
+    L.ws.ev_nclusters[e] = 0;
+  }
+  if (threadIdx.x < kModOffStride) L.ws.ev_modoff[e * kModOffStride + threadIdx.x] = 0;
+  if (offsets_ok && L.out.pixel_cluster)
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) L.out.pixel_cluster[p0 + i] = kNone;
+}
+
+}  // namespace
+
+uint32_t cluster_smem_bytes() { return (uint32_t)sizeof(ClusterSmem) + 2u * kClusterSmemPixels * 4u; }
+
+__global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
+  constexpr int NT = kClusterThreads;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  ClusterSmem& S = *reinterpret_cast<ClusterSmem*>(smem_raw);
+  uint32_t* region = reinterpret_cast<uint32_t*>(smem_raw + sizeof(ClusterSmem));
+  const Workspace& W = L.ws;
+  const uint64_t e = blockIdx.x;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t M = L.geo.n_modules;
+
+  const bool offsets_ok = *(const volatile uint32_t*)W.flag == 0u;
+  uint64_t p0 = 0, p1 = 0;
+  if (offsets_ok) {
+    p0 = L.off[e];
+    p1 = L.off[e + 1];
+  }
+  const uint32_t n = (uint32_t)(p1 - p0);
+  if (tid == 0) S.flag = offsets_ok ? 0u : 1u;
+  if (tid < VELO_MAX_MODULES) S.mod_count[tid] = 0;
+  __syncthreads();
+
+  // 1. load + validate
+  const bool smem_tier = n <= kClusterSmemPixels;
+  uint32_t* A = smem_tier ? region : W.sa + p0;
+  uint32_t* B = smem_tier ? region + kClusterSmemPixels : W.sb + p0;
+  if (offsets_ok) {
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t w = __ldg(L.pix + p0 + i);
+      if (!word_valid(w, L.geo)) S.flag = 1u;
+      A[i] = w;
+    }
+  }
+  __syncthreads();
+  if (S.flag) {
+    fail_event(L, e, VELO_EVT_BADWORD, offsets_ok, p0, n);
+    return;
+  }
+
+  // 2. sort by (module, row, col); 4 passes A->B->A->B->A
+  radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                        [](uint32_t k, uint32_t) { return (k & kKeyMask) & 255u; }, S.cnt, S.tmp);
+  radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                        [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 8) & 255u; }, S.cnt, S.tmp);
+  radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                        [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 16) & 255u; }, S.cnt, S.tmp);
+  radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                        [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 24; }, S.cnt, S.tmp);
+
+  // 3. union-find over 8-connected neighbours
+  for (uint32_t i = tid; i < n; i += NT) B[i] = i;
+  __syncthreads();
+  bool ok = true;
+  for (uint32_t i = tid; i < n; i += NT) {
+    const uint32_t k = A[i] & kKeyMask;
+    const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
+    // duplicates of k and the left neighbour (k - 1) are the words just before i
+    for (int64_t j = (int64_t)i - 1; j >= 0; --j) {
+      const uint32_t kj = A[j] & kKeyMask;
+      if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)j);
+      else break;
+    }
+    if (r > 0u) {  // previous row, columns c-1 .. c+1 of the same module
+      const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u);
+      const uint32_t hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
+      uint32_t j = lower_bound_by(0u, i, [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+      for (; j < i && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j);
+    }
+  }
+  if (!ok) S.flag = 2u;
+  __syncthreads();
+  if (S.flag) {
+    fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
+    return;
+  }
+  for (uint32_t i = tid; i < n; i += NT) B[i] = uf_find(B, i);
+  __syncthreads();
+
+  // 4. cluster ids: rank of each root among the roots (chunked block scan)
+  const uint32_t ch = (n + NT - 1) / NT;
+  const uint32_t lo = min(n, tid * ch), hi = min(n, lo + ch);
+  uint32_t nroot = 0;
+  for (uint32_t i = lo; i < hi; ++i) nroot += (B[i] == i);
+  uint32_t n_clusters;
+  uint32_t rank = block_exclusive_scan<NT, uint32_t>(nroot, &n_clusters, S.tmp);
+  for (uint32_t i = lo; i < hi; ++i)
+    if (B[i] == i) {
+      B[i] = rank++ | kRootFlag;
+      atomicAdd(&S.mod_count[(A[i] >> 22) & 31u], 1u);
+    }
+  __syncthreads();
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t v = B[i];
+    B[i] = (v & kRootFlag) ? (v & ~kRootFlag) : (vload(B + v) & ~kRootFlag);
+  }
+  if (tid == 0) {
+    uint32_t o = 0;
+    for (uint32_t m = 0; m < M; ++m) {
+      S.mod_off[m] = o;
+      if (S.mod_count[m] > VELO_MAX_MODULE_CLUSTERS) S.flag = 3u;
+      o += S.mod_count[m];
+    }
+    S.mod_off[M] = o;
+  }
+  __syncthreads();
+  if (S.flag) {
+    fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
+    return;
+  }
+
+  // optional per-word labels in input order
+  if (L.out.pixel_cluster) {
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t k = __ldg(L.pix + p0 + i) & kKeyMask;
+      const uint32_t j = lower_bound_by(0u, n, [&](uint32_t x) { return (A[x] & kKeyMask) < k; });
+      L.out.pixel_cluster[p0 + i] = j < n ? B[j] : kNone;  // j < n always: the word is in A
+    }
+  }
+
+  // 5. integer charge sums per cluster, then the binary32 centroid
+  unsigned long long* acc = W.acc + 3 * p0;
+  for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc[i] = 0ull;
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += NT) {
+    const uint32_t w = A[i];
+    const uint32_t q = (w >> 27) & 15u, c = w & 2047u, r = (w >> 11) & 2047u;
+    unsigned long long* a3 = acc + 3ull * B[i];
+    atomicAdd(a3 + 0, (unsigned long long)q);
+    atomicAdd(a3 + 1, (unsigned long long)(q * (2u * c + 1u)));
+    atomicAdd(a3 + 2, (unsigned long long)(q * (2u * r + 1u)));
+  }
+  __syncthreads();
+
+  // the pixel arrays are dead from here on: the hit sort reuses the region
+  const bool hit_smem = 2u * n_clusters <= kClusterSmemPixels;
+  uint32_t* KA = hit_smem ? region : W.sa + p0;
+  uint32_t* KB = hit_smem ? region + n_clusters : W.sb + p0;
+  uint32_t* VA = hit_smem ? region + kClusterSmemPixels : W.sc + p0;
+  uint32_t* VB = hit_smem ? region + kClusterSmemPixels + n_clusters : W.sd + p0;
+  const Geo& g = L.geo;
+  for (uint32_t id = tid; id < n_clusters; id += NT) {
+    const unsigned long long sq = acc[3 * id], snx = acc[3 * id + 1], sny = acc[3 * id + 2];
+    const unsigned long long D = 2ull * sq;
+    const float Df = __ull2float_rn(D);
+    const float u = __fadd_rn(__ull2float_rn(snx / D), __fdiv_rn(__ull2float_rn(snx % D), Df));
+    const float v = __fadd_rn(__ull2float_rn(sny / D), __fdiv_rn(__ull2float_rn(sny % D), Df));
+    const float x = __fadd_rn(g.x0, __fmul_rn(g.pitch, u));
+    const float y = __fadd_rn(g.y0, __fmul_rn(g.pitch, v));
+    W.cl_x[p0 + id] = x;
+    W.cl_y[p0 + id] = y;
+    KA[id] = __float_as_uint(pseudo_angle(x, y));
+    VA[id] = id;
+  }
+  __syncthreads();
+
+  // 6. hits sorted by (module, key, id): key bits LSD (ids enter ascending,
+  // so equal keys stay in id order), then a stable pass on the module.
+  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k & 255u; }, S.cnt, S.tmp);
+  radix_pass<NT, true>(KB, KA, VB, VA, n_clusters, [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.cnt,
+                       S.tmp);
+  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.cnt,
+                       S.tmp);
+  radix_pass<NT, true>(KB, KA, VB, VA, n_clusters, [](uint32_t k, uint32_t) { return k >> 24; }, S.cnt, S.tmp);
+  const uint32_t* mo = S.mod_off;
+  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters,
+                       [mo, M](uint32_t, uint32_t id) { return module_of(mo, M, id); }, S.cnt, S.tmp);
+  for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
+    const uint32_t id = VB[pos];
+    W.h_x[p0 + pos] = W.cl_x[p0 + id];
+    W.h_y[p0 + pos] = W.cl_y[p0 + id];
+    W.h_key[p0 + pos] = __uint_as_float(KB[pos]);
+    W.h_id[p0 + pos] = id;
+  }
+  if (tid <= M) W.ev_modoff[e * kModOffStride + tid] = S.mod_off[tid];
+  if (tid == 0) {
+    W.ev_nclusters[e] = n_clusters;
+    L.out.status[e] = VELO_EVT_OK;
+  }
+}
+
+}  // namespace velo

@@ -1,0 +1,192 @@
+// Device helpers of the VELO tracking kernels (sm_103a).
+//
+// Everything here is either integer work or binary32 arithmetic written in
+// the one order the method fixes; the library is compiled with -fmad=false so
+// that no multiply-add pair is contracted into an FMA.
+#pragma once
+
+#include <stdint.h>
+
+namespace velo {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kKeyMask = 0x7FFFFFFu;  // (module, row, col) bits of a pixel word
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t warp_id() { return threadIdx.x >> 5; }
+
+// ---------------------------------------------------------------- scans
+// Exclusive block-wide scan of one value per thread.  tmp: >= NT/32 + 1 words
+// of shared memory, reused on return.  *total receives the block sum.
+template <int NT, class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* tmp) {
+  constexpr int NW = NT / 32;
+  const uint32_t lane = lane_id(), w = warp_id();
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(kFull, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) tmp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T s = lane < (uint32_t)NW ? tmp[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(kFull, s, o);
+      if (lane >= (uint32_t)o) s += y;
+    }
+    if (lane < (uint32_t)NW) tmp[lane] = s;
+  }
+  __syncthreads();
+  T base = w ? tmp[w - 1] : T(0);
+  *total = tmp[NW - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// ---------------------------------------------------------------- radix sort
+// One stable LSD pass of a block-wide radix sort with 8-bit digits.
+// The n elements are cut into one contiguous chunk per warp; every warp
+// histograms its chunk into its own column of cnt (256 x NW counters in
+// shared memory), one exclusive scan in (digit, warp) order gives each
+// (digit, warp) its first output slot, and every warp then scatters its chunk
+// in index order (rank among equal digits from __match_any_sync), so equal
+// digits keep their relative order.  a/b (and va/vb) may live in shared or
+// global memory.
+template <int NT, bool HAS_VAL, class K, class DigitF>
+__device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, uint32_t n, DigitF digit,
+                           uint32_t* cnt, uint32_t* tmp) {
+  constexpr int NW = NT / 32;
+  constexpr uint32_t NB = 256;
+  const uint32_t lane = lane_id(), w = warp_id();
+  for (uint32_t i = threadIdx.x; i < NB * NW; i += NT) cnt[i] = 0;
+  __syncthreads();
+  const uint32_t chunk = (n + NW - 1) / NW;
+  const uint32_t s = min(n, w * chunk), e = min(n, s + chunk);
+  for (uint32_t base = s; base < e; base += 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < e;
+    uint32_t d = NB;
+    if (valid) d = digit(a[i], HAS_VAL ? va[i] : 0u);
+    const uint32_t peers = __match_any_sync(kFull, d);
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) cnt[d * NW + w] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive scan of the 256*NW counters; thread t owns 8 consecutive entries
+  constexpr int PER = NB * NW / NT;
+  uint32_t loc[PER], sum = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    loc[j] = cnt[threadIdx.x * PER + j];
+    sum += loc[j];
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &tot, tmp);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    cnt[threadIdx.x * PER + j] = run;
+    run += loc[j];
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t base = s; base < e; base += 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < e;
+    K k = K(0);
+    uint32_t v = 0, d = NB;
+    if (valid) {
+      k = a[i];
+      if (HAS_VAL) v = va[i];
+      d = digit(k, v);
+    }
+    const uint32_t peers = __match_any_sync(kFull, d);
+    if (valid) {
+      const uint32_t pos = cnt[d * NW + w] + __popc(peers & lt);
+      b[pos] = k;
+      if (HAS_VAL) vb[pos] = v;
+    }
+    __syncwarp();
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) cnt[d * NW + w] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- searches
+// first index in [lo, hi) with key(a[i]) >= v (a sorted by key)
+template <class F>
+__device__ __forceinline__ uint32_t lower_bound_by(uint32_t lo, uint32_t hi, F key_less_than_v) {
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (key_less_than_v(mid)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- geometry
+// Pseudo-angle ("diamond angle") in [0, 4), monotone in phi: one division,
+// no transcendental function (so CPU and GPU agree bit for bit).
+__device__ __forceinline__ float pseudo_angle(float x, float y) {
+  float k;
+  if (y >= 0.0f) {
+    if (x >= 0.0f) {
+      const float d = __fadd_rn(x, y);
+      k = d > 0.0f ? __fdiv_rn(y, d) : 0.0f;
+    } else {
+      k = __fadd_rn(1.0f, __fdiv_rn(-x, __fsub_rn(y, x)));
+    }
+  } else {
+    if (x < 0.0f) {
+      k = __fadd_rn(2.0f, __fdiv_rn(-y, __fsub_rn(-x, y)));
+    } else {
+      k = __fadd_rn(3.0f, __fdiv_rn(x, __fsub_rn(x, y)));
+    }
+  }
+  return __fadd_rn(k, 0.0f);  // -0 -> +0
+}
+
+// |a - b| on the circle of circumference 4
+__device__ __forceinline__ float dmod4(float a, float b) {
+  float d = fabsf(__fsub_rn(a, b));
+  if (d > 2.0f) d = __fsub_rn(4.0f, d);
+  return d;
+}
+
+// Candidate index ranges of a sorted key array (positions [lo, hi)) that
+// contain every key within half-width w of k on the circle [0, 4).  The
+// ranges are a superset (margin 1e-5 >> rounding of k +- w); callers apply
+// the exact dmod4 test to every candidate.
+struct Ranges {
+  uint32_t a0, a1, b0, b1;  // [a0, a1) and [b0, b1)
+};
+
+__device__ __forceinline__ Ranges window_ranges(const float* keys, uint32_t lo, uint32_t hi, float k, float w) {
+  const float eps = 1e-5f;
+  const float a = k - w - eps, b = k + w + eps;
+  auto lb = [&](float v) { return lower_bound_by(lo, hi, [&](uint32_t i) { return keys[i] < v; }); };
+  auto ub = [&](float v) { return lower_bound_by(lo, hi, [&](uint32_t i) { return keys[i] <= v; }); };
+  Ranges r;
+  if (a < 0.0f) {
+    r.a0 = lo;
+    r.a1 = ub(b);
+    r.b0 = max(lb(a + 4.0f), r.a1);
+    r.b1 = hi;
+  } else if (b >= 4.0f) {
+    r.a0 = lo;
+    r.a1 = ub(b - 4.0f);
+    r.b0 = max(lb(a), r.a1);
+    r.b1 = hi;
+  } else {
+    r.a0 = lb(a);
+    r.a1 = ub(b);
+    r.b0 = r.b1 = r.a1;
+  }
+  return r;
+}
+
+}  // namespace velo

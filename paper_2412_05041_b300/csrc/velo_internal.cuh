@@ -1,0 +1,97 @@
+// Internal launch arguments and workspace layout of the VELO tracking library.
+#pragma once
+
+#include <stdint.h>
+
+#include "velo.h"
+
+namespace velo {
+
+// Block shapes.
+constexpr int kClusterThreads = 1024;  // one CTA per event, one CTA per SM (shared-memory bound)
+constexpr int kTrackThreads = 256;     // one CTA per event, several CTAs per SM
+constexpr int kOutputThreads = 256;
+constexpr int kScanThreads = 1024;
+
+// Clustering keeps an event's sorted pixel words and their union-find
+// parents in shared memory when it has at most this many words; larger
+// events run the same code on their slice of the global workspace.
+constexpr uint32_t kClusterSmemPixels = 23552;
+constexpr uint32_t kRadixCounters = 256 * (kClusterThreads / 32);
+constexpr uint32_t kModOffStride = 33;  // per-event module offsets, n_modules + 1 <= 33
+
+// Per-track metadata word: n_hits (8 bits) | active (1 bit) << 8 |
+// module of the last (most upstream) hit << 16 | module of the one before << 24.
+constexpr uint32_t kTrkActive = 1u << 8;
+
+// Device scratch, carved out of the caller's workspace.  Arrays marked
+// "pixel-indexed" give each event the slice [event_offsets[e], +n_e); arrays
+// marked "track-indexed" the slice [event_offsets[e] / 3, + n_e / 3): an
+// event has at most n_e clusters and n_e / 3 tracks, so slices never overlap.
+struct Workspace {
+  uint32_t* flag;            // [1] offsets invalid
+  uint32_t* ev_nclusters;    // [E]
+  uint32_t* ev_modoff;       // [E * 33] cluster-id (= sorted position) offsets per module
+  uint32_t* ev_ntracks_all;  // [E] tracks built (kept or not)
+  uint32_t* ev_ntracks;      // [E] tracks kept
+  uint32_t* ev_nhits;        // [E] hits on kept tracks
+  uint64_t* ev_hitbase;      // [E] first global position of the event's track hits
+  uint32_t* sa;              // pixel-indexed u32: sort ping-pong / seed h0
+  uint32_t* sb;              // pixel-indexed u32: sort ping-pong / seed h2
+  uint32_t* sc;              // pixel-indexed u32: hit-sort values / prev link
+  uint32_t* sd;              // pixel-indexed u32: hit-sort values / first_of
+  unsigned long long* acc;   // pixel-indexed x3: centroid sums / claims + seed keys
+  float* cl_x;               // pixel-indexed: cluster x in id order
+  float* cl_y;               // pixel-indexed: cluster y in id order
+  float* h_x;                // pixel-indexed: hits sorted by (module, key, id)
+  float* h_y;
+  float* h_key;
+  uint32_t* h_id;
+  uint8_t* used;             // pixel-indexed
+  uint32_t* trk_meta;        // track-indexed
+  uint32_t* trk_a;           // last hit position
+  uint32_t* trk_b;           // hit position before it
+  uint32_t* trk_pick;        // extension candidate of this step
+  unsigned long long* trk_pick_key;
+  uint32_t* trk_rank;        // canonical rank among kept tracks, kNone if dropped
+  uint32_t* trk_hoff;        // first hit of the track among the event's kept hits
+};
+
+struct Geo {
+  uint32_t n_modules, n_rows, n_cols;
+  float pitch, x0, y0;
+  float z[VELO_MAX_MODULES];
+};
+
+struct Par {
+  float win_seed, win_fwd, max_slope, max_scatter_seed, max_scatter_fwd;
+  uint32_t max_skipped;
+  float sigma, ms_theta, chi2ndf_max, chi2ndf_max_3hit;
+};
+
+struct Launch {
+  uint64_t n_events, n_pixels;
+  const uint64_t* off;
+  const uint32_t* pix;
+  Geo geo;
+  Par par;
+  Workspace ws;
+  velo_output_t out;
+};
+
+// byte size of the workspace for E events and P pixels
+uint64_t workspace_bytes(uint64_t E, uint64_t P);
+// carve a workspace; returns false if too small
+bool carve_workspace(void* base, uint64_t bytes, uint64_t E, uint64_t P, Workspace* ws);
+
+// kernels
+__global__ void k_validate_offsets(Launch L);
+__global__ void k_cluster(Launch L);
+__global__ void k_track(Launch L);
+__global__ void k_scan(Launch L);
+__global__ void k_output(Launch L);
+
+uint32_t cluster_smem_bytes();
+uint32_t track_smem_bytes();
+
+}  // namespace velo

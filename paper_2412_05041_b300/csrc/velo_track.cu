@@ -1,0 +1,409 @@
+// Pattern recognition, fit and output kernels.
+//
+// The first stage's "simplified pattern recognition" (Sec. "HLT1 details and
+// results") is realised as search by triplet + forward extension, run per
+// event from the most downstream module to the most upstream one.  At step m
+// (m = M-2 .. 0):
+//   extension  every active track whose last hit sits on module l > m and
+//              that has missed at most max_skipped modules extrapolates the
+//              line through its last two hits to module m and takes the
+//              unused hit within the pseudo-angle window and the scatter cut
+//              with the smallest (d^2, id); several tracks on one hit -> the
+//              smallest (bits(d^2), track index) wins (64-bit atomicMin, so
+//              the outcome does not depend on thread order);
+//   seeding    (m >= 1) every unused hit h1 on m takes the (h0 on m+1 unused,
+//              h2 on m-1) pair inside the windows, slope and scatter cuts with
+//              the smallest (s, id0, id2); a seed claims h0 and h2 with
+//              (bits(s), id1) and survives if it holds both claims; survivors
+//              become tracks in the order of h1 (block scan).
+// Then every track is fitted (straight line + simplified Kalman), cut on
+// chi2/ndf, and ranked canonically by its smallest cluster id.
+//
+// One CTA of 256 threads per event; the event's hits stay in the global
+// workspace (sorted by module, pseudo-angle key, id; L1/L2 resident), the
+// per-step claims and used flags too.
+#include "velo_device.cuh"
+#include "velo_fit.cuh"
+#include "velo_internal.cuh"
+
+namespace velo {
+
+namespace {
+
+struct TrackSmem {
+  uint32_t mod_off[kModOffStride];
+  float z[VELO_MAX_MODULES];
+  uint32_t tmp[64];
+  unsigned long long tmp64[64];
+};
+
+__device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
+
+__device__ __forceinline__ uint32_t module_of_pos(const uint32_t* mod_off, uint32_t M, uint32_t pos) {
+  uint32_t lo = 0, hi = M;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (mod_off[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// hits of track t, ascending in z (upstream first), into x/y/z; returns n
+__device__ __forceinline__ uint32_t gather_track(const Workspace& W, uint64_t p0, uint64_t tb, uint32_t t,
+                                                 const uint32_t* mod_off, const float* mz, uint32_t M, float* xs,
+                                                 float* ys, float* zs, uint32_t* ids) {
+  const uint32_t n = W.trk_meta[tb + t] & 255u;
+  uint32_t p = W.trk_a[tb + t];
+  for (uint32_t j = 0; j < n; ++j) {
+    xs[j] = W.h_x[p0 + p];
+    ys[j] = W.h_y[p0 + p];
+    zs[j] = mz[module_of_pos(mod_off, M, p)];
+    if (ids) ids[j] = W.h_id[p0 + p];
+    p = W.sc[p0 + p];  // link to the next hit downstream
+  }
+  return n;
+}
+
+}  // namespace
+
+uint32_t track_smem_bytes() { return (uint32_t)sizeof(TrackSmem); }
+
+__global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
+  constexpr int NT = kTrackThreads;
+  __shared__ TrackSmem S;
+  const Workspace& W = L.ws;
+  const uint64_t e = blockIdx.x;
+  const uint32_t tid = threadIdx.x;
+  const Par& P = L.par;
+  const uint32_t M = L.geo.n_modules;
+
+  if (*(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK) {
+    if (tid == 0) {
+      W.ev_ntracks_all[e] = 0;
+      W.ev_ntracks[e] = 0;
+      W.ev_nhits[e] = 0;
+    }
+    return;
+  }
+  const uint64_t p0 = L.off[e];
+  const uint64_t tb = p0 / 3;
+  const uint32_t H = W.ev_nclusters[e];
+  const uint32_t track_cap = (uint32_t)((L.off[e + 1] - p0) / 3);
+  if (tid < kModOffStride) S.mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
+  if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
+
+  const float* hx = W.h_x + p0;
+  const float* hy = W.h_y + p0;
+  const float* hk = W.h_key + p0;
+  const uint32_t* hid = W.h_id + p0;
+  uint8_t* used = W.used + p0;
+  uint32_t* prev = W.sc + p0;
+  uint32_t* first_of = W.sd + p0;
+  uint32_t* seed_h0 = W.sa + p0;
+  uint32_t* seed_h2 = W.sb + p0;
+  unsigned long long* claim = W.acc + p0;
+  unsigned long long* seedkey = W.acc + L.n_pixels + p0;
+  uint32_t* meta = W.trk_meta + tb;
+  uint32_t* ta = W.trk_a + tb;
+  uint32_t* tbk = W.trk_b + tb;
+  uint32_t* pick = W.trk_pick + tb;
+  unsigned long long* pick_key = W.trk_pick_key + tb;
+
+  for (uint32_t i = tid; i < H; i += NT) {
+    used[i] = 0;
+    first_of[i] = kNone;
+  }
+  __syncthreads();
+
+  uint32_t n_tr = 0;
+  for (int m = (int)M - 2; m >= 0; --m) {
+    const uint32_t clo = S.mod_off[m > 0 ? m - 1 : 0], chi = S.mod_off[min((uint32_t)m + 2u, M)];
+    for (uint32_t pos = clo + tid; pos < chi; pos += NT) claim[pos] = ~0ull;
+    __syncthreads();
+
+    // ---- extension into module m (against the used flags of the step start)
+    const float zm = S.z[m];
+    const uint32_t mlo = S.mod_off[m], mhi = S.mod_off[m + 1];
+    for (uint32_t t = tid; t < n_tr; t += NT) {
+      const uint32_t mt = meta[t];
+      uint32_t pk = kNone;
+      if (mt & kTrkActive) {
+        const int la = (int)((mt >> 16) & 255u), lb = (int)(mt >> 24);
+        if (la - m - 1 > (int)P.max_skipped) {
+          meta[t] = mt & ~kTrkActive;
+        } else if (la > m) {
+          const uint32_t a = ta[t], b = tbk[t];
+          const float xa = hx[a], ya = hy[a], ka = hk[a], xb = hx[b], yb = hy[b];
+          const float za = S.z[la], zb = S.z[lb];
+          const float dzab = fs(za, zb);
+          const float tx = fd(fs(xa, xb), dzab), ty = fd(fs(ya, yb), dzab);
+          const float dzm = fs(zm, za);
+          const float xp = fa(xa, fm(tx, dzm)), yp = fa(ya, fm(ty, dzm));
+          const Ranges R = window_ranges(hk, mlo, mhi, ka, P.win_fwd);
+          unsigned long long best = ~0ull;
+          for (int part = 0; part < 2; ++part) {
+            const uint32_t s = part ? R.b0 : R.a0, en = part ? R.b1 : R.a1;
+            for (uint32_t pos = s; pos < en; ++pos) {
+              if (used[pos]) continue;
+              if (dmod4(hk[pos], ka) > P.win_fwd) continue;
+              const float dx = fs(xp, hx[pos]), dy = fs(yp, hy[pos]);
+              const float d2 = fa(fm(dx, dx), fm(dy, dy));
+              if (d2 > P.max_scatter_fwd) continue;
+              const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | hid[pos];
+              if (cand < best) {
+                best = cand;
+                pk = pos;
+              }
+            }
+          }
+          if (pk != kNone) {
+            const unsigned long long key = (best >> 32) << 32 | t;
+            pick_key[t] = key;
+            atomicMin(claim + pk, key);
+          }
+        }
+      }
+      pick[t] = pk;
+    }
+    __syncthreads();
+    for (uint32_t t = tid; t < n_tr; t += NT) {
+      const uint32_t pk = pick[t];
+      if (pk == kNone || claim[pk] != pick_key[t]) continue;
+      const uint32_t mt = meta[t];
+      const uint32_t n = mt & 255u, la = (mt >> 16) & 255u;
+      prev[pk] = ta[t];
+      tbk[t] = ta[t];
+      ta[t] = pk;
+      meta[t] = (n + 1u) | kTrkActive | ((uint32_t)m << 16) | (la << 24);
+      used[pk] = 1;
+    }
+    __syncthreads();
+    if (m == 0) break;
+
+    // ---- seeding with the middle hit on m
+    const uint32_t lo0 = S.mod_off[m + 1], hi0 = S.mod_off[m + 2];
+    const uint32_t lo2 = S.mod_off[m - 1], hi2 = mlo;
+    const float z0 = S.z[m + 1], z2 = S.z[m - 1];
+    const float dz02 = fs(z0, z2), dz12 = fs(zm, z2);
+    for (uint32_t p1 = mlo + tid; p1 < mhi; p1 += NT) {
+      unsigned long long skey = ~0ull;
+      if (!used[p1]) {
+        const float k1 = hk[p1], x1 = hx[p1], y1 = hy[p1];
+        const Ranges R0 = window_ranges(hk, lo0, hi0, k1, P.win_seed);
+        const Ranges R2 = window_ranges(hk, lo2, hi2, k1, P.win_seed);
+        unsigned long long best = ~0ull;
+        uint32_t b0 = kNone, b2 = kNone;
+        for (int part0 = 0; part0 < 2; ++part0) {
+          const uint32_t s0 = part0 ? R0.b0 : R0.a0, e0 = part0 ? R0.b1 : R0.a1;
+          for (uint32_t q0 = s0; q0 < e0; ++q0) {
+            if (used[q0]) continue;
+            if (dmod4(hk[q0], k1) > P.win_seed) continue;
+            const float x0 = hx[q0], y0 = hy[q0];
+            const unsigned long long lid0 = hid[q0] - lo0;
+            for (int part2 = 0; part2 < 2; ++part2) {
+              const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
+              for (uint32_t q2 = s2; q2 < e2; ++q2) {
+                if (dmod4(hk[q2], k1) > P.win_seed) continue;
+                const float x2 = hx[q2], y2 = hy[q2];
+                const float tx = fd(fs(x0, x2), dz02), ty = fd(fs(y0, y2), dz02);
+                if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
+                const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
+                const float dx = fs(xp, x1), dy = fs(yp, y1);
+                const float s = fa(fm(dx, dx), fm(dy, dy));
+                if (s > P.max_scatter_seed) continue;
+                const unsigned long long cand =
+                    (unsigned long long)fbits(s) << 32 | lid0 << 16 | (unsigned long long)(hid[q2] - lo2);
+                if (cand < best) {
+                  best = cand;
+                  b0 = q0;
+                  b2 = q2;
+                }
+              }
+            }
+          }
+        }
+        if (b0 != kNone) {
+          skey = (best >> 32) << 32 | hid[p1];
+          seed_h0[p1] = b0;
+          seed_h2[p1] = b2;
+          atomicMin(claim + b0, skey);
+          atomicMin(claim + b2, skey);
+        }
+      }
+      seedkey[p1] = skey;
+    }
+    __syncthreads();
+    for (uint32_t base = mlo; base < mhi; base += NT) {
+      const uint32_t p1 = base + tid;
+      bool surv = false;
+      uint32_t b0 = 0, b2 = 0;
+      if (p1 < mhi) {
+        const unsigned long long skey = seedkey[p1];
+        if (skey != ~0ull) {
+          b0 = seed_h0[p1];
+          b2 = seed_h2[p1];
+          surv = claim[b0] == skey && claim[b2] == skey;
+        }
+      }
+      uint32_t tot;
+      const uint32_t r = block_exclusive_scan<NT, uint32_t>(surv ? 1u : 0u, &tot, S.tmp);
+      // tracks hold >= 3 hits each and never share one, so n_tr <= H / 3 <= the
+      // event's track slice (n / 3); the test only guards the slice bound.
+      if (surv && n_tr + r < track_cap) {
+        const uint32_t t = n_tr + r;
+        ta[t] = b2;
+        tbk[t] = p1;
+        meta[t] = 3u | kTrkActive | ((uint32_t)(m - 1) << 16) | ((uint32_t)m << 24);
+        prev[b2] = p1;
+        prev[p1] = b0;
+        prev[b0] = kNone;
+        used[b0] = 1;
+        used[p1] = 1;
+        used[b2] = 1;
+      }
+      n_tr = min(n_tr + tot, track_cap);
+    }
+    __syncthreads();
+  }
+
+  // ---- fit, cut, canonical rank (by smallest cluster id) of every track
+  uint32_t* rank = W.trk_rank + tb;
+  uint32_t* hoff = W.trk_hoff + tb;
+  for (uint32_t t = tid; t < n_tr; t += NT) {
+    float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
+    const uint32_t n = gather_track(W, p0, tb, t, S.mod_off, S.z, M, xs, ys, zs, nullptr);
+    fit_track(n, xs, ys, zs, P.sigma, P.ms_theta, st);
+    rank[t] = kNone;
+    if (keep_track(n, st, P.ms_theta, P.chi2ndf_max, P.chi2ndf_max_3hit)) first_of[hid[ta[t]]] = t;
+  }
+  __syncthreads();
+  unsigned long long run = 0;
+  for (uint32_t base = 0; base < H; base += NT) {
+    const uint32_t id = base + tid;
+    uint32_t t = kNone;
+    unsigned long long v = 0;
+    if (id < H) {
+      t = first_of[id];
+      if (t != kNone) v = (1ull << 32) | (meta[t] & 255u);
+    }
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(v, &tot, S.tmp64) + run;
+    if (t != kNone) {
+      rank[t] = (uint32_t)(ex >> 32);
+      hoff[t] = (uint32_t)ex;
+    }
+    run += tot;
+  }
+  if (tid == 0) {
+    W.ev_ntracks_all[e] = n_tr;
+    W.ev_ntracks[e] = (uint32_t)(run >> 32);
+    W.ev_nhits[e] = (uint32_t)run;
+  }
+}
+
+// Compaction: clusters and kept tracks of event e into the caller's CSR
+// arrays (offsets from k_scan); the states are recomputed by the same fit.
+__global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
+  constexpr int NT = kOutputThreads;
+  __shared__ uint32_t mod_off[kModOffStride];
+  __shared__ float mz[VELO_MAX_MODULES];
+  const Workspace& W = L.ws;
+  const uint64_t e = blockIdx.x;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t M = L.geo.n_modules;
+  if (*(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK) return;
+  const uint64_t p0 = L.off[e];
+  const uint64_t tb = p0 / 3;
+  if (tid < kModOffStride) mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
+  if (tid < VELO_MAX_MODULES) mz[tid] = L.geo.z[tid];
+  __syncthreads();
+  const uint32_t H = W.ev_nclusters[e];
+  const uint64_t co = L.out.cluster_offsets[e];
+  for (uint32_t id = tid; id < H; id += NT) {
+    L.out.cluster_x[co + id] = W.cl_x[p0 + id];
+    L.out.cluster_y[co + id] = W.cl_y[p0 + id];
+    L.out.cluster_z[co + id] = mz[module_of_pos(mod_off, M, id)];
+  }
+  const uint32_t nt = W.ev_ntracks_all[e];
+  const uint64_t to = L.out.track_offsets[e];
+  const uint64_t hb = W.ev_hitbase[e];
+  for (uint32_t t = tid; t < nt; t += NT) {
+    const uint32_t r = W.trk_rank[tb + t];
+    if (r == kNone) continue;
+    float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
+    uint32_t ids[VELO_MAX_MODULES];
+    const uint32_t n = gather_track(W, p0, tb, t, mod_off, mz, M, xs, ys, zs, ids);
+    fit_track(n, xs, ys, zs, L.par.sigma, L.par.ms_theta, st);
+    const uint64_t dst = to + r;
+    const uint64_t h0 = hb + W.trk_hoff[tb + t];
+    L.out.track_hit_offsets[dst] = h0;
+    for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = ids[j];
+    float* o = L.out.track_states + dst * VELO_STATE_STRIDE;
+#pragma unroll
+    for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = st[k];
+  }
+}
+
+// One CTA: event offsets into the output CSR arrays and the batch totals.
+__global__ void __launch_bounds__(kScanThreads) k_scan(Launch L) {
+  constexpr int NT = kScanThreads;
+  __shared__ unsigned long long tmp[64];
+  const Workspace& W = L.ws;
+  const uint64_t E = L.n_events;
+  unsigned long long rc = 0, rt = 0, rh = 0, rf = 0;
+  for (uint64_t base = 0; base < E; base += NT) {
+    const uint64_t e = base + threadIdx.x;
+    unsigned long long c = 0, t = 0, h = 0, f = 0;
+    if (e < E) {
+      c = W.ev_nclusters[e];
+      t = W.ev_ntracks[e];
+      h = W.ev_nhits[e];
+      f = L.out.status[e] != VELO_EVT_OK;
+    }
+    unsigned long long tc, tt, th, tf;
+    const unsigned long long xc = block_exclusive_scan<NT, unsigned long long>(c, &tc, tmp);
+    const unsigned long long xt = block_exclusive_scan<NT, unsigned long long>(t, &tt, tmp);
+    const unsigned long long xh = block_exclusive_scan<NT, unsigned long long>(h, &th, tmp);
+    block_exclusive_scan<NT, unsigned long long>(f, &tf, tmp);
+    if (e < E) {
+      L.out.cluster_offsets[e] = rc + xc;
+      L.out.track_offsets[e] = rt + xt;
+      W.ev_hitbase[e] = rh + xh;
+    }
+    rc += tc;
+    rt += tt;
+    rh += th;
+    rf += tf;
+  }
+  if (threadIdx.x == 0) {
+    L.out.cluster_offsets[E] = rc;
+    L.out.track_offsets[E] = rt;
+    L.out.track_hit_offsets[rt] = rh;
+    L.out.totals[0] = rc;
+    L.out.totals[1] = rt;
+    L.out.totals[2] = rh;
+    L.out.totals[3] = rf;
+  }
+}
+
+// One CTA: the event offsets must start at 0, never decrease, end at
+// n_pixels and give no event 2^30 words or more; otherwise every event fails.
+__global__ void __launch_bounds__(kScanThreads) k_validate_offsets(Launch L) {
+  const uint64_t E = L.n_events;
+  int bad = 0;
+  if (threadIdx.x == 0) bad |= (L.off[0] != 0ull) | (L.off[E] != L.n_pixels);
+  for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) {
+    const uint64_t a = L.off[e], b = L.off[e + 1];
+    bad |= (b < a) | (b - a >= (1ull << 30));
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) *L.ws.flag = bad ? 1u : 0u;
+  if (bad) {
+    for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.out.status[e] = VELO_EVT_BADWORD;
+    if (L.out.pixel_cluster)
+      for (uint64_t i = threadIdx.x; i < L.n_pixels; i += blockDim.x) L.out.pixel_cluster[i] = kNone;
+  }
+}
+
+}  // namespace velo

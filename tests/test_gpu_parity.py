@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA library against the CPU oracle, element by element.
+
+Cluster ids and positions, per-word labels, track hit lists and event
+offsets must be identical; track states within 1e-5 relative (they are
+produced by the same binary32 operations in the same order, so in practice
+they are identical too).  Inputs are seeded synthetic events; no expected
+value comes from the CUDA path.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2412_05041_b300 as velo
+import velogen
+from _compare import assert_labels, assert_same, exact_state_fraction, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+PARAM_VALUES = dict(win_seed=0.04, win_fwd=0.04, max_slope=0.3, max_scatter_seed=0.01, max_scatter_fwd=0.02,
+                    max_skipped=1, sigma_meas=0.0159, ms_theta=5e-4, chi2ndf_max=10.0, chi2ndf_max_3hit=2.0)
+
+
+def params(ms_theta):
+    v = dict(PARAM_VALUES, ms_theta=ms_theta)
+    return velo.default_params(**v), oracle.Params(**v)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    velo.build()
+    assert torch.cuda.is_available()
+
+
+def gpu_run(offsets, pixels, geometry, p, labels=True):
+    off = torch.from_numpy(np.ascontiguousarray(offsets, np.uint64).view(np.int64)).cuda()
+    pix = torch.from_numpy(np.ascontiguousarray(pixels, np.uint32).view(np.int32)).cuda()
+    return velo.reconstruct(off, pix, geometry, p, pixel_labels=labels)
+
+
+def check_batch(b, ms_theta, labels=True):
+    vp, op = params(ms_theta)
+    g = gpu_run(b.offsets, b.pixels, b.geometry, vp, labels)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    assert_same(g, r)
+    if labels:
+        assert_labels(g["pixel_cluster"].cpu().numpy(), r["pixel_cluster"], b.offsets, b.offsets)
+    return g, r
+
+
+def test_config1_full():
+    b = velogen.generate(velogen.C1)
+    g, r = check_batch(b, 0.0)
+    assert len(r["track_states"]) > 3900
+    assert exact_state_fraction(g, r) == 1.0
+
+
+def test_config2_subset():
+    b = velogen.generate(velogen.C2, n_events=300)
+    g, r = check_batch(b, 5e-4)
+    assert exact_state_fraction(g, r) == 1.0
+
+
+def test_config2_full_size_sampled():
+    """The benchmark's configuration (10k pile-up-5.5 events, one launch sequence);
+    sampled events are re-generated alone and checked against the oracle one by one."""
+    cfg = velogen.C2
+    b = velogen.generate(cfg)
+    vp, op = params(cfg.ms_theta)
+    g = to_numpy(gpu_run(b.offsets, b.pixels, b.geometry, vp, labels=True))
+    rng = np.random.default_rng(123)
+    sample = sorted(rng.choice(cfg.n_events, size=40, replace=False).tolist()) + [0, cfg.n_events - 1]
+    for e in sample:
+        one = velogen.generate(cfg, n_events=1, first_event=e)
+        np.testing.assert_array_equal(one.pixels, b.event(e))
+        r = oracle.reconstruct(one.offsets, one.pixels, one.geometry, op)
+        assert_same(g, r, events=[e])
+        assert_labels(g["pixel_cluster"], r["pixel_cluster"], b.offsets, one.offsets, events=[e])
+    # properties at full size
+    assert (g["status"] == 0).all()
+    assert g["cluster_offsets"][-1] == len(g["cluster_x"]) and g["track_offsets"][-1] == len(g["track_states"])
+    assert g["track_hit_offsets"][-1] == len(g["track_hits"])
+    assert (np.diff(g["cluster_offsets"].astype(np.int64)) >= 0).all()
+    assert (np.diff(g["track_hit_offsets"].astype(np.int64)) >= 3).all()
+
+
+def _word(q, m, r, c):
+    return (q << 27) | (m << 22) | (r << 11) | c
+
+
+def edge_batch():
+    """Ragged events: empty, one pixel, duplicates, a bad word, a module over the
+    cluster capacity, an event larger than the shared-memory tier, normal events."""
+    evs = []
+    evs.append(np.zeros(0, np.uint32))
+    evs.append(np.array([_word(7, 3, 100, 200)], np.uint32))
+    evs.append(np.array([_word(3, 2, 10, 10), _word(4, 2, 10, 10), _word(5, 2, 11, 11)], np.uint32))
+    c2 = velogen.generate(velogen.C2, n_events=3, first_event=77)
+    evs.append(c2.event(0))
+    bad = c2.event(1).copy()
+    bad[len(bad) // 2] = _word(3, 30, 5, 5)  # module 30 does not exist
+    evs.append(bad)
+    idx = np.arange(65536)
+    evs.append(((5 << 27) | (3 << 22) | ((2 * (idx // 764)) << 11) | (2 * (idx % 764))).astype(np.uint32))
+    hi = velogen.Config(seed=9, n_events=1, hi_frac=1.0, hi_min_tracks=2500, hi_max_tracks=2500)
+    big = velogen.generate(hi)
+    assert len(big.pixels) > 23552  # exercises the global-memory tier
+    evs.append(big.pixels)
+    evs.append(c2.event(2))
+    evs.append(np.zeros(0, np.uint32))
+    offsets = np.zeros(len(evs) + 1, np.uint64)
+    offsets[1:] = np.cumsum([len(e) for e in evs])
+    return offsets, np.concatenate(evs).astype(np.uint32)
+
+
+def test_edge_cases():
+    offsets, pixels = edge_batch()
+    vp, op = params(5e-4)
+    geo = velogen.Geometry()
+    g = gpu_run(offsets, pixels, geo, vp)
+    r = oracle.reconstruct(offsets, pixels, geo, op)
+    assert list(r["status"]) == [0, 0, 0, 0, 1, 2, 0, 0, 0]
+    assert_same(g, r)
+    assert_labels(g["pixel_cluster"].cpu().numpy(), r["pixel_cluster"], offsets, offsets)
+    assert g["n_failed"] == 2
+
+
+def test_bad_offsets_fail_every_event():
+    b = velogen.generate(velogen.C2, n_events=4)
+    off = b.offsets.copy()
+    off[2], off[3] = off[3], off[2]  # not monotone
+    vp, _ = params(5e-4)
+    g = to_numpy(gpu_run(off, b.pixels, b.geometry, vp))
+    assert (g["status"] == velo.EVT_BADWORD).all()
+    assert g["n_failed"] == 4 and len(g["cluster_x"]) == 0 and len(g["track_states"]) == 0
+    assert (g["pixel_cluster"] == -1).all()
+
+
+def test_empty_batch():
+    vp, _ = params(5e-4)
+    g = to_numpy(gpu_run(np.zeros(1, np.uint64), np.zeros(0, np.uint32), velogen.Geometry(), vp))
+    assert len(g["status"]) == 0 and list(g["cluster_offsets"]) == [0] and list(g["track_offsets"]) == [0]
+
+
+def test_deterministic_and_split_batches_agree():
+    """Same input twice gives identical bytes; a batch split in two (as replicas
+    on several devices would run it) gives the same per-event results."""
+    b = velogen.generate(velogen.C2, n_events=200, first_event=5000)
+    vp, op = params(5e-4)
+    a1 = to_numpy(gpu_run(b.offsets, b.pixels, b.geometry, vp))
+    a2 = to_numpy(gpu_run(b.offsets, b.pixels, b.geometry, vp))
+    for k in a1:
+        np.testing.assert_array_equal(a1[k], a2[k])
+    half = 77
+    o1 = b.offsets[: half + 1]
+    o2 = b.offsets[half:] - b.offsets[half]
+    p1 = b.pixels[: int(b.offsets[half])]
+    p2 = b.pixels[int(b.offsets[half]):]
+    r1 = oracle.reconstruct(o1, p1, b.geometry, op)
+    r2 = oracle.reconstruct(o2, p2, b.geometry, op)
+    assert_same(a1, r1, events=range(half))
+    assert_same(a1, r2, events=range(half, b.n_events))
+
+
+def test_host_buffer_entry_point():
+    b = velogen.generate(velogen.C2, n_events=120, first_event=300)
+    vp, op = params(5e-4)
+    H = velo.HostReconstructor(b.geometry, vp, max_events=200, max_pixels=len(b.pixels) + 1000, pixel_labels=True)
+    off = torch.from_numpy(b.offsets.view(np.int64)).pin_memory()
+    pix = torch.from_numpy(b.pixels.view(np.int32)).pin_memory()
+    g = H.run(off, pix)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    assert_same(g, r)
+    assert_labels(g["pixel_cluster"].numpy(), r["pixel_cluster"], b.offsets, b.offsets)
+    # reuse of the same context with a different batch
+    b2 = velogen.generate(velogen.C1, n_events=30)
+    vp0, op0 = params(0.0)
+    H.params = vp0
+    g2 = H.run(torch.from_numpy(b2.offsets.view(np.int64)), torch.from_numpy(b2.pixels.view(np.int32)))
+    assert_same(g2, oracle.reconstruct(b2.offsets, b2.pixels, b2.geometry, op0))
+
+
+class _DevArray:
+    """Zero-copy torch view of a raw device pointer (CUDA array interface)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, n, typestr):
+    if n == 0:
+        return torch.empty(0)
+    return torch.as_tensor(_DevArray(ptr, n, typestr), device="cuda")
+
+
+def test_library_owned_result():
+    import ctypes
+    b = velogen.generate(velogen.C2, n_events=50, first_event=900)
+    vp, op = params(5e-4)
+    off = torch.from_numpy(b.offsets.view(np.int64)).cuda()
+    pix = torch.from_numpy(b.pixels.view(np.int32)).cuda()
+    L = velo.lib()
+    ev = velo.Events(b.n_events, len(b.pixels), off.data_ptr(), pix.data_ptr())
+    geo = velo.geometry_struct(b.geometry)
+    res = ctypes.c_void_p()
+    stream = torch.cuda.current_stream()
+    velo.check(L.velo_reconstruct(ctypes.byref(ev), ctypes.byref(geo.s), ctypes.byref(vp), ctypes.byref(res),
+                                  stream.cuda_stream))
+    view = velo.ResultView()
+    velo.check(L.velo_result_view(res, ctypes.byref(view)))
+    assert view.n_events == b.n_events and view.cap_clusters == len(b.pixels)
+    stream.synchronize()
+    o = view.out
+    tot = _view(o.totals, 4, "<i8").cpu().numpy()
+    E, nc, nt, nh = b.n_events, int(tot[0]), int(tot[1]), int(tot[2])
+    g = dict(status=_view(o.status, E, "<i4").cpu(), cluster_offsets=_view(o.cluster_offsets, E + 1, "<i8").cpu(),
+             cluster_x=_view(o.cluster_x, nc, "<f4").cpu(), cluster_y=_view(o.cluster_y, nc, "<f4").cpu(),
+             cluster_z=_view(o.cluster_z, nc, "<f4").cpu(), track_offsets=_view(o.track_offsets, E + 1, "<i8").cpu(),
+             track_hit_offsets=_view(o.track_hit_offsets, nt + 1, "<i8").cpu(),
+             track_hits=_view(o.track_hits, nh, "<i4").cpu(),
+             track_states=_view(o.track_states, nt * velo.STATE_STRIDE, "<f4").cpu().view(-1, velo.STATE_STRIDE))
+    L.velo_result_free(res)
+    torch.cuda.synchronize()
+    assert_same(g, oracle.reconstruct(b.offsets, b.pixels, b.geometry, op))
+
+
+def test_mc_quality_matches_oracle():
+    b = velogen.generate(velogen.C2, n_events=200, first_event=2000, truth=True)
+    vp, op = params(5e-4)
+    from oracle import mc
+    g = to_numpy(gpu_run(b.offsets, b.pixels, b.geometry, vp))
+    m = mc.evaluate_batch(b, g)
+    assert m["efficiency"] >= 0.99 and m["ghost_rate"] <= 0.05
