@@ -187,6 +187,28 @@ int velo_reconstruct_host(velo_context_t* ctx, const velo_events_t* host_events,
                           const velo_geometry_t* geometry, const velo_params_t* params,
                           const velo_output_t* host_out, void* stream);
 
+/* Allocation-free form, for callers that cannot allocate device memory
+ * while they reconstruct: a trigger node whose device memory is fixed at
+ * start-up, or code running inside another framework's callbacks, where a
+ * cudaMalloc could block or re-enter that framework's allocator.  The paper
+ * has no counterpart of this entry point.
+ * Same as velo_reconstruct_into, but the scratch is a file-scope __device__
+ * array of VELO_STATIC_SCRATCH_BYTES inside the library (every device that
+ * loads the library holds it until the process exits); the caller passes
+ * device inputs and outputs exactly as for velo_reconstruct_into.  A batch
+ * whose scratch need (velo_query_sizes' workspace_bytes) exceeds
+ * VELO_STATIC_SCRATCH_BYTES -- about 850k pixel words, some 65 pile-up-5.5
+ * events -- is rejected with VELO_ECAPACITY before any device work.  Calls
+ * no cudaMalloc, cudaFree or allocating routine.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, that device
+ * current): make that first call before any stream capture.  Every call
+ * shares the one array, which keeps the previous call's contents (nothing
+ * needs clearing: the kernels initialise what they read); calls that overlap
+ * on the GPU race on it. */
+#define VELO_STATIC_SCRATCH_BYTES (64ull << 20)
+int velo_reconstruct_static(const velo_events_t* events, const velo_geometry_t* geometry,
+                            const velo_params_t* params, const velo_output_t* out, void* stream);
+
 /* Name of a VELO_* return code. */
 const char* velo_strerror(int code);
 

@@ -18,6 +18,7 @@ from ._build import LIB_PATH, build  # noqa: F401
 
 STATE_STRIDE = 20
 MAX_MODULES = 32
+STATIC_SCRATCH_BYTES = 64 << 20  # scratch array behind velo_reconstruct_static
 EVT_OK, EVT_BADWORD, EVT_OVERFLOW = 0, 1, 2
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOMEM = range(6)
 STATE_FIELDS = ("x", "y", "tx", "ty", "z_first", "z_beam", "chi2_lsq", "chi2_kf", "kf_x", "kf_y", "kf_tx",
@@ -70,7 +71,7 @@ _lib = None
 EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "velo_reconstruct_into_marked",
            "velo_reconstruct",
            "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
-           "velo_reconstruct_host", "velo_strerror", "velo_version")
+           "velo_reconstruct_host", "velo_reconstruct_static", "velo_strerror", "velo_version")
 
 
 def lib():
@@ -95,6 +96,8 @@ def lib():
         L.velo_context_destroy.restype = None
         L.velo_reconstruct_host.argtypes = [_P, ctypes.POINTER(Events), ctypes.POINTER(Geometry),
                                             ctypes.POINTER(Params), ctypes.POINTER(Output), _P]
+        L.velo_reconstruct_static.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry),
+                                              ctypes.POINTER(Params), ctypes.POINTER(Output), _P]
         L.velo_strerror.restype = ctypes.c_char_p
         L.velo_strerror.argtypes = [ctypes.c_int]
         _lib = L
