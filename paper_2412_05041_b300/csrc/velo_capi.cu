@@ -43,6 +43,7 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   ws->h_y = c.take<float>(P);
   ws->h_key = c.take<float>(P);
   ws->h_id = c.take<uint32_t>(P);
+  ws->h_pos = c.take<uint32_t>(P);
   ws->used = c.take<uint8_t>(P);
   ws->trk_meta = c.take<uint32_t>(T);
   ws->trk_a = c.take<uint32_t>(T);

@@ -12,8 +12,8 @@
 //      the smaller with atomicMin, so every root ends as the smallest sorted
 //      position of its component, i.e. its smallest (module, row, col);
 //   4. cluster id = exclusive scan of root flags (canonical, order-free);
-//   5. integer charge sums per cluster with 64-bit atomics (exact, so the
-//      order of the additions does not matter) and the binary32 centroid;
+//   5. integer charge sums per cluster with atomics (exact, so the order of
+//      the additions does not matter) and the binary32 centroid;
 //   6. pseudo-angle key and a stable block radix sort of the hits by
 //      (module, key, id): 4 passes over the key bits + 1 over the module.
 // Events larger than the shared-memory tier run the same code on their
@@ -150,17 +150,42 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
   for (uint32_t i = tid; i < n; i += NT) {
     const uint32_t k = A[i] & kKeyMask;
     const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
-    // duplicates of k and the left neighbour (k - 1) are the words just before i
-    for (int64_t j = (int64_t)i - 1; j >= 0; --j) {
+    // Every earlier neighbour has a key in [lo_all, k]: duplicates (k), the
+    // left neighbour (k - 1) and, if r > 0, the previous row's columns c-1 ..
+    // c+1 ([lo_k, hi_k]).  Those keys sit just before i in the sorted array,
+    // so a backward scan that stops below lo_all sees all of them; the words
+    // of a sparse event are a few rows apart, so it usually stops within a
+    // few steps.  Past 16 steps the full search below takes over (unions are
+    // idempotent, so visiting a neighbour twice is harmless).
+    const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
+    const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
+    const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
+    bool done = false;
+    int64_t j = (int64_t)i - 1;
+    for (int steps = 0; steps < 16; ++steps, --j) {
+      if (j < 0) {
+        done = true;
+        break;
+      }
       const uint32_t kj = A[j] & kKeyMask;
-      if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)j);
-      else break;
+      if (kj < lo_all) {
+        done = true;
+        break;
+      }
+      if (kj == k || (c > 0u && kj == k - 1u) || (r > 0u && kj >= lo_k && kj <= hi_k))
+        ok &= uf_unite(B, i, (uint32_t)j);
     }
-    if (r > 0u) {  // previous row, columns c-1 .. c+1 of the same module
-      const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u);
-      const uint32_t hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
-      uint32_t j = lower_bound_by(0u, i, [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
-      for (; j < i && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j);
+    if (!done) {
+      // duplicates of k and the left neighbour (k - 1) are the words just before i
+      for (int64_t jj = (int64_t)i - 1; jj >= 0; --jj) {
+        const uint32_t kj = A[jj] & kKeyMask;
+        if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)jj);
+        else break;
+      }
+      if (r > 0u) {  // previous row, columns c-1 .. c+1 of the same module
+        uint32_t jj = lower_bound_by(0u, i, [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+        for (; jj < i && (A[jj] & kKeyMask) <= hi_k; ++jj) ok &= uf_unite(B, i, jj);
+      }
     }
   }
   if (!ok) S.flag = 2u;
@@ -213,37 +238,64 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
     }
   }
 
-  // 5. integer charge sums per cluster, then the binary32 centroid
+  // 5. integer charge sums per cluster, then the binary32 centroid.  With at
+  // most kClusterSmemPixels words, sum q(2c+1) <= 15 * 4095 * 23552 < 2^32, so
+  // 32-bit sums (and a 32-bit division) are exact; larger events use 64 bits.
+  const bool narrow = n <= kClusterSmemPixels;
   unsigned long long* acc = W.acc + 3 * p0;
-  for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc[i] = 0ull;
+  uint32_t* acc32 = reinterpret_cast<uint32_t*>(W.acc) + 3 * p0;
+  if (narrow) {
+    for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc32[i] = 0u;
+  } else {
+    for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc[i] = 0ull;
+  }
   __syncthreads();
   for (uint32_t i = tid; i < n; i += NT) {
     const uint32_t w = A[i];
     const uint32_t q = (w >> 27) & 15u, c = w & 2047u, r = (w >> 11) & 2047u;
-    unsigned long long* a3 = acc + 3ull * B[i];
-    atomicAdd(a3 + 0, (unsigned long long)q);
-    atomicAdd(a3 + 1, (unsigned long long)(q * (2u * c + 1u)));
-    atomicAdd(a3 + 2, (unsigned long long)(q * (2u * r + 1u)));
+    if (narrow) {
+      uint32_t* a3 = acc32 + 3u * B[i];
+      atomicAdd(a3 + 0, q);
+      atomicAdd(a3 + 1, q * (2u * c + 1u));
+      atomicAdd(a3 + 2, q * (2u * r + 1u));
+    } else {
+      unsigned long long* a3 = acc + 3ull * B[i];
+      atomicAdd(a3 + 0, (unsigned long long)q);
+      atomicAdd(a3 + 1, (unsigned long long)(q * (2u * c + 1u)));
+      atomicAdd(a3 + 2, (unsigned long long)(q * (2u * r + 1u)));
+    }
   }
   __syncthreads();
 
   // the pixel arrays are dead from here on: the hit sort reuses the region
-  const bool hit_smem = 2u * n_clusters <= kClusterSmemPixels;
+  // (keys, values, their ping-pong copies and the cluster x, y: 6 words per cluster)
+  const bool hit_smem = 6u * n_clusters <= 2u * kClusterSmemPixels;
   uint32_t* KA = hit_smem ? region : W.sa + p0;
   uint32_t* KB = hit_smem ? region + n_clusters : W.sb + p0;
-  uint32_t* VA = hit_smem ? region + kClusterSmemPixels : W.sc + p0;
-  uint32_t* VB = hit_smem ? region + kClusterSmemPixels + n_clusters : W.sd + p0;
+  uint32_t* VA = hit_smem ? region + 2 * n_clusters : W.sc + p0;
+  uint32_t* VB = hit_smem ? region + 3 * n_clusters : W.sd + p0;
+  float* cx = hit_smem ? reinterpret_cast<float*>(region + 4 * n_clusters) : W.cl_x + p0;
+  float* cy = hit_smem ? reinterpret_cast<float*>(region + 5 * n_clusters) : W.cl_y + p0;
   const Geo& g = L.geo;
   for (uint32_t id = tid; id < n_clusters; id += NT) {
-    const unsigned long long sq = acc[3 * id], snx = acc[3 * id + 1], sny = acc[3 * id + 2];
-    const unsigned long long D = 2ull * sq;
-    const float Df = __ull2float_rn(D);
-    const float u = __fadd_rn(__ull2float_rn(snx / D), __fdiv_rn(__ull2float_rn(snx % D), Df));
-    const float v = __fadd_rn(__ull2float_rn(sny / D), __fdiv_rn(__ull2float_rn(sny % D), Df));
+    float u, v;
+    if (narrow) {
+      const uint32_t sq = acc32[3 * id], snx = acc32[3 * id + 1], sny = acc32[3 * id + 2];
+      const uint32_t D = 2u * sq;
+      const float Df = __uint2float_rn(D);
+      u = __fadd_rn(__uint2float_rn(snx / D), __fdiv_rn(__uint2float_rn(snx % D), Df));
+      v = __fadd_rn(__uint2float_rn(sny / D), __fdiv_rn(__uint2float_rn(sny % D), Df));
+    } else {
+      const unsigned long long sq = acc[3 * id], snx = acc[3 * id + 1], sny = acc[3 * id + 2];
+      const unsigned long long D = 2ull * sq;
+      const float Df = __ull2float_rn(D);
+      u = __fadd_rn(__ull2float_rn(snx / D), __fdiv_rn(__ull2float_rn(snx % D), Df));
+      v = __fadd_rn(__ull2float_rn(sny / D), __fdiv_rn(__ull2float_rn(sny % D), Df));
+    }
     const float x = __fadd_rn(g.x0, __fmul_rn(g.pitch, u));
     const float y = __fadd_rn(g.y0, __fmul_rn(g.pitch, v));
-    W.cl_x[p0 + id] = x;
-    W.cl_y[p0 + id] = y;
+    cx[id] = x;
+    cy[id] = y;
     KA[id] = __float_as_uint(pseudo_angle(x, y));
     VA[id] = id;
   }
@@ -262,10 +314,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
                        [mo, M](uint32_t, uint32_t id) { return module_of(mo, M, id); }, S.cnt, S.tmp);
   for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
     const uint32_t id = VB[pos];
-    W.h_x[p0 + pos] = W.cl_x[p0 + id];
-    W.h_y[p0 + pos] = W.cl_y[p0 + id];
+    W.h_x[p0 + pos] = cx[id];
+    W.h_y[p0 + pos] = cy[id];
     W.h_key[p0 + pos] = __uint_as_float(KB[pos]);
     W.h_id[p0 + pos] = id;
+    W.h_pos[p0 + id] = pos;
   }
   if (tid <= M) W.ev_modoff[e * kModOffStride + tid] = S.mod_off[tid];
   if (tid == 0) {

@@ -50,19 +50,25 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* tmp) {
 // ---------------------------------------------------------------- radix sort
 // One stable LSD pass of a block-wide radix sort with 8-bit digits.
 // The n elements are cut into one contiguous chunk per warp; every warp
-// histograms its chunk into its own column of cnt (256 x NW counters in
-// shared memory), one exclusive scan in (digit, warp) order gives each
+// histograms its chunk into its own row of cnt (NW rows of 257 counters in
+// shared memory: the pad word makes both the per-warp access, lanes on
+// different digits, and the scan's access, one digit across warps, hit 32
+// different banks), one exclusive scan in (digit, warp) order gives each
 // (digit, warp) its first output slot, and every warp then scatters its chunk
 // in index order (rank among equal digits from __match_any_sync), so equal
 // digits keep their relative order.  a/b (and va/vb) may live in shared or
-// global memory.
+// global memory.  cnt: radix_counters(NT) words.
+constexpr uint32_t kRadixRow = 257;  // 256 digit counters + 1 pad word per warp
+__host__ __device__ constexpr uint32_t radix_counters(int nt) { return kRadixRow * (uint32_t)(nt / 32); }
+
 template <int NT, bool HAS_VAL, class K, class DigitF>
 __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, uint32_t n, DigitF digit,
                            uint32_t* cnt, uint32_t* tmp) {
   constexpr int NW = NT / 32;
   constexpr uint32_t NB = 256;
   const uint32_t lane = lane_id(), w = warp_id();
-  for (uint32_t i = threadIdx.x; i < NB * NW; i += NT) cnt[i] = 0;
+  uint32_t* row = cnt + w * kRadixRow;  // this warp's counters
+  for (uint32_t i = threadIdx.x; i < kRadixRow * NW; i += NT) cnt[i] = 0;
   __syncthreads();
   const uint32_t chunk = (n + NW - 1) / NW;
   const uint32_t s = min(n, w * chunk), e = min(n, s + chunk);
@@ -72,23 +78,26 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
     uint32_t d = NB;
     if (valid) d = digit(a[i], HAS_VAL ? va[i] : 0u);
     const uint32_t peers = __match_any_sync(kFull, d);
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) cnt[d * NW + w] += __popc(peers);
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) row[d] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // exclusive scan of the 256*NW counters; thread t owns 8 consecutive entries
+  // exclusive scan of the 256*NW counters in (digit, warp) order; thread t
+  // owns the 8 consecutive entries j = 8t .. 8t+7 (digit j / NW, warp j % NW)
   constexpr int PER = NB * NW / NT;
   uint32_t loc[PER], sum = 0;
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
-    loc[j] = cnt[threadIdx.x * PER + j];
+    const uint32_t jj = threadIdx.x * PER + j;
+    loc[j] = cnt[(jj % NW) * kRadixRow + jj / NW];
     sum += loc[j];
   }
   uint32_t tot;
   uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &tot, tmp);
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
-    cnt[threadIdx.x * PER + j] = run;
+    const uint32_t jj = threadIdx.x * PER + j;
+    cnt[(jj % NW) * kRadixRow + jj / NW] = run;
     run += loc[j];
   }
   __syncthreads();
@@ -105,12 +114,12 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
     }
     const uint32_t peers = __match_any_sync(kFull, d);
     if (valid) {
-      const uint32_t pos = cnt[d * NW + w] + __popc(peers & lt);
+      const uint32_t pos = row[d] + __popc(peers & lt);
       b[pos] = k;
       if (HAS_VAL) vb[pos] = v;
     }
     __syncwarp();
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) cnt[d * NW + w] += __popc(peers);
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) row[d] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();

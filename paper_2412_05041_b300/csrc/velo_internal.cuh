@@ -17,7 +17,7 @@ constexpr int kScanThreads = 1024;
 // parents in shared memory when it has at most this many words; larger
 // events run the same code on their slice of the global workspace.
 constexpr uint32_t kClusterSmemPixels = 23552;
-constexpr uint32_t kRadixCounters = 256 * (kClusterThreads / 32);
+constexpr uint32_t kRadixCounters = 257 * (kClusterThreads / 32);  // radix_counters(kClusterThreads)
 constexpr uint32_t kModOffStride = 33;  // per-event module offsets, n_modules + 1 <= 33
 
 // Per-track metadata word: n_hits (8 bits) | active (1 bit) << 8 |
@@ -41,12 +41,13 @@ struct Workspace {
   uint32_t* sc;              // pixel-indexed u32: hit-sort values / prev link
   uint32_t* sd;              // pixel-indexed u32: hit-sort values / first_of
   unsigned long long* acc;   // pixel-indexed x3: centroid sums / claims + seed keys
-  float* cl_x;               // pixel-indexed: cluster x in id order
+  float* cl_x;               // pixel-indexed: cluster x in id order (events whose hits overflow shared memory)
   float* cl_y;               // pixel-indexed: cluster y in id order
   float* h_x;                // pixel-indexed: hits sorted by (module, key, id)
   float* h_y;
   float* h_key;
   uint32_t* h_id;
+  uint32_t* h_pos;           // pixel-indexed: sorted position of each cluster id
   uint8_t* used;             // pixel-indexed
   uint32_t* trk_meta;        // track-indexed
   uint32_t* trk_a;           // last hit position

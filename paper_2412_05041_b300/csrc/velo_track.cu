@@ -13,9 +13,10 @@
 //              the outcome does not depend on thread order);
 //   seeding    (m >= 1) every unused hit h1 on m takes the (h0 on m+1 unused,
 //              h2 on m-1) pair inside the windows, slope and scatter cuts with
-//              the smallest (s, id0, id2); a seed claims h0 and h2 with
-//              (bits(s), id1) and survives if it holds both claims; survivors
-//              become tracks in the order of h1 (block scan).
+//              the smallest (s, id0, id2) -- the pairs of all h1 are spread
+//              evenly over the block as (h1, h0) work items; a seed claims h0
+//              and h2 with (bits(s), id1) and survives if it holds both claims;
+//              survivors become tracks in the order of h1 (block scan).
 // Then every track is fitted (straight line + simplified Kalman), cut on
 // chi2/ndf, and ranked canonically by its smallest cluster id.
 //
@@ -30,11 +31,17 @@ namespace velo {
 
 namespace {
 
+constexpr uint32_t kSeedChunk = 512;  // middle hits per seeding chunk (a multiple of the block size)
+
 struct TrackSmem {
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   uint32_t tmp[64];
   unsigned long long tmp64[64];
+  uint4 r0[kSeedChunk];                // h0 window (two index ranges) of each middle hit
+  uint4 r2[kSeedChunk];                // h2 window
+  uint32_t ioff[kSeedChunk];           // first work item of each middle hit
+  unsigned long long best[kSeedChunk]; // smallest (bits(s), id0, id2) key of each middle hit
 };
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
@@ -181,59 +188,97 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
     __syncthreads();
     if (m == 0) break;
 
-    // ---- seeding with the middle hit on m
+    // ---- seeding with the middle hit on m.  The (h0, h2) pairs of all middle
+    // hits are spread evenly over the block: one work item per (h1, h0
+    // candidate), each looping over h1's h2 window, in chunks of kSeedChunk
+    // middle hits; per h1 the smallest pair key wins (shared 64-bit atomicMin).
     const uint32_t lo0 = S.mod_off[m + 1], hi0 = S.mod_off[m + 2];
     const uint32_t lo2 = S.mod_off[m - 1], hi2 = mlo;
     const float z0 = S.z[m + 1], z2 = S.z[m - 1];
     const float dz02 = fs(z0, z2), dz12 = fs(zm, z2);
-    for (uint32_t p1 = mlo + tid; p1 < mhi; p1 += NT) {
-      unsigned long long skey = ~0ull;
-      if (!used[p1]) {
-        const float k1 = hk[p1], x1 = hx[p1], y1 = hy[p1];
-        const Ranges R0 = window_ranges(hk, lo0, hi0, k1, P.win_seed);
-        const Ranges R2 = window_ranges(hk, lo2, hi2, k1, P.win_seed);
-        unsigned long long best = ~0ull;
-        uint32_t b0 = kNone, b2 = kNone;
-        for (int part0 = 0; part0 < 2; ++part0) {
-          const uint32_t s0 = part0 ? R0.b0 : R0.a0, e0 = part0 ? R0.b1 : R0.a1;
-          for (uint32_t q0 = s0; q0 < e0; ++q0) {
-            if (used[q0]) continue;
-            if (dmod4(hk[q0], k1) > P.win_seed) continue;
-            const float x0 = hx[q0], y0 = hy[q0];
-            const unsigned long long lid0 = hid[q0] - lo0;
-            for (int part2 = 0; part2 < 2; ++part2) {
-              const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
-              for (uint32_t q2 = s2; q2 < e2; ++q2) {
-                if (dmod4(hk[q2], k1) > P.win_seed) continue;
-                const float x2 = hx[q2], y2 = hy[q2];
-                const float tx = fd(fs(x0, x2), dz02), ty = fd(fs(y0, y2), dz02);
-                if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
-                const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
-                const float dx = fs(xp, x1), dy = fs(yp, y1);
-                const float s = fa(fm(dx, dx), fm(dy, dy));
-                if (s > P.max_scatter_seed) continue;
-                const unsigned long long cand =
-                    (unsigned long long)fbits(s) << 32 | lid0 << 16 | (unsigned long long)(hid[q2] - lo2);
-                if (cand < best) {
-                  best = cand;
-                  b0 = q0;
-                  b2 = q2;
-                }
-              }
-            }
+    for (uint32_t cbase = mlo; cbase < mhi; cbase += kSeedChunk) {
+      const uint32_t cn = min(kSeedChunk, mhi - cbase);
+      constexpr int PER = kSeedChunk / NT;
+      uint32_t cnt[PER], sum = 0;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {  // thread tid owns middle hits PER*tid .. PER*tid+PER-1
+        const uint32_t i = tid * PER + k;
+        uint32_t c = 0;
+        if (i < cn) {
+          const uint32_t p1 = cbase + i;
+          S.best[i] = ~0ull;
+          if (!used[p1]) {
+            const float k1 = hk[p1];
+            const Ranges R0 = window_ranges(hk, lo0, hi0, k1, P.win_seed);
+            S.r0[i] = make_uint4(R0.a0, R0.a1, R0.b0, R0.b1);
+            const Ranges R2 = window_ranges(hk, lo2, hi2, k1, P.win_seed);
+            S.r2[i] = make_uint4(R2.a0, R2.a1, R2.b0, R2.b1);
+            c = (R0.a1 - R0.a0) + (R0.b1 - R0.b0);
           }
         }
-        if (b0 != kNone) {
-          skey = (best >> 32) << 32 | hid[p1];
+        cnt[k] = c;
+        sum += c;
+      }
+      uint32_t n_items;
+      uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &n_items, S.tmp);
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const uint32_t i = tid * PER + k;
+        if (i < cn) S.ioff[i] = run;
+        run += cnt[k];
+      }
+      __syncthreads();
+      for (uint32_t j = tid; j < n_items; j += NT) {
+        // middle hit of item j: the last i with ioff[i] <= j (empty entries
+        // share the offset of the next one, so that i owns item j)
+        const uint32_t i = lower_bound_by(0u, cn, [&](uint32_t x) { return S.ioff[x] <= j; }) - 1u;
+        const uint32_t p1 = cbase + i;
+        const uint4 R0 = S.r0[i];
+        const uint32_t kk = j - S.ioff[i], na = R0.y - R0.x;
+        const uint32_t q0 = kk < na ? R0.x + kk : R0.z + (kk - na);
+        if (used[q0]) continue;
+        const float k1 = hk[p1];
+        if (dmod4(hk[q0], k1) > P.win_seed) continue;
+        const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
+        const unsigned long long lid0 = hid[q0] - lo0;
+        const uint4 R2 = S.r2[i];
+        unsigned long long best = ~0ull;
+        for (int part2 = 0; part2 < 2; ++part2) {
+          const uint32_t s2 = part2 ? R2.z : R2.x, e2 = part2 ? R2.w : R2.y;
+          for (uint32_t q2 = s2; q2 < e2; ++q2) {
+            if (dmod4(hk[q2], k1) > P.win_seed) continue;
+            const float x2 = hx[q2], y2 = hy[q2];
+            const float tx = fd(fs(x0, x2), dz02), ty = fd(fs(y0, y2), dz02);
+            if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
+            const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
+            const float dx = fs(xp, x1), dy = fs(yp, y1);
+            const float sc = fa(fm(dx, dx), fm(dy, dy));
+            if (sc > P.max_scatter_seed) continue;
+            const unsigned long long cand =
+                (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(hid[q2] - lo2);
+            best = cand < best ? cand : best;
+          }
+        }
+        if (best != ~0ull) atomicMin(&S.best[i], best);
+      }
+      __syncthreads();
+      for (uint32_t i = tid; i < cn; i += NT) {  // seeds claim their h0 and h2
+        const uint32_t p1 = cbase + i;
+        const unsigned long long key = S.best[i];
+        unsigned long long skey = ~0ull;
+        if (key != ~0ull) {
+          const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
+          const uint32_t b2 = W.h_pos[p0 + lo2 + (uint32_t)(key & 0xFFFFu)];
+          skey = (key >> 32) << 32 | hid[p1];
           seed_h0[p1] = b0;
           seed_h2[p1] = b2;
           atomicMin(claim + b0, skey);
           atomicMin(claim + b2, skey);
         }
+        seedkey[p1] = skey;
       }
-      seedkey[p1] = skey;
+      __syncthreads();
     }
-    __syncthreads();
     for (uint32_t base = mlo; base < mhi; base += NT) {
       const uint32_t p1 = base + tid;
       bool surv = false;
@@ -320,10 +365,11 @@ __global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
   __syncthreads();
   const uint32_t H = W.ev_nclusters[e];
   const uint64_t co = L.out.cluster_offsets[e];
-  for (uint32_t id = tid; id < H; id += NT) {
-    L.out.cluster_x[co + id] = W.cl_x[p0 + id];
-    L.out.cluster_y[co + id] = W.cl_y[p0 + id];
-    L.out.cluster_z[co + id] = mz[module_of_pos(mod_off, M, id)];
+  for (uint32_t pos = tid; pos < H; pos += NT) {  // sorted hits -> clusters in id order
+    const uint32_t id = W.h_id[p0 + pos];
+    L.out.cluster_x[co + id] = W.h_x[p0 + pos];
+    L.out.cluster_y[co + id] = W.h_y[p0 + pos];
+    L.out.cluster_z[co + id] = mz[module_of_pos(mod_off, M, pos)];
   }
   const uint32_t nt = W.ev_ntracks_all[e];
   const uint64_t to = L.out.track_offsets[e];
