@@ -27,6 +27,11 @@ _HDR = os.path.join(_HERE, "velo_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 STATE_STRIDE = 20
+N_FEATURES = 12
+MLP_HIDDEN = 32
+MLP_FLOATS = 1529
+FEATURE_NAMES = ("n_hits", "chi2ndf", "tx", "ty", "z_first", "z_last", "n_skipped", "mean_rx", "rms_rx", "mean_ry",
+                 "rms_ry", "max_abs_r")
 MAX_MODULE_CLUSTERS = 65535
 EVT_OK, EVT_BADWORD, EVT_OVERFLOW = 0, 1, 2
 STATE_FIELDS = ("x", "y", "tx", "ty", "z_first", "z_beam", "chi2_lsq", "chi2_kf", "kf_x", "kf_y", "kf_tx",
@@ -45,6 +50,8 @@ class Params:
     ms_theta: float = 5e-4
     chi2ndf_max: float = 10.0
     chi2ndf_max_3hit: float = 2.0
+    use_mlp: int = 0
+    mlp_logit_min: float = 0.0
 
 
 class _Geo(ctypes.Structure):
@@ -57,7 +64,8 @@ class _Par(ctypes.Structure):
     _fields_ = [("win_seed", ctypes.c_float), ("win_fwd", ctypes.c_float), ("max_slope", ctypes.c_float),
                 ("max_scatter_seed", ctypes.c_float), ("max_scatter_fwd", ctypes.c_float),
                 ("max_skipped", ctypes.c_uint32), ("sigma_meas", ctypes.c_float), ("ms_theta", ctypes.c_float),
-                ("chi2ndf_max", ctypes.c_float), ("chi2ndf_max_3hit", ctypes.c_float)]
+                ("chi2ndf_max", ctypes.c_float), ("chi2ndf_max_3hit", ctypes.c_float),
+                ("use_mlp", ctypes.c_uint32), ("mlp_logit_min", ctypes.c_float), ("mlp", ctypes.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -92,7 +100,10 @@ def _load():
         lib.vo_reconstruct.restype = ctypes.c_void_p
         lib.vo_reconstruct.argtypes = [ctypes.c_uint64, _P, _P, ctypes.POINTER(_Geo), ctypes.POINTER(_Par), ctypes.c_int]
         lib.vo_batch_sizes.argtypes = [ctypes.c_void_p, _P, _P, _P]
-        lib.vo_batch_copy.argtypes = [ctypes.c_void_p] + [_P] * 10
+        lib.vo_batch_copy.argtypes = [ctypes.c_void_p] + [_P] * 11
+        lib.vo_features.argtypes = [ctypes.c_uint32, _P, _P, _P, _P, _P, ctypes.c_float, _P]
+        lib.vo_mlp_logit.restype = ctypes.c_float
+        lib.vo_mlp_logit.argtypes = [_P, _P]
         lib.vo_batch_free.argtypes = [ctypes.c_void_p]
         _lib = lib
     return _lib
@@ -110,8 +121,13 @@ class _GeoHolder:
                       float(geometry.y0))
 
 
-def _par(params: Params) -> _Par:
-    return _Par(**asdict(params))
+def _par(params: Params, mlp=None) -> _Par:
+    p = _Par(**asdict(params))
+    if params.use_mlp:
+        if mlp is None or mlp.dtype != np.float32 or mlp.size != MLP_FLOATS or not mlp.flags.c_contiguous:
+            raise ValueError("use_mlp needs a contiguous float32 model blob of MLP_FLOATS values")
+        p.mlp = mlp.ctypes.data
+    return p
 
 
 def pseudo_angle(x: float, y: float) -> float:
@@ -134,7 +150,7 @@ def cluster_event(words: np.ndarray, geometry):
     return dict(status=st, x=cx[:k], y=cy[:k], z=cz[:k], module=cm[:k], pixel_cluster=pc[:n])
 
 
-def track_event(module: np.ndarray, x: np.ndarray, y: np.ndarray, geometry, params: Params = Params()):
+def track_event(module: np.ndarray, x: np.ndarray, y: np.ndarray, geometry, params: Params = Params(), mlp=None):
     """Tracks of one event from hits given in cluster-id order -> (list of hit-id arrays, states[T,20])."""
     lib = _load()
     module = np.ascontiguousarray(module, np.uint32)
@@ -147,7 +163,7 @@ def track_event(module: np.ndarray, x: np.ndarray, y: np.ndarray, geometry, para
     st = np.zeros((cap, STATE_STRIDE), np.float32)
     nt = ctypes.c_uint64()
     g = _GeoHolder(geometry)
-    p = _par(params)
+    p = _par(params, mlp)
     rc = lib.vo_track_event(n, _ptr(module), _ptr(x), _ptr(y), ctypes.byref(g.s), ctypes.byref(p), cap,
                             ctypes.byref(nt), _ptr(offs), _ptr(ids), _ptr(st))
     if rc != 0:
@@ -169,14 +185,16 @@ def fit(x, y, z, sigma: float, ms_theta: float, dtype=np.float32) -> np.ndarray:
     return out
 
 
-def reconstruct(offsets: np.ndarray, pixels: np.ndarray, geometry, params: Params = Params(), n_threads: int = 0):
-    """Whole batch on the host cores -> dict of numpy arrays in the library's output layout."""
+def reconstruct(offsets: np.ndarray, pixels: np.ndarray, geometry, params: Params = Params(), n_threads: int = 0,
+                mlp=None):
+    """Whole batch on the host cores -> dict of numpy arrays in the library's output layout.
+    mlp: float32 model blob (MLP_FLOATS) when params.use_mlp."""
     lib = _load()
     off = np.ascontiguousarray(offsets, np.uint64)
     pix = np.ascontiguousarray(pixels, np.uint32)
     ne = len(off) - 1
     g = _GeoHolder(geometry)
-    p = _par(params)
+    p = _par(params, mlp)
     h = lib.vo_reconstruct(ne, _ptr(off), _ptr(pix), ctypes.byref(g.s), ctypes.byref(p), n_threads)
     try:
         nc, nt, nh = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
@@ -192,10 +210,33 @@ def reconstruct(offsets: np.ndarray, pixels: np.ndarray, geometry, params: Param
             track_hit_offsets=np.zeros(nt.value + 1, np.uint64),
             track_hits=np.zeros(nh.value, np.uint32),
             track_states=np.zeros((nt.value, STATE_STRIDE), np.float32),
+            track_features=np.zeros((nt.value, N_FEATURES), np.float32),
         )
         lib.vo_batch_copy(h, *(_ptr(out[k]) for k in ("status", "cluster_offsets", "cluster_x", "cluster_y",
                                                        "cluster_z", "pixel_cluster", "track_offsets",
-                                                       "track_hit_offsets", "track_hits", "track_states")))
+                                                       "track_hit_offsets", "track_hits", "track_states",
+                                                       "track_features")))
     finally:
         lib.vo_batch_free(h)
     return out
+
+
+def features(x, y, z, module, state, chi2ndf) -> np.ndarray:
+    """The 12 candidate features of one track (hits ascending in z)."""
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    z = np.ascontiguousarray(z, np.float32)
+    module = np.ascontiguousarray(module, np.uint32)
+    state = np.ascontiguousarray(state, np.float32)
+    out = np.zeros(N_FEATURES, np.float32)
+    lib.vo_features(len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(module), _ptr(state), float(chi2ndf), _ptr(out))
+    return out
+
+
+def mlp_logit(mlp: np.ndarray, f: np.ndarray) -> float:
+    """The network's logit for one feature vector (bfloat16 emulation, see velo_oracle.h)."""
+    lib = _load()
+    mlp = np.ascontiguousarray(mlp, np.float32)
+    f = np.ascontiguousarray(f, np.float32)
+    return float(lib.vo_mlp_logit(_ptr(mlp), _ptr(f)))

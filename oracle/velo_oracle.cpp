@@ -14,7 +14,7 @@
 //   6. step order and used flags
 //   7. termination and the 3-hit rule
 //   8. straight-line fit and simplified Kalman filter
-//   9. chi2/ndf cut
+//   9. chi2/ndf cut (optionally with the learned ghost rejection)
 //  10. canonical output order
 // Arithmetic: binary32, one rounding per operation in the written order,
 // no FMA contraction (compiled with -ffp-contract=off), no transcendental
@@ -278,6 +278,75 @@ void fit_track(uint32_t n, const R* x, const R* y, const R* z, R sigma, R theta,
   st[19] = 0;
 }
 
+// ---------------------------------------------------------------- learned ghost rejection
+// Candidate features (binary32, fixed order).  Residuals are the straight-line
+// fit's: r_i = (x_i - x) - tx dz_i, as in its chi2.
+void features(uint32_t n, const float* x, const float* y, const float* z, const uint32_t* module, const float* st,
+              float chi2ndf, float* f) {
+  f[0] = (float)n;
+  f[1] = chi2ndf;
+  f[2] = st[2];
+  f[3] = st[3];
+  f[4] = z[0];
+  f[5] = z[n - 1];
+  f[6] = (float)((int)(module[n - 1] - module[0] + 1) - (int)n);
+  float sx = 0.0f, sxx = 0.0f, sy = 0.0f, syy = 0.0f, mx = 0.0f;
+  for (uint32_t i = 0; i < n; ++i) {
+    float dz = z[i] - z[0];
+    float rx = (x[i] - st[0]) - st[2] * dz;
+    float ry = (y[i] - st[1]) - st[3] * dz;
+    sx = sx + rx;
+    sxx = sxx + rx * rx;
+    sy = sy + ry;
+    syy = syy + ry * ry;
+    mx = std::fmax(mx, std::fmax(std::fabs(rx), std::fabs(ry)));
+  }
+  float fn = (float)n;
+  f[7] = sx / fn;
+  f[8] = std::sqrt(sxx / fn);  // IEEE square root: correctly rounded
+  f[9] = sy / fn;
+  f[10] = std::sqrt(syy / fn);
+  f[11] = mx;
+}
+
+float bf16(float v) {  // round to nearest even, to bfloat16 (finite inputs)
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  std::memcpy(&v, &u, 4);
+  return v;
+}
+
+float mlp_logit(const float* w, const float* f) {
+  const int H = VO_MLP_HIDDEN, F = VO_N_FEATURES;
+  const float* mean = w;
+  const float* istd = w + F;
+  const float* W1 = w + 2 * F;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float b3 = W3[H];
+  float xin[VO_N_FEATURES], h1[VO_MLP_HIDDEN], h2[VO_MLP_HIDDEN];
+  for (int k = 0; k < F; ++k) xin[k] = bf16((f[k] - mean[k]) * istd[k]);
+  for (int j = 0; j < H; ++j) {
+    float a = 0.0f;
+    for (int k = 0; k < F; ++k) a = a + bf16(W1[j * F + k]) * xin[k];
+    a = a + b1[j];
+    h1[j] = bf16(a > 0.0f ? a : 0.0f);
+  }
+  for (int j = 0; j < H; ++j) {
+    float a = 0.0f;
+    for (int k = 0; k < H; ++k) a = a + bf16(W2[j * H + k]) * h1[k];
+    a = a + b2[j];
+    h2[j] = a > 0.0f ? a : 0.0f;
+  }
+  float z = 0.0f;
+  for (int j = 0; j < H; ++j) z = z + W3[j] * h2[j];
+  return z + b3;
+}
+
 // ---------------------------------------------------------------- steps 4-7, 9, 10
 struct Hits {
   uint32_t n = 0;
@@ -294,6 +363,7 @@ struct Track {
 struct TrackOut {
   std::vector<std::vector<uint32_t>> hits;  // ascending ids, canonical order
   std::vector<float> states;
+  std::vector<float> features;
 };
 
 void track_event(const Hits& H, const vo_geometry_t* g, const vo_params_t* p, TrackOut& out) {
@@ -387,31 +457,43 @@ void track_event(const Hits& H, const vo_geometry_t* g, const vo_params_t* p, Tr
     }
   }
   // 7-9. every track terminates; fit; 3-hit rule; chi2/ndf cut
-  struct Kept { std::vector<uint32_t> hits; std::vector<float> st; };
+  struct Kept { std::vector<uint32_t> hits; std::vector<float> st, f; };
   std::vector<Kept> kept;
   for (const Track& T : tracks) {
     uint32_t n = (uint32_t)T.hits.size();
     std::vector<uint32_t> asc(T.hits.rbegin(), T.hits.rend());  // ascending z == ascending id
     std::vector<float> xs(n), ys(n), zs(n);
-    for (uint32_t i = 0; i < n; ++i) { xs[i] = H.x[asc[i]]; ys[i] = H.y[asc[i]]; zs[i] = H.z[asc[i]]; }
-    std::vector<float> st(VO_STATE_STRIDE);
+    std::vector<uint32_t> ms(n);
+    for (uint32_t i = 0; i < n; ++i) {
+      xs[i] = H.x[asc[i]]; ys[i] = H.y[asc[i]]; zs[i] = H.z[asc[i]]; ms[i] = H.module[asc[i]];
+    }
+    std::vector<float> st(VO_STATE_STRIDE), f(VO_N_FEATURES);
     fit_track<float>(n, xs.data(), ys.data(), zs.data(), p->sigma_meas, p->ms_theta, st.data());
     float chi2 = p->ms_theta == 0.0f ? st[6] : st[7];
     float ndf = (float)(2 * n - 4);
     float r = chi2 / ndf;
-    // hits are never shared between tracks (every claim is exclusive), so
-    // "no hit in another candidate" always holds for a 3-hit track.
-    if (n == 3 && !(r <= p->chi2ndf_max_3hit)) continue;
+    features(n, xs.data(), ys.data(), zs.data(), ms.data(), st.data(), r, f.data());
+    if (p->use_mlp) {
+      // learned rejection: the network's logit replaces the 3-hit rule
+      st[19] = mlp_logit(p->mlp, f.data());
+      if (!(st[19] >= p->mlp_logit_min)) continue;
+    } else {
+      // hits are never shared between tracks (every claim is exclusive), so
+      // "no hit in another candidate" always holds for a 3-hit track.
+      if (n == 3 && !(r <= p->chi2ndf_max_3hit)) continue;
+    }
     if (!(r <= p->chi2ndf_max)) continue;
-    kept.push_back({asc, st});
+    kept.push_back({asc, st, f});
   }
   // 10. canonical order: lexicographic by the ascending hit-id list
   std::sort(kept.begin(), kept.end(), [](const Kept& a, const Kept& b) { return a.hits < b.hits; });
   out.hits.clear();
   out.states.clear();
+  out.features.clear();
   for (auto& k : kept) {
     out.hits.push_back(k.hits);
     out.states.insert(out.states.end(), k.st.begin(), k.st.end());
+    out.features.insert(out.features.end(), k.f.begin(), k.f.end());
   }
 }
 
@@ -537,7 +619,7 @@ void vo_batch_sizes(void* h, uint64_t* n_clusters, uint64_t* n_tracks, uint64_t*
 
 void vo_batch_copy(void* h, int32_t* status, uint64_t* cluster_offsets, float* cx, float* cy, float* cz,
                    uint32_t* pixel_cluster, uint64_t* track_offsets, uint64_t* track_hit_offsets,
-                   uint32_t* track_hits, float* track_states) {
+                   uint32_t* track_hits, float* track_states, float* track_features) {
   Batch* B = (Batch*)h;
   uint64_t c = 0, t = 0, k = 0, p = 0;
   for (size_t e = 0; e < B->ev.size(); ++e) {
@@ -562,6 +644,8 @@ void vo_batch_copy(void* h, int32_t* status, uint64_t* cluster_offsets, float* c
         ++k;
       }
       if (track_states) std::memcpy(track_states + t * VO_STATE_STRIDE, R.tr.states.data() + i * VO_STATE_STRIDE, VO_STATE_STRIDE * 4);
+      if (track_features)
+        std::memcpy(track_features + t * VO_N_FEATURES, R.tr.features.data() + i * VO_N_FEATURES, VO_N_FEATURES * 4);
     }
   }
   if (cluster_offsets) cluster_offsets[B->ev.size()] = c;
@@ -570,5 +654,12 @@ void vo_batch_copy(void* h, int32_t* status, uint64_t* cluster_offsets, float* c
 }
 
 void vo_batch_free(void* h) { delete (Batch*)h; }
+
+void vo_features(uint32_t n, const float* x, const float* y, const float* z, const uint32_t* module,
+                 const float* state, float chi2ndf, float* f) {
+  features(n, x, y, z, module, state, chi2ndf, f);
+}
+
+float vo_mlp_logit(const float* mlp, const float* f) { return mlp_logit(mlp, f); }
 
 }  // extern "C"

@@ -29,6 +29,11 @@ extern "C" {
 #endif
 
 #define VO_STATE_STRIDE 20
+#define VO_N_FEATURES 12
+/* Ghost-rejection network blob (float32): mean[12], inv_std[12], W1[32][12],
+ * b1[32], W2[32][32], b2[32], W3[32], b3 -- 1529 floats. */
+#define VO_MLP_HIDDEN 32
+#define VO_MLP_FLOATS 1529
 #define VO_MAX_MODULE_CLUSTERS 65535u
 #define VO_MAX_MODULES 32u
 
@@ -53,6 +58,9 @@ typedef struct vo_params {
   float ms_theta;          /* rad; 0 -> the cut uses the straight-line chi2 */
   float chi2ndf_max;
   float chi2ndf_max_3hit;
+  uint32_t use_mlp;        /* 1: the network's logit >= mlp_logit_min replaces the 3-hit rule */
+  float mlp_logit_min;
+  const float* mlp;        /* host, VO_MLP_FLOATS, used when use_mlp */
 } vo_params_t;
 
 /* Pseudo-angle ("diamond angle") in [0, 4), monotone in phi. */
@@ -81,6 +89,18 @@ void vo_fit_f32(uint32_t n, const float* x, const float* y, const float* z, floa
 void vo_fit_f64(uint32_t n, const double* x, const double* y, const double* z, double sigma,
                 double ms_theta, double* state);
 
+/* The 12 candidate features of one track (hits ascending in z, their module
+ * indices, the fitted state from vo_fit_f32, the cut's chi2/ndf): n_hits,
+ * chi2/ndf, tx, ty, z_first, z_last, modules skipped, mean and RMS of the x
+ * residuals, mean and RMS of the y residuals, largest |residual|. */
+void vo_features(uint32_t n, const float* x, const float* y, const float* z, const uint32_t* module,
+                 const float* state, float chi2ndf, float* features);
+/* The network's logit for one feature vector: inputs, weights and the first
+ * hidden layer rounded to bfloat16 (round to nearest even), sums in float32
+ * in index order, bias added after the sum, ReLU; the second hidden layer stays
+ * float32; logit = sum_j W3[j] h2[j] (j ascending) + b3. */
+float vo_mlp_logit(const float* mlp, const float* features);
+
 /* Whole batch (the oracle form of velo_reconstruct): events in CSR form on
  * the host.  Returns an opaque handle; read it with vo_batch_sizes and
  * vo_batch_copy, release with vo_batch_free.  n_threads <= 0: all cores. */
@@ -89,10 +109,11 @@ void* vo_reconstruct(uint64_t n_events, const uint64_t* event_offsets, const uin
 void vo_batch_sizes(void* h, uint64_t* n_clusters, uint64_t* n_tracks, uint64_t* n_track_hits);
 /* Any pointer may be NULL.  status[E], cluster_offsets[E+1], cluster_x/y/z[C],
  * pixel_cluster[P], track_offsets[E+1], track_hit_offsets[T+1] (global),
- * track_hits[H] (event-local cluster ids), track_states[T*20]. */
+ * track_hits[H] (event-local cluster ids), track_states[T*20] (state[19] = the
+ * network's logit when use_mlp, else 0), track_features[T*12]. */
 void vo_batch_copy(void* h, int32_t* status, uint64_t* cluster_offsets, float* cx, float* cy, float* cz,
                    uint32_t* pixel_cluster, uint64_t* track_offsets, uint64_t* track_hit_offsets,
-                   uint32_t* track_hits, float* track_states);
+                   uint32_t* track_hits, float* track_states, float* track_features);
 void vo_batch_free(void* h);
 
 #ifdef __cplusplus
