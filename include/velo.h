@@ -37,6 +37,10 @@ extern "C" {
 #endif
 
 #define VELO_STATE_STRIDE 20          /* floats per track state, layout below */
+#define VELO_N_FEATURES 12            /* candidate features (learned ghost rejection) */
+#define VELO_MLP_HIDDEN 32
+#define VELO_MLP_WEIGHTS 1505         /* trainable: W1[32][12] b1[32] W2[32][32] b2[32] W3[32] b3 */
+#define VELO_MLP_FLOATS 1529          /* model blob: mean[12] inv_std[12] + the weights */
 #define VELO_MAX_MODULES 32u          /* geometry limit (5-bit module field) */
 #define VELO_MAX_MODULE_CLUSTERS 65535u /* per module per event; beyond it the event fails */
 
@@ -81,6 +85,15 @@ typedef struct velo_params {
                               > 0 -> the Kalman chi2 with slope noise ms_theta^2 per module */
   float chi2ndf_max;       /* keep a track if chi2/ndf <= chi2ndf_max */
   float chi2ndf_max_3hit;  /* ... and a 3-hit track only if also <= chi2ndf_max_3hit */
+  /* Learned ghost rejection (the paper has no learned component; this is the
+   * project's extension): when use_mlp is 1 a 12 -> 32 -> 32 -> 1 network
+   * scores every candidate on bfloat16 tensor cores (float32 accumulation) and
+   * "logit >= mlp_logit_min" replaces the 3-hit rule; chi2ndf_max still applies.
+   * mlp: device pointer to a VELO_MLP_FLOATS float32 blob
+   * (mean[12], inv_std[12], W1[32][12], b1[32], W2[32][32], b2[32], W3[32], b3). */
+  uint32_t use_mlp;
+  float mlp_logit_min;
+  const float* mlp;
 } velo_params_t;
 
 /* A batch of events in CSR form.  Pixel word layout (any order inside an event):
@@ -105,7 +118,11 @@ typedef struct velo_events {
  *   8 kf_x, 9 kf_y, 10 kf_tx, 11 kf_ty   Kalman state at the first hit
  *  12 C_xx, 13 C_xtx, 14 C_txtx          Kalman covariance, x projection
  *  15 C_yy, 16 C_yty, 17 C_tyty          Kalman covariance, y projection
- *  18 ndf = 2 n_hits - 4, 19 reserved (0) */
+ *  18 ndf = 2 n_hits - 4, 19 the network's logit when use_mlp, else 0
+ * Candidate features (VELO_N_FEATURES floats per track, optional output):
+ *   n_hits, chi2/ndf (of the cut), tx, ty, z_first, z_last, modules skipped,
+ *   mean and RMS of the x residuals, mean and RMS of the y residuals,
+ *   largest |residual| (residuals of the straight-line fit, mm). */
 typedef struct velo_output {
   int32_t* status;              /* [n_events] VELO_EVT_* */
   uint64_t* cluster_offsets;    /* [n_events + 1] into cluster_x/y/z */
@@ -119,6 +136,7 @@ typedef struct velo_output {
   uint32_t* track_hits;         /* [cap_track_hits] event-local cluster ids */
   float* track_states;          /* [cap_tracks * VELO_STATE_STRIDE] */
   uint64_t* totals;             /* [4]: n_clusters, n_tracks, n_track_hits, n_failed_events */
+  float* track_features;        /* optional (NULL = not written) [cap_tracks * VELO_N_FEATURES] */
 } velo_output_t;
 
 /* Capacities that always suffice for a batch of n_events events holding
@@ -208,6 +226,26 @@ int velo_reconstruct_host(velo_context_t* ctx, const velo_events_t* host_events,
 #define VELO_STATIC_SCRATCH_BYTES (64ull << 20)
 int velo_reconstruct_static(const velo_events_t* events, const velo_geometry_t* geometry,
                             const velo_params_t* params, const velo_output_t* out, void* stream);
+
+/* ---- Training and evaluation of the ghost-rejection network (device pointers,
+ * asynchronous on `stream`).  Inputs x are normalised features
+ * ((f - mean) * inv_std) [n * 12], labels y in {0, 1} [n]; weights w are the
+ * VELO_MLP_WEIGHTS trainable floats in blob order.  Gradients are summed over
+ * the batch in a fixed order (deterministic). */
+
+/* Logits of n feature vectors (raw features [n * 12], the model blob):
+ * mode 0 = the reconstruction's bfloat16 tensor-core path, mode 1 = float32
+ * on CUDA cores (no bfloat16 rounding). */
+int velo_mlp_infer(const float* features, uint64_t n, const float* mlp, float* logits, int mode, void* stream);
+/* Device scratch velo_mlp_loss_grad needs for a batch of n samples. */
+int velo_mlp_workspace_size(uint64_t n, uint64_t* bytes);
+/* Mean binary cross-entropy of sigmoid(logit) (float32, written to *loss) and
+ * its gradient with respect to w (grad[VELO_MLP_WEIGHTS]). */
+int velo_mlp_loss_grad(const float* x, const float* y, uint64_t n, const float* w, float* grad, float* loss,
+                       void* workspace, uint64_t workspace_bytes, void* stream);
+/* One Adam step on w with moments m, v (all [n_weights]); step counts from 1. */
+int velo_mlp_adam_step(float* w, const float* grad, float* m, float* v, uint32_t n_weights, float lr, float beta1,
+                       float beta2, float eps, uint32_t step, void* stream);
 
 /* Name of a VELO_* return code. */
 const char* velo_strerror(int code);

@@ -19,6 +19,11 @@ from ._build import LIB_PATH, build  # noqa: F401
 STATE_STRIDE = 20
 MAX_MODULES = 32
 STATIC_SCRATCH_BYTES = 64 << 20  # scratch array behind velo_reconstruct_static
+N_FEATURES = 12
+MLP_WEIGHTS = 1505
+MLP_FLOATS = 1529
+FEATURE_NAMES = ("n_hits", "chi2ndf", "tx", "ty", "z_first", "z_last", "n_skipped", "mean_rx", "rms_rx", "mean_ry",
+                 "rms_ry", "max_abs_r")
 EVT_OK, EVT_BADWORD, EVT_OVERFLOW = 0, 1, 2
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOMEM = range(6)
 STATE_FIELDS = ("x", "y", "tx", "ty", "z_first", "z_beam", "chi2_lsq", "chi2_kf", "kf_x", "kf_y", "kf_tx",
@@ -37,7 +42,8 @@ class Params(ctypes.Structure):
     _fields_ = [("win_seed", ctypes.c_float), ("win_fwd", ctypes.c_float), ("max_slope", ctypes.c_float),
                 ("max_scatter_seed", ctypes.c_float), ("max_scatter_fwd", ctypes.c_float),
                 ("max_skipped", ctypes.c_uint32), ("sigma_meas", ctypes.c_float), ("ms_theta", ctypes.c_float),
-                ("chi2ndf_max", ctypes.c_float), ("chi2ndf_max_3hit", ctypes.c_float)]
+                ("chi2ndf_max", ctypes.c_float), ("chi2ndf_max_3hit", ctypes.c_float),
+                ("use_mlp", ctypes.c_uint32), ("mlp_logit_min", ctypes.c_float), ("mlp", _P)]
 
 
 class Events(ctypes.Structure):
@@ -48,7 +54,7 @@ class Events(ctypes.Structure):
 class Output(ctypes.Structure):
     _fields_ = [("status", _P), ("cluster_offsets", _P), ("cluster_x", _P), ("cluster_y", _P), ("cluster_z", _P),
                 ("pixel_cluster", _P), ("track_offsets", _P), ("track_hit_offsets", _P), ("track_hits", _P),
-                ("track_states", _P), ("totals", _P)]
+                ("track_states", _P), ("totals", _P), ("track_features", _P)]
 
 
 class Sizes(ctypes.Structure):
@@ -71,7 +77,8 @@ _lib = None
 EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "velo_reconstruct_into_marked",
            "velo_reconstruct",
            "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
-           "velo_reconstruct_host", "velo_reconstruct_static", "velo_strerror", "velo_version")
+           "velo_reconstruct_host", "velo_reconstruct_static", "velo_mlp_infer", "velo_mlp_workspace_size",
+           "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_strerror", "velo_version")
 
 
 def lib():
@@ -98,6 +105,11 @@ def lib():
                                             ctypes.POINTER(Params), ctypes.POINTER(Output), _P]
         L.velo_reconstruct_static.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry),
                                               ctypes.POINTER(Params), ctypes.POINTER(Output), _P]
+        L.velo_mlp_infer.argtypes = [_P, ctypes.c_uint64, _P, _P, ctypes.c_int, _P]
+        L.velo_mlp_workspace_size.argtypes = [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+        L.velo_mlp_loss_grad.argtypes = [_P, _P, ctypes.c_uint64, _P, _P, _P, _P, ctypes.c_uint64, _P]
+        L.velo_mlp_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_float, ctypes.c_uint32, _P]
         L.velo_strerror.restype = ctypes.c_char_p
         L.velo_strerror.argtypes = [ctypes.c_int]
         _lib = L

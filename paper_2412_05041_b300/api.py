@@ -9,7 +9,8 @@ import ctypes
 
 import torch
 
-from . import (Events, Output, STATE_STRIDE, VeloError, check, default_params, geometry_struct, lib, query_sizes)
+from . import (N_FEATURES, Events, Output, STATE_STRIDE, VeloError, check, default_params, geometry_struct, lib,
+               query_sizes)
 
 
 def _stream_handle(stream) -> int:
@@ -27,7 +28,7 @@ class Reconstructor:
     events and ``max_pixels`` pixel words, reused across calls."""
 
     def __init__(self, geometry, params=None, max_events: int = 1, max_pixels: int = 1, device="cuda",
-                 pixel_labels: bool = False):
+                 pixel_labels: bool = False, features: bool = False):
         self.geo = geometry_struct(geometry)
         self.params = params if params is not None else default_params()
         self.max_events, self.max_pixels = int(max_events), int(max_pixels)
@@ -47,11 +48,13 @@ class Reconstructor:
         self.track_hits = torch.empty(max(s.cap_track_hits, 1), dtype=torch.int32, device=dev)
         self.track_states = torch.empty((max(s.cap_tracks, 1), STATE_STRIDE), dtype=torch.float32, device=dev)
         self.totals = torch.empty(4, dtype=torch.int64, device=dev)
+        self.track_features = (torch.empty((max(s.cap_tracks, 1), N_FEATURES), dtype=torch.float32, device=dev)
+                               if features else None)
         self.workspace = torch.empty(s.workspace_bytes, dtype=torch.uint8, device=dev)
         self._out = Output(_ptr(self.status), _ptr(self.cluster_offsets), _ptr(self.cluster_x), _ptr(self.cluster_y),
                            _ptr(self.cluster_z), _ptr(self.pixel_cluster), _ptr(self.track_offsets),
                            _ptr(self.track_hit_offsets), _ptr(self.track_hits), _ptr(self.track_states),
-                           _ptr(self.totals))
+                           _ptr(self.totals), _ptr(self.track_features))
         self.n_events = 0
 
     def run(self, offsets: torch.Tensor, pixels: torch.Tensor, stream=None, marks=None) -> None:
@@ -93,14 +96,16 @@ class Reconstructor:
                  track_states=self.track_states[:nt], n_failed=nf)
         if self.pixel_cluster is not None:
             r["pixel_cluster"] = self.pixel_cluster[:self.n_pixels]
+        if self.track_features is not None:
+            r["track_features"] = self.track_features[:nt]
         return r
 
 
 def reconstruct(offsets: torch.Tensor, pixels: torch.Tensor, geometry, params=None, pixel_labels: bool = False,
-                stream=None) -> dict:
+                stream=None, features: bool = False) -> dict:
     """One-shot: allocate, run, wait, return trimmed device tensors."""
     R = Reconstructor(geometry, params, max(offsets.numel() - 1, 0), pixels.numel(), device=pixels.device,
-                      pixel_labels=pixel_labels)
+                      pixel_labels=pixel_labels, features=features)
     R.run(offsets, pixels, stream)
     return R.result(stream)
 
@@ -132,7 +137,7 @@ class HostReconstructor:
         self._out = Output(_ptr(self.status), _ptr(self.cluster_offsets), _ptr(self.cluster_x), _ptr(self.cluster_y),
                            _ptr(self.cluster_z), _ptr(self.pixel_cluster), _ptr(self.track_offsets),
                            _ptr(self.track_hit_offsets), _ptr(self.track_hits), _ptr(self.track_states),
-                           _ptr(self.totals))
+                           _ptr(self.totals), None)
 
     def __del__(self):
         if getattr(self, "ctx", None) and self.ctx.value:

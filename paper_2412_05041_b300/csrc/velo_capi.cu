@@ -52,6 +52,7 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   ws->trk_pick_key = c.take<unsigned long long>(T);
   ws->trk_rank = c.take<uint32_t>(T);
   ws->trk_hoff = c.take<uint32_t>(T);
+  ws->trk_logit = c.take<float>(T);
 }
 
 bool geometry_ok(const velo_geometry_t* g) {
@@ -79,6 +80,7 @@ bool params_ok(const velo_params_t* p) {
   if (!fin(p->sigma_meas) || !(p->sigma_meas > 0.0f)) return false;
   if (!fin(p->ms_theta) || p->ms_theta < 0.0f) return false;
   if (!fin(p->chi2ndf_max) || !fin(p->chi2ndf_max_3hit)) return false;
+  if (p->use_mlp > 1 || (p->use_mlp && (!p->mlp || !fin(p->mlp_logit_min)))) return false;
   return true;
 }
 
@@ -112,6 +114,9 @@ Par make_par(const velo_params_t* p) {
   P.ms_theta = p->ms_theta;
   P.chi2ndf_max = p->chi2ndf_max;
   P.chi2ndf_max_3hit = p->chi2ndf_max_3hit;
+  P.use_mlp = p->use_mlp;
+  P.mlp_logit_min = p->mlp_logit_min;
+  P.mlp = p->mlp;
   return P;
 }
 
@@ -180,6 +185,9 @@ int velo_params_default(velo_params_t* p) {
   p->ms_theta = 5e-4f;
   p->chi2ndf_max = 10.0f;
   p->chi2ndf_max_3hit = 2.0f;
+  p->use_mlp = 0;
+  p->mlp_logit_min = 0.0f;
+  p->mlp = nullptr;
   return VELO_OK;
 }
 
@@ -330,6 +338,7 @@ int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t
   alloc((void**)&c->d_out.track_hits, 4 * sz.cap_track_hits);
   alloc((void**)&c->d_out.track_states, 4ull * VELO_STATE_STRIDE * (sz.cap_tracks ? sz.cap_tracks : 1));
   alloc((void**)&c->d_out.totals, 8 * 4);
+  alloc((void**)&c->d_out.track_features, 4ull * VELO_N_FEATURES * (sz.cap_tracks ? sz.cap_tracks : 1));
   alloc(&c->workspace, sz.workspace_bytes);
   if (!ok) {
     velo_context_destroy(c);
@@ -345,7 +354,7 @@ void velo_context_destroy(velo_context_t* c) {
   void* ptrs[] = {c->d_off,           c->d_pix,           c->d_out.status,           c->d_out.cluster_offsets,
                   c->d_out.cluster_x, c->d_out.cluster_y, c->d_out.cluster_z,        c->d_out.pixel_cluster,
                   c->d_out.track_offsets, c->d_out.track_hit_offsets, c->d_out.track_hits, c->d_out.track_states,
-                  c->d_out.totals,    c->workspace};
+                  c->d_out.totals,    c->d_out.track_features, c->workspace};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -366,6 +375,7 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
   velo_events_t dev = {E, P, c->d_off, c->d_pix};
   velo_output_t dout = c->d_out;
   if (!ho->pixel_cluster) dout.pixel_cluster = nullptr;
+  if (!ho->track_features) dout.track_features = nullptr;
   int rc = velo_reconstruct_into(&dev, geometry, params, &dout, c->workspace, c->sizes.workspace_bytes, stream);
   if (rc != VELO_OK) return rc;
   bool ok = true;
@@ -385,6 +395,7 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
   d2h(ho->track_hit_offsets, dout.track_hit_offsets, 8 * (nt + 1));
   d2h(ho->track_hits, dout.track_hits, 4 * nh);
   d2h(ho->track_states, dout.track_states, 4ull * VELO_STATE_STRIDE * nt);
+  if (ho->track_features) d2h(ho->track_features, dout.track_features, 4ull * VELO_N_FEATURES * nt);
   if (!ok || cudaStreamSynchronize(s) != cudaSuccess) return VELO_ECUDA;
   return VELO_OK;
 }

@@ -56,6 +56,7 @@ struct Workspace {
   unsigned long long* trk_pick_key;
   uint32_t* trk_rank;        // canonical rank among kept tracks, kNone if dropped
   uint32_t* trk_hoff;        // first hit of the track among the event's kept hits
+  float* trk_logit;          // the network's logit (learned rejection)
 };
 
 struct Geo {
@@ -68,6 +69,9 @@ struct Par {
   float win_seed, win_fwd, max_slope, max_scatter_seed, max_scatter_fwd;
   uint32_t max_skipped;
   float sigma, ms_theta, chi2ndf_max, chi2ndf_max_3hit;
+  uint32_t use_mlp;
+  float mlp_logit_min;
+  const float* mlp;
 };
 
 struct Launch {

@@ -18,7 +18,8 @@
 //              and h2 with (bits(s), id1) and survives if it holds both claims;
 //              survivors become tracks in the order of h1 (block scan).
 // Then every track is fitted (straight line + simplified Kalman), cut on
-// chi2/ndf, and ranked canonically by its smallest cluster id.
+// chi2/ndf (or, in the learned form, scored by the ghost-rejection network on
+// tensor cores), and ranked canonically by its smallest cluster id.
 //
 // One CTA of 256 threads per event; the event's hits stay in the global
 // workspace (sorted by module, pseudo-angle key, id; L1/L2 resident), the
@@ -26,6 +27,7 @@
 #include "velo_device.cuh"
 #include "velo_fit.cuh"
 #include "velo_internal.cuh"
+#include "velo_mlp.cuh"
 
 namespace velo {
 
@@ -33,15 +35,23 @@ namespace {
 
 constexpr uint32_t kSeedChunk = 512;  // middle hits per seeding chunk (a multiple of the block size)
 
+struct SeedArrays {
+  uint4 r0[kSeedChunk];                // h0 window (two index ranges) of each middle hit
+  uint4 r2[kSeedChunk];                // h2 window
+  uint32_t ioff[kSeedChunk];           // first work item of each middle hit
+  unsigned long long best[kSeedChunk]; // smallest (bits(s), id0, id2) key of each middle hit
+};
+
 struct TrackSmem {
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   uint32_t tmp[64];
   unsigned long long tmp64[64];
-  uint4 r0[kSeedChunk];                // h0 window (two index ranges) of each middle hit
-  uint4 r2[kSeedChunk];                // h2 window
-  uint32_t ioff[kSeedChunk];           // first work item of each middle hit
-  unsigned long long best[kSeedChunk]; // smallest (bits(s), id0, id2) key of each middle hit
+  MlpWeights mlp;
+  union {                                   // seeding (module loop) and scoring (fit phase) never overlap
+    SeedArrays sd;
+    MlpTiles tiles[kTrackThreads / 32];
+  };
 };
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
@@ -56,20 +66,28 @@ __device__ __forceinline__ uint32_t module_of_pos(const uint32_t* mod_off, uint3
   return lo;
 }
 
-// hits of track t, ascending in z (upstream first), into x/y/z; returns n
+// hits of track t, ascending in z (upstream first), into x/y/z (+ modules,
+// cluster ids when asked); returns n
 __device__ __forceinline__ uint32_t gather_track(const Workspace& W, uint64_t p0, uint64_t tb, uint32_t t,
                                                  const uint32_t* mod_off, const float* mz, uint32_t M, float* xs,
-                                                 float* ys, float* zs, uint32_t* ids) {
+                                                 float* ys, float* zs, uint32_t* mods, uint32_t* ids) {
   const uint32_t n = W.trk_meta[tb + t] & 255u;
   uint32_t p = W.trk_a[tb + t];
   for (uint32_t j = 0; j < n; ++j) {
+    const uint32_t m = module_of_pos(mod_off, M, p);
     xs[j] = W.h_x[p0 + p];
     ys[j] = W.h_y[p0 + p];
-    zs[j] = mz[module_of_pos(mod_off, M, p)];
+    zs[j] = mz[m];
+    mods[j] = m;
     if (ids) ids[j] = W.h_id[p0 + p];
     p = W.sc[p0 + p];  // link to the next hit downstream
   }
   return n;
+}
+
+// chi2/ndf of the cut: straight-line chi2 without scattering, Kalman chi2 with it
+__device__ __forceinline__ float cut_chi2ndf(uint32_t n, const float* st, float theta) {
+  return fd(theta == 0.0f ? st[6] : st[7], (float)(2 * n - 4));
 }
 
 }  // namespace
@@ -121,6 +139,7 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
     used[i] = 0;
     first_of[i] = kNone;
   }
+  if (P.use_mlp) mlp_load(P.mlp, S.mlp, tid, NT);
   __syncthreads();
 
   uint32_t n_tr = 0;
@@ -206,13 +225,13 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
         uint32_t c = 0;
         if (i < cn) {
           const uint32_t p1 = cbase + i;
-          S.best[i] = ~0ull;
+          S.sd.best[i] = ~0ull;
           if (!used[p1]) {
             const float k1 = hk[p1];
             const Ranges R0 = window_ranges(hk, lo0, hi0, k1, P.win_seed);
-            S.r0[i] = make_uint4(R0.a0, R0.a1, R0.b0, R0.b1);
+            S.sd.r0[i] = make_uint4(R0.a0, R0.a1, R0.b0, R0.b1);
             const Ranges R2 = window_ranges(hk, lo2, hi2, k1, P.win_seed);
-            S.r2[i] = make_uint4(R2.a0, R2.a1, R2.b0, R2.b1);
+            S.sd.r2[i] = make_uint4(R2.a0, R2.a1, R2.b0, R2.b1);
             c = (R0.a1 - R0.a0) + (R0.b1 - R0.b0);
           }
         }
@@ -224,24 +243,24 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
         const uint32_t i = tid * PER + k;
-        if (i < cn) S.ioff[i] = run;
+        if (i < cn) S.sd.ioff[i] = run;
         run += cnt[k];
       }
       __syncthreads();
       for (uint32_t j = tid; j < n_items; j += NT) {
         // middle hit of item j: the last i with ioff[i] <= j (empty entries
         // share the offset of the next one, so that i owns item j)
-        const uint32_t i = lower_bound_by(0u, cn, [&](uint32_t x) { return S.ioff[x] <= j; }) - 1u;
+        const uint32_t i = lower_bound_by(0u, cn, [&](uint32_t x) { return S.sd.ioff[x] <= j; }) - 1u;
         const uint32_t p1 = cbase + i;
-        const uint4 R0 = S.r0[i];
-        const uint32_t kk = j - S.ioff[i], na = R0.y - R0.x;
+        const uint4 R0 = S.sd.r0[i];
+        const uint32_t kk = j - S.sd.ioff[i], na = R0.y - R0.x;
         const uint32_t q0 = kk < na ? R0.x + kk : R0.z + (kk - na);
         if (used[q0]) continue;
         const float k1 = hk[p1];
         if (dmod4(hk[q0], k1) > P.win_seed) continue;
         const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
         const unsigned long long lid0 = hid[q0] - lo0;
-        const uint4 R2 = S.r2[i];
+        const uint4 R2 = S.sd.r2[i];
         unsigned long long best = ~0ull;
         for (int part2 = 0; part2 < 2; ++part2) {
           const uint32_t s2 = part2 ? R2.z : R2.x, e2 = part2 ? R2.w : R2.y;
@@ -259,12 +278,12 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
             best = cand < best ? cand : best;
           }
         }
-        if (best != ~0ull) atomicMin(&S.best[i], best);
+        if (best != ~0ull) atomicMin(&S.sd.best[i], best);
       }
       __syncthreads();
       for (uint32_t i = tid; i < cn; i += NT) {  // seeds claim their h0 and h2
         const uint32_t p1 = cbase + i;
-        const unsigned long long key = S.best[i];
+        const unsigned long long key = S.sd.best[i];
         unsigned long long skey = ~0ull;
         if (key != ~0ull) {
           const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
@@ -315,12 +334,36 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
   // ---- fit, cut, canonical rank (by smallest cluster id) of every track
   uint32_t* rank = W.trk_rank + tb;
   uint32_t* hoff = W.trk_hoff + tb;
-  for (uint32_t t = tid; t < n_tr; t += NT) {
+  // every thread takes part in every round (the learned rule scores a warp's
+  // 32 candidates with warp-wide tensor-core instructions)
+  for (uint32_t base = 0; base < n_tr; base += NT) {
+    const uint32_t t = base + tid;
+    const bool valid = t < n_tr;
     float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
-    const uint32_t n = gather_track(W, p0, tb, t, S.mod_off, S.z, M, xs, ys, zs, nullptr);
-    fit_track(n, xs, ys, zs, P.sigma, P.ms_theta, st);
-    rank[t] = kNone;
-    if (keep_track(n, st, P.ms_theta, P.chi2ndf_max, P.chi2ndf_max_3hit)) first_of[hid[ta[t]]] = t;
+    float f[VELO_N_FEATURES];
+    uint32_t mods[VELO_MAX_MODULES];
+    uint32_t n = 0;
+    bool keep = false;
+    if (valid) {
+      n = gather_track(W, p0, tb, t, S.mod_off, S.z, M, xs, ys, zs, mods, nullptr);
+      fit_track(n, xs, ys, zs, P.sigma, P.ms_theta, st);
+      keep = keep_track(n, st, P.ms_theta, P.chi2ndf_max, P.chi2ndf_max_3hit);
+    }
+    if (P.use_mlp) {
+      const float r = valid ? cut_chi2ndf(n, st, P.ms_theta) : 0.0f;
+      if (valid) candidate_features(n, xs, ys, zs, mods, st, r, f);
+      else
+        for (int k = 0; k < VELO_N_FEATURES; ++k) f[k] = 0.0f;
+      const float logit = mlp_logit_warp(f, S.mlp, S.tiles[tid >> 5]);
+      if (valid) {
+        W.trk_logit[tb + t] = logit;
+        keep = r <= P.chi2ndf_max && logit >= P.mlp_logit_min;
+      }
+    }
+    if (valid) {
+      rank[t] = kNone;
+      if (keep) first_of[hid[ta[t]]] = t;
+    }
   }
   __syncthreads();
   unsigned long long run = 0;
@@ -378,10 +421,18 @@ __global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
     const uint32_t r = W.trk_rank[tb + t];
     if (r == kNone) continue;
     float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
-    uint32_t ids[VELO_MAX_MODULES];
-    const uint32_t n = gather_track(W, p0, tb, t, mod_off, mz, M, xs, ys, zs, ids);
+    uint32_t ids[VELO_MAX_MODULES], mods[VELO_MAX_MODULES];
+    const uint32_t n = gather_track(W, p0, tb, t, mod_off, mz, M, xs, ys, zs, mods, ids);
     fit_track(n, xs, ys, zs, L.par.sigma, L.par.ms_theta, st);
+    if (L.par.use_mlp) st[19] = W.trk_logit[tb + t];
     const uint64_t dst = to + r;
+    if (L.out.track_features) {
+      float f[VELO_N_FEATURES];
+      candidate_features(n, xs, ys, zs, mods, st, cut_chi2ndf(n, st, L.par.ms_theta), f);
+      float* of = L.out.track_features + dst * VELO_N_FEATURES;
+#pragma unroll
+      for (int k = 0; k < VELO_N_FEATURES; ++k) of[k] = f[k];
+    }
     const uint64_t h0 = hb + W.trk_hoff[tb + t];
     L.out.track_hit_offsets[dst] = h0;
     for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = ids[j];

@@ -1,0 +1,151 @@
+"""GPU checks of the learned ghost rejection (candidate features, bfloat16
+tensor-core inference, training kernels) against the CPU oracle, and what the
+trained network gains over the plain chi2 method.
+
+Features and the plain decisions are bit-exact (same binary32 steps); logits
+agree to the accumulation-order error of the tensor-core MMA (the oracle
+emulates the same bfloat16 roundings, but the order of the float32 sums inside
+an MMA is the hardware's); gradients agree with the float64 backprop to float32
+rounding.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2412_05041_b300 as velo
+import velogen
+from _compare import to_numpy
+from oracle import mlp as omlp
+from paper_2412_05041_b300 import mlp
+
+pytestmark = pytest.mark.gpu
+
+LOGIT_ATOL = 2e-2
+LOGIT_RTOL = 1e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    velo.build()
+    assert torch.cuda.is_available()
+
+
+def gpu(b, params, **kw):
+    off = torch.from_numpy(b.offsets.view(np.int64)).cuda()
+    pix = torch.from_numpy(b.pixels.view(np.int32)).cuda()
+    return to_numpy(velo.reconstruct(off, pix, b.geometry, params, **kw))
+
+
+def test_candidate_features_bit_exact():
+    b = velogen.generate(velogen.C2, n_events=80, first_event=123)
+    g = gpu(b, velo.default_params(), features=True)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, oracle.Params())
+    np.testing.assert_array_equal(g["track_hits"], r["track_hits"].astype(np.int32))
+    np.testing.assert_array_equal(g["track_features"], r["track_features"])
+
+
+def test_bf16_inference_matches_oracle_emulation():
+    b = velogen.generate(velogen.C2, n_events=40, first_event=555)
+    f = gpu(b, velo.default_params(), features=True)["track_features"]
+    mean, inv = mlp.normalisation(f)
+    rng = np.random.default_rng(1)
+    blob = omlp.pack(mean, inv, rng.normal(0, 0.5, omlp.N_WEIGHTS))
+    z_gpu = mlp.infer(f, blob, mode=0)
+    z_ref = np.array([oracle.mlp_logit(blob, fi) for fi in f])
+    np.testing.assert_allclose(z_gpu, z_ref, atol=LOGIT_ATOL, rtol=LOGIT_RTOL)
+    assert np.mean(np.abs(z_gpu - z_ref) <= 1e-4 * (1 + np.abs(z_ref))) > 0.9
+    # float32 path against the float64 reference (no bfloat16 rounding)
+    z32 = mlp.infer(f, blob, mode=1)
+    xn = (f.astype(np.float64) - mean) * inv
+    z64 = omlp.forward(blob[24:].astype(np.float64), xn)[0]
+    np.testing.assert_allclose(z32, z64, atol=1e-4, rtol=1e-4)
+    # ragged sizes: a partial last warp and a single candidate
+    for n in (1, 33, 257):
+        np.testing.assert_array_equal(mlp.infer(f[:n], blob, 0), z_gpu[:n])
+
+
+def test_loss_and_gradient_match_float64_backprop():
+    rng = np.random.default_rng(2)
+    for n in (1, 37, 512, 3000):
+        w = rng.normal(0, 0.4, omlp.N_WEIGHTS).astype(np.float32)
+        X = rng.normal(0, 1, (n, 12)).astype(np.float32)
+        y = (rng.random(n) < 0.3).astype(np.float32)
+        L64, g64 = omlp.backward(w.astype(np.float64), X, y)
+        tr = mlp.Trainer(w, n)
+        tr.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+        g = tr.g.cpu().numpy()
+        assert abs(float(tr.loss.item()) - L64) <= 1e-5 * (1 + L64)
+        np.testing.assert_allclose(g, g64, atol=1e-5 * np.abs(g64).max(), rtol=1e-3)
+
+
+def test_adam_step_matches_numpy():
+    rng = np.random.default_rng(3)
+    w = rng.normal(0, 1, omlp.N_WEIGHTS).astype(np.float32)
+    tr = mlp.Trainer(w, 64, lr=0.01)
+    X = rng.normal(0, 1, (64, 12)).astype(np.float32)
+    y = (rng.random(64) < 0.5).astype(np.float32)
+    m = np.zeros_like(w, np.float64)
+    v = np.zeros_like(w, np.float64)
+    wn = w.astype(np.float64)
+    for t in range(1, 4):
+        tr.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+        g = tr.g.cpu().numpy().astype(np.float64)
+        tr.t = t - 1
+        tr.step(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        wn = wn - 0.01 * (m / (1 - 0.9 ** t)) / (np.sqrt(v / (1 - 0.999 ** t)) + 1e-8)
+        np.testing.assert_allclose(tr.w.cpu().numpy(), wn, atol=1e-5, rtol=1e-4)
+
+
+def _learned_vs_oracle(b, blob, thr):
+    """GPU and oracle learned reconstructions agree except on candidates whose
+    logit lies within the inference tolerance of the threshold."""
+    vp = velo.default_params(use_mlp=1, mlp_logit_min=thr)
+    blob_dev = torch.from_numpy(blob).cuda()
+    vp.mlp = blob_dev.data_ptr()
+    g = gpu(b, vp, features=True)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, oracle.Params(use_mlp=1, mlp_logit_min=thr), mlp=blob)
+    cand = oracle.reconstruct(b.offsets, b.pixels, b.geometry, oracle.Params(chi2ndf_max_3hit=10.0))
+
+    def tracks(res):
+        out = {}
+        for e in range(b.n_events):
+            for t in range(int(res["track_offsets"][e]), int(res["track_offsets"][e + 1])):
+                h0, h1 = int(res["track_hit_offsets"][t]), int(res["track_hit_offsets"][t + 1])
+                out[(e, tuple(int(v) for v in res["track_hits"][h0:h1]))] = t
+        return out
+
+    tg, to_, tc = tracks(g), tracks(r), tracks(cand)
+    for key in set(tg) ^ set(to_):
+        z = oracle.mlp_logit(blob, cand["track_features"][tc[key]])
+        assert abs(z - thr) <= LOGIT_ATOL + LOGIT_RTOL * abs(thr), (key, z, thr)
+    common = set(tg) & set(to_)
+    for key in common:
+        a, c = g["track_states"][tg[key]], r["track_states"][to_[key]]
+        np.testing.assert_array_equal(a[:19], c[:19])
+        assert abs(a[19] - c[19]) <= LOGIT_ATOL + LOGIT_RTOL * abs(c[19])
+    return len(common), len(set(tg) ^ set(to_))
+
+
+@pytest.mark.slow
+def test_trained_network_beats_plain_cut_and_matches_oracle():
+    """Train on candidates of seed-4 pile-up-5.5 events, choose the threshold
+    there, and evaluate on seed-5 events: the learned rule keeps the efficiency
+    within 0.5 % of the plain chi2 method and lowers the ghost rate."""
+    train_b = velogen.generate(velogen.Config(seed=4, n_events=1200), truth=True)
+    test_b = velogen.generate(velogen.Config(seed=5, n_events=400), truth=True)
+    tr = mlp.collect(train_b)
+    assert len(tr.labels) > 250_000 and 0.02 < 1 - tr.labels.mean() < 0.3
+    blob, hist = mlp.train(tr.features, tr.labels, epochs=6, batch_size=4096, lr=3e-3)
+    assert hist[-1] < hist[0] and hist[-1] < 0.2
+    thr = mlp.choose_threshold(tr, mlp.infer(tr.features, blob, 0), cut3=2.0)
+    te = mlp.collect(test_b)
+    z = mlp.infer(te.features, blob, 0)
+    plain = mlp.event_metrics_at(te, mlp.plain_keep(te, 2.0))
+    learned = mlp.event_metrics_at(te, z >= thr)
+    assert learned["efficiency"] >= plain["efficiency"] - 0.005, (plain, learned)
+    assert learned["ghost_rate"] < plain["ghost_rate"], (plain, learned)
+    n_common, n_diff = _learned_vs_oracle(velogen.generate(velogen.Config(seed=5, n_events=60)), blob, thr)
+    assert n_common > 10_000 and n_diff <= 5
