@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--events", type=int, default=10_000, help="events per GPU per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -272,6 +273,37 @@ def run_ours(args):
         ms = float(t.item())
     value = world * n_ev / (ms / 1000.0)
 
+    # learned form: the same batch with the ghost-rejection network on tensor cores
+    learned = None
+    model = os.path.join(ROOT, "paper_2412_05041_b300", "models", "ghost_mlp.bin")
+    if os.path.exists(model) and not args.no_learned:
+        from paper_2412_05041_b300 import mlp as vmlp
+        blob, thr = vmlp.load(model)
+        blob_dev = torch.from_numpy(blob).to(dev)
+        lp = velo.default_params(**params_values(cfg.ms_theta))
+        lp.use_mlp, lp.mlp_logit_min, lp.mlp = 1, thr, blob_dev.data_ptr()
+        RL = velo.Reconstructor(b.geometry, lp, max_events=n_ev, max_pixels=P, device=dev)
+        for _ in range(max(args.warmup, 0)):
+            RL.run(off, pix, stream)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        l0.record(stream)
+        for _ in range(K):
+            RL.run(off, pix, stream)
+        l1.record(stream)
+        torch.cuda.synchronize(dev)
+        lms = l0.elapsed_time(l1) / K
+        learned = {"value": n_ev / (lms / 1000.0), "unit": UNIT, "ms_per_step": lms, "logit_min": thr,
+                   "tracks": int(RL.result()["track_offsets"][-1])}
+        if rank == 0:
+            hold = velogen.generate(velogen.Config(seed=5, n_events=300, ms_theta=cfg.ms_theta), truth=True)
+            c = vmlp.collect(hold, velo.default_params(**params_values(cfg.ms_theta)))
+            z = vmlp.infer(c.features, blob, 0)
+            pm, lm = vmlp.event_metrics_at(c, vmlp.plain_keep(c, 2.0)), vmlp.event_metrics_at(c, z >= thr)
+            learned.update({"efficiency_plain": pm["efficiency"], "ghost_rate_plain": pm["ghost_rate"],
+                            "efficiency_learned": lm["efficiency"], "ghost_rate_learned": lm["ghost_rate"],
+                            "quality_sample": "300 held-out pile-up-5.5 events (generator seed 5)"})
+
     # batch latency percentiles: 1k-event batches, one at a time
     lat = []
     nb = min(1000, n_ev)
@@ -336,10 +368,11 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (event sharding)"},
         "p50_batch_latency_ms": float(np.percentile(lat, 50)), "p99_batch_latency_ms": float(np.percentile(lat, 99)),
         "latency_batch_events": nb,
-        "gpu_launches": 5 * K,
+        "gpu_launches": 5 * K,  # validate, cluster, track, scan, output per step
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": e2e,
+        "learned": learned,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfg)

@@ -61,6 +61,8 @@ class Candidates:
     labels: np.ndarray     # [N] float32 (1 = matches a particle)
     batch: object          # generator batch (with truth)
     result: dict           # numpy result of the candidate reconstruction
+    match: np.ndarray      # [N] matched batch-global particle id, -1 = ghost
+    reconstructible: np.ndarray  # batch-global ids of reconstructible particles
 
 
 def candidate_params(base=None):
@@ -81,7 +83,8 @@ def collect(batch, params=None) -> Candidates:
     res = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in r.items()}
     ct = truth.cluster_truth(batch, res)
     m = truth.track_matches(res, ct)
-    return Candidates(res["track_features"].astype(np.float32), (m >= 0).astype(np.float32), batch, res)
+    rec = truth.reconstructible(batch, res, ct)
+    return Candidates(res["track_features"].astype(np.float32), (m >= 0).astype(np.float32), batch, res, m, rec)
 
 
 # ------------------------------------------------------------------ training
@@ -168,14 +171,10 @@ def infer(features: np.ndarray, blob: np.ndarray, mode: int = 0) -> np.ndarray:
 # ------------------------------------------------------------------ threshold and evaluation
 def event_metrics_at(cands: Candidates, keep: np.ndarray) -> dict:
     """Efficiency / ghost rate of the candidate set restricted to `keep` (bool per candidate)."""
-    res = cands.result
-    ct = truth.cluster_truth(cands.batch, res)
-    m = truth.track_matches(res, ct)
-    rec = truth.reconstructible(cands.batch, res, ct)
-    mk = m[keep]
-    found = np.intersect1d(rec, mk[mk >= 0])
-    return dict(efficiency=len(found) / max(len(rec), 1), ghost_rate=float((mk < 0).mean()) if len(mk) else 0.0,
-                tracks=int(keep.sum()))
+    mk = cands.match[keep]
+    found = np.intersect1d(cands.reconstructible, mk[mk >= 0])
+    return dict(efficiency=len(found) / max(len(cands.reconstructible), 1),
+                ghost_rate=float((mk < 0).mean()) if len(mk) else 0.0, tracks=int(keep.sum()))
 
 
 def plain_keep(cands: Candidates, cut3: float) -> np.ndarray:
