@@ -137,6 +137,11 @@ typedef struct velo_output {
   float* track_states;          /* [cap_tracks * VELO_STATE_STRIDE] */
   uint64_t* totals;             /* [4]: n_clusters, n_tracks, n_track_hits, n_failed_events */
   float* track_features;        /* optional (NULL = not written) [cap_tracks * VELO_N_FEATURES] */
+  /* Capacities of the arrays above (0 = the bounds velo_query_sizes gives,
+   * which always suffice).  A batch whose totals exceed a capacity writes no
+   * cluster and no track: the caller sees totals[0..2] above its capacities
+   * and retries with larger buffers or a smaller batch. */
+  uint64_t cap_clusters, cap_tracks, cap_track_hits;
 } velo_output_t;
 
 /* Capacities that always suffice for a batch of n_events events holding
@@ -175,6 +180,24 @@ int velo_reconstruct_into(const velo_events_t* events, const velo_geometry_t* ge
 int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometry_t* geometry,
                                  const velo_params_t* params, const velo_output_t* out, void* workspace,
                                  uint64_t workspace_bytes, void* stream, void* const* stage_events);
+
+/* Block shapes of the persistent kernels (events of any size are spread over
+ * the SMs by work queues; these choose how).  Any valid setting gives the same
+ * results bit for bit; speed depends on the workload (autotuned by the Python
+ * layer).  velo_tuning_default: 1024 / largest tier / 256 / all resident. */
+typedef struct velo_tuning {
+  uint32_t cluster_threads;      /* 512 (two CTAs per SM) or 1024 (one) */
+  uint32_t cluster_smem_pixels;  /* words per event sorted in shared memory, 0 = the most that fits;
+                                    larger events run on their global-memory slice */
+  uint32_t track_threads;        /* 128 or 256 */
+  uint32_t ctas_per_sm;          /* persistent grid per kernel: 0 = every CTA that fits */
+} velo_tuning_t;
+int velo_tuning_default(velo_tuning_t* t);
+/* velo_reconstruct_into_marked with explicit block shapes (NULL = defaults). */
+int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry_t* geometry,
+                                const velo_params_t* params, const velo_output_t* out, void* workspace,
+                                uint64_t workspace_bytes, void* stream, void* const* stage_events,
+                                const velo_tuning_t* tuning);
 
 /* The same with library-owned results (the form of the call that returns
  * "tracks"): allocates the output buffers and the workspace on `stream`

@@ -54,7 +54,16 @@ class Events(ctypes.Structure):
 class Output(ctypes.Structure):
     _fields_ = [("status", _P), ("cluster_offsets", _P), ("cluster_x", _P), ("cluster_y", _P), ("cluster_z", _P),
                 ("pixel_cluster", _P), ("track_offsets", _P), ("track_hit_offsets", _P), ("track_hits", _P),
-                ("track_states", _P), ("totals", _P), ("track_features", _P)]
+                ("track_states", _P), ("totals", _P), ("track_features", _P), ("cap_clusters", ctypes.c_uint64),
+                ("cap_tracks", ctypes.c_uint64), ("cap_track_hits", ctypes.c_uint64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("cluster_threads", ctypes.c_uint32), ("cluster_smem_pixels", ctypes.c_uint32),
+                ("track_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Sizes(ctypes.Structure):
@@ -75,7 +84,7 @@ _lib = None
 
 # every entry point declared in include/velo.h
 EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "velo_reconstruct_into_marked",
-           "velo_reconstruct",
+           "velo_tuning_default", "velo_reconstruct_into_tuned", "velo_reconstruct",
            "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
            "velo_reconstruct_host", "velo_reconstruct_static", "velo_mlp_infer", "velo_mlp_workspace_size",
            "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_strerror", "velo_version")
@@ -93,6 +102,8 @@ def lib():
         L.velo_reconstruct_into.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry), ctypes.POINTER(Params),
                                             ctypes.POINTER(Output), _P, ctypes.c_uint64, _P]
         L.velo_reconstruct_into_marked.argtypes = L.velo_reconstruct_into.argtypes + [ctypes.POINTER(_P)]
+        L.velo_tuning_default.argtypes = [ctypes.POINTER(Tuning)]
+        L.velo_reconstruct_into_tuned.argtypes = L.velo_reconstruct_into_marked.argtypes + [ctypes.POINTER(Tuning)]
         L.velo_reconstruct.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry), ctypes.POINTER(Params),
                                        ctypes.POINTER(_P), _P]
         L.velo_result_view.argtypes = [_P, ctypes.POINTER(ResultView)]
@@ -144,10 +155,18 @@ def geometry_struct(g) -> _GeometryHolder:
     return _GeometryHolder(g)
 
 
+def default_tuning(**overrides) -> Tuning:
+    t = Tuning()
+    check(lib().velo_tuning_default(ctypes.byref(t)), "velo_tuning_default")
+    for k, v in overrides.items():
+        setattr(t, k, v)
+    return t
+
+
 def query_sizes(n_events: int, n_pixels: int) -> Sizes:
     s = Sizes()
     check(lib().velo_query_sizes(n_events, n_pixels, ctypes.byref(s)), "velo_query_sizes")
     return s
 
 
-from .api import Reconstructor, HostReconstructor, reconstruct  # noqa: E402,F401
+from .api import GraphReconstructor, HostReconstructor, Reconstructor, reconstruct  # noqa: E402,F401

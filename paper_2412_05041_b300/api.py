@@ -28,11 +28,20 @@ class Reconstructor:
     events and ``max_pixels`` pixel words, reused across calls."""
 
     def __init__(self, geometry, params=None, max_events: int = 1, max_pixels: int = 1, device="cuda",
-                 pixel_labels: bool = False, features: bool = False):
+                 pixel_labels: bool = False, features: bool = False, tuning=None, cap_tracks: int | None = None,
+                 cap_clusters: int | None = None):
+        """cap_tracks / cap_clusters: output capacities below the always-sufficient
+        bounds (a batch that does not fit writes no output; see ``fits()``)."""
         self.geo = geometry_struct(geometry)
         self.params = params if params is not None else default_params()
+        self.tuning = tuning
         self.max_events, self.max_pixels = int(max_events), int(max_pixels)
         s = query_sizes(self.max_events, self.max_pixels)
+        if cap_clusters is not None:
+            s.cap_clusters = min(s.cap_clusters, int(cap_clusters))
+            s.cap_track_hits = min(s.cap_track_hits, int(cap_clusters))
+        if cap_tracks is not None:
+            s.cap_tracks = min(s.cap_tracks, int(cap_tracks))
         dev = torch.device(device)
         E = self.max_events
         self.sizes = s
@@ -54,7 +63,8 @@ class Reconstructor:
         self._out = Output(_ptr(self.status), _ptr(self.cluster_offsets), _ptr(self.cluster_x), _ptr(self.cluster_y),
                            _ptr(self.cluster_z), _ptr(self.pixel_cluster), _ptr(self.track_offsets),
                            _ptr(self.track_hit_offsets), _ptr(self.track_hits), _ptr(self.track_states),
-                           _ptr(self.totals), _ptr(self.track_features))
+                           _ptr(self.totals), _ptr(self.track_features), max(s.cap_clusters, 1),
+                           max(s.cap_tracks, 1), max(s.cap_track_hits, 1))
         self.n_events = 0
 
     def run(self, offsets: torch.Tensor, pixels: torch.Tensor, stream=None, marks=None) -> None:
@@ -77,18 +87,27 @@ class Reconstructor:
                 if not m.cuda_event:  # torch creates the handle lazily at the first record
                     m.record(stream if stream is not None else torch.cuda.current_stream())
             mk = (ctypes.c_void_p * 5)(*[m.cuda_event for m in marks])
-        rc = lib().velo_reconstruct_into_marked(ctypes.byref(ev), ctypes.byref(self.geo.s), ctypes.byref(self.params),
-                                                ctypes.byref(self._out), _ptr(self.workspace), self.workspace.numel(),
-                                                _stream_handle(stream), mk)
-        check(rc, "velo_reconstruct_into_marked")
+        rc = lib().velo_reconstruct_into_tuned(ctypes.byref(ev), ctypes.byref(self.geo.s), ctypes.byref(self.params),
+                                               ctypes.byref(self._out), _ptr(self.workspace), self.workspace.numel(),
+                                               _stream_handle(stream), mk,
+                                               None if self.tuning is None else ctypes.byref(self.tuning))
+        check(rc, "velo_reconstruct_into_tuned")
         self.n_events = E
         self.n_pixels = P
+
+    def fits(self, totals) -> bool:
+        nc, nt, nh = (int(v) for v in totals[:3])
+        return nc <= self.sizes.cap_clusters and nt <= self.sizes.cap_tracks and nh <= self.sizes.cap_track_hits
 
     def result(self, stream=None) -> dict:
         """Views of the last batch's outputs, trimmed to their sizes (waits for the stream)."""
         s = stream if stream is not None else torch.cuda.current_stream()
         s.synchronize()
-        nc, nt, nh, nf = (int(v) for v in self.totals.cpu())
+        tot = self.totals.cpu()
+        if not self.fits(tot):
+            raise VeloError(f"batch output {tot[:3].tolist()} exceeds the capacities "
+                            f"({self.sizes.cap_clusters}, {self.sizes.cap_tracks}, {self.sizes.cap_track_hits})")
+        nc, nt, nh, nf = (int(v) for v in tot)
         E = self.n_events
         r = dict(status=self.status[:E], cluster_offsets=self.cluster_offsets[:E + 1], cluster_x=self.cluster_x[:nc],
                  cluster_y=self.cluster_y[:nc], cluster_z=self.cluster_z[:nc], track_offsets=self.track_offsets[:E + 1],
@@ -102,12 +121,42 @@ class Reconstructor:
 
 
 def reconstruct(offsets: torch.Tensor, pixels: torch.Tensor, geometry, params=None, pixel_labels: bool = False,
-                stream=None, features: bool = False) -> dict:
+                stream=None, features: bool = False, tuning=None) -> dict:
     """One-shot: allocate, run, wait, return trimmed device tensors."""
     R = Reconstructor(geometry, params, max(offsets.numel() - 1, 0), pixels.numel(), device=pixels.device,
-                      pixel_labels=pixel_labels, features=features)
+                      pixel_labels=pixel_labels, features=features, tuning=tuning)
     R.run(offsets, pixels, stream)
     return R.result(stream)
+
+
+class GraphReconstructor(Reconstructor):
+    """A Reconstructor whose launch sequence (validation, persistent clustering,
+    persistent tracking, offsets scan, persistent output) is captured once into
+    a CUDA graph for a fixed batch shape and replayed as one graph launch.
+    ``load`` copies a new batch of the same shape into the captured inputs."""
+
+    def __init__(self, offsets: torch.Tensor, pixels: torch.Tensor, geometry, params=None, **kw):
+        super().__init__(geometry, params, offsets.numel() - 1, pixels.numel(), device=pixels.device, **kw)
+        self.off_in = offsets.clone()
+        self.pix_in = pixels.clone()
+        s = torch.cuda.Stream(device=pixels.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(self.off_in, self.pix_in, s)  # first call outside capture: one-time set-up
+        s.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=s):
+            self.run(self.off_in, self.pix_in, s)
+        torch.cuda.current_stream().wait_stream(s)
+
+    def load(self, offsets: torch.Tensor, pixels: torch.Tensor) -> None:
+        if offsets.shape != self.off_in.shape or pixels.shape != self.pix_in.shape:
+            raise VeloError("a graph replays one batch shape")
+        self.off_in.copy_(offsets)
+        self.pix_in.copy_(pixels)
+
+    def replay(self) -> None:
+        self.graph.replay()
 
 
 class HostReconstructor:
@@ -137,7 +186,7 @@ class HostReconstructor:
         self._out = Output(_ptr(self.status), _ptr(self.cluster_offsets), _ptr(self.cluster_x), _ptr(self.cluster_y),
                            _ptr(self.cluster_z), _ptr(self.pixel_cluster), _ptr(self.track_offsets),
                            _ptr(self.track_hit_offsets), _ptr(self.track_hits), _ptr(self.track_states),
-                           _ptr(self.totals), None)
+                           _ptr(self.totals), None, 0, 0, 0)
 
     def __del__(self):
         if getattr(self, "ctx", None) and self.ctx.value:

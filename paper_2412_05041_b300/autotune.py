@@ -1,0 +1,86 @@
+"""Autotuner of the persistent kernels' block shapes (velo_tuning_t).
+
+Times every candidate shape on a sample of the target workload (CUDA events,
+best of a few repetitions after warm-up), checks that each one reproduces the
+default shape's output bit for bit, and returns the fastest.  Results are
+cached per (device, workload signature) in a JSON file.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import default_tuning, Tuning
+from .api import Reconstructor
+
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "velo_b300", "tuning.json")
+
+
+def candidates():
+    out = []
+    for ct, tt, cps in itertools.product((1024, 512), (128, 256), (0, 1, 2)):
+        if ct == 512 and cps == 1:
+            continue
+        out.append(default_tuning(cluster_threads=ct, cluster_smem_pixels=0, track_threads=tt, ctas_per_sm=cps))
+    return out
+
+
+def _signature(offsets: torch.Tensor, pixels: torch.Tensor) -> str:
+    n = np.diff(offsets.cpu().numpy())
+    return f"{torch.cuda.get_device_name()}|E{len(n)}|P{int(n.sum())}|p99={int(np.percentile(n, 99))}"
+
+
+def _outputs(R: Reconstructor) -> dict:
+    r = R.result()
+    return {k: v.cpu().numpy() for k, v in r.items() if hasattr(v, "cpu")}
+
+
+def tune(offsets: torch.Tensor, pixels: torch.Tensor, geometry, params=None, reps: int = 3, use_cache: bool = True,
+         verbose: bool = False):
+    """Returns (best Tuning, table of (tuning dict, ms)) for this batch."""
+    sig = _signature(offsets, pixels)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            cache = json.load(open(CACHE))
+        except (OSError, ValueError):
+            cache = {}
+        if sig in cache:
+            return default_tuning(**cache[sig]["best"]), cache[sig]["table"]
+    E, P = offsets.numel() - 1, pixels.numel()
+    ref = None
+    table = []
+    stream = torch.cuda.current_stream()
+    for t in candidates():
+        R = Reconstructor(geometry, params, E, P, device=pixels.device, tuning=t)
+        R.run(offsets, pixels, stream)
+        out = _outputs(R)
+        if ref is None:
+            ref = out
+        else:
+            for k in ref:
+                if not np.array_equal(ref[k], out[k]):
+                    raise RuntimeError(f"tuning {t.as_dict()} changed {k}")
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            R.run(offsets, pixels, stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        table.append((t.as_dict(), best))
+        if verbose:
+            print(t.as_dict(), f"{best:.3f} ms")
+        del R
+    best_t = min(table, key=lambda x: x[1])[0]
+    if use_cache:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        cache[sig] = {"best": best_t, "table": table}
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return default_tuning(**best_t), table

@@ -2,8 +2,10 @@
 // workspace layout, the launch sequence, and the allocating conveniences.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "velo_internal.cuh"
 
@@ -26,6 +28,7 @@ struct Carver {
 void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   const uint64_t T = P / 3 + 1;
   ws->flag = c.take<uint32_t>(4);
+  ws->queue = c.take<uint32_t>(4);
   ws->ev_nclusters = c.take<uint32_t>(E);
   ws->ev_modoff = c.take<uint32_t>(E * kModOffStride);
   ws->ev_ntracks_all = c.take<uint32_t>(E);
@@ -120,7 +123,59 @@ Par make_par(const velo_params_t* p) {
   return P;
 }
 
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+uint32_t g_smem_set[kMaxDev] = {};  // bit per kernel slot: dynamic shared-memory limit raised
+struct OccKey {
+  int dev;
+  const void* func;
+  uint32_t smem;
+  int occ;
+};
+OccKey g_occ[256];
+int g_nocc = 0;
+int g_sms[kMaxDev] = {};
+
+int current_device() {
+  int d = 0;
+  return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+
+int sm_count() {
+  const int d = current_device();
+  if (d < 0 || d >= kMaxDev) return 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_sms[d]) cudaDeviceGetAttribute(&g_sms[d], cudaDevAttrMultiProcessorCount, d);
+  return g_sms[d];
+}
+
 }  // namespace
+
+bool set_max_smem_once(const void* func, int slot) {
+  const int d = current_device();
+  if (d < 0 || d >= kMaxDev) return false;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_smem_set[d] & (1u << slot)) return true;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPerBlock) != cudaSuccess) {
+    cudaGetLastError();  // do not leave the failure as the sticky last error
+    return false;
+  }
+  g_smem_set[d] |= 1u << slot;
+  return true;
+}
+
+int occupancy(const void* func, int threads, uint32_t smem, int slot) {
+  const int d = current_device();
+  if (d < 0 || d >= kMaxDev) return 0;
+  if (slot >= 0 && !set_max_smem_once(func, slot)) return 0;  // slot < 0: static shared memory only
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int i = 0; i < g_nocc; ++i)
+    if (g_occ[i].dev == d && g_occ[i].func == func && g_occ[i].smem == smem) return g_occ[i].occ;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, threads, smem) != cudaSuccess) occ = 0;
+  if (g_nocc < 256) g_occ[g_nocc++] = {d, func, smem, occ};
+  return occ;
+}
 
 uint64_t workspace_bytes(uint64_t E, uint64_t P) {
   Carver c{nullptr};
@@ -208,10 +263,36 @@ int velo_reconstruct_into(const velo_events_t* events, const velo_geometry_t* ge
 int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometry_t* geometry,
                                  const velo_params_t* params, const velo_output_t* out, void* workspace,
                                  uint64_t workspace_bytes_, void* stream, void* const* marks) {
+  return velo_reconstruct_into_tuned(events, geometry, params, out, workspace, workspace_bytes_, stream, marks,
+                                     nullptr);
+}
+
+int velo_tuning_default(velo_tuning_t* t) {
+  if (!t) return VELO_EINVAL;
+  t->cluster_threads = 1024;
+  t->cluster_smem_pixels = 0;
+  t->track_threads = 256;
+  t->ctas_per_sm = 0;
+  return VELO_OK;
+}
+
+int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry_t* geometry,
+                                const velo_params_t* params, const velo_output_t* out, void* workspace,
+                                uint64_t workspace_bytes_, void* stream, void* const* marks,
+                                const velo_tuning_t* tuning) {
   if (!events || !events->event_offsets || (events->n_pixels && !events->pixels)) return VELO_EINVAL;
   if (events->n_events >= (1ull << 31) || events->n_pixels >= (1ull << 40)) return VELO_EINVAL;
   if (!geometry_ok(geometry) || !params_ok(params) || !output_ok(out)) return VELO_EINVAL;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return VELO_EINVAL;
+  velo_tuning_t tu;
+  velo_tuning_default(&tu);
+  if (tuning) tu = *tuning;
+  if ((tu.cluster_threads != 512 && tu.cluster_threads != 1024) ||
+      (tu.track_threads != 128 && tu.track_threads != 256))
+    return VELO_EINVAL;
+  const uint32_t max_tier = cluster_max_tier((int)tu.cluster_threads);
+  const uint32_t tier = tu.cluster_smem_pixels ? tu.cluster_smem_pixels : max_tier;
+  if (tier > max_tier || tier < 256) return VELO_EINVAL;
   Launch L;
   std::memset(&L, 0, sizeof(L));
   L.n_events = events->n_events;
@@ -221,26 +302,33 @@ int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometr
   L.geo = make_geo(geometry);
   L.par = make_par(params);
   L.out = *out;
+  L.cluster_tier = tier;
   if (!carve_workspace(workspace, workspace_bytes_, L.n_events, L.n_pixels, &L.ws)) return VELO_ECAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const unsigned E = (unsigned)L.n_events;
+  const uint64_t E = L.n_events;
+  const int sms = sm_count();
+  if (sms <= 0) return VELO_ECUDA;
+  auto grid = [&](int per_sm) -> uint32_t {  // persistent grid, never more CTAs than events
+    if (tu.ctas_per_sm) per_sm = per_sm > 0 ? (int)std::min<uint32_t>((uint32_t)per_sm, tu.ctas_per_sm) : 0;
+    const uint64_t g = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)sms;
+    return (uint32_t)std::min<uint64_t>(g, E);
+  };
   auto mark = [&](int i) {
     if (marks && marks[i]) cudaEventRecord(reinterpret_cast<cudaEvent_t>(marks[i]), s);
   };
   k_validate_offsets<<<1, kScanThreads, 0, s>>>(L);
   mark(0);
-  if (E) {
-    const uint32_t smem = cluster_smem_bytes();
-    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return VELO_ECUDA;
-    k_cluster<<<E, kClusterThreads, smem, s>>>(L);
-  }
+  int rc = VELO_OK;
+  if (E) rc = launch_cluster(L, (int)tu.cluster_threads, grid(cluster_blocks_per_sm((int)tu.cluster_threads, tier)), s);
+  if (rc != VELO_OK) return rc;
   mark(1);
-  if (E) k_track<<<E, kTrackThreads, 0, s>>>(L);
+  if (E) rc = launch_track(L, (int)tu.track_threads, grid(track_blocks_per_sm((int)tu.track_threads)), s);
+  if (rc != VELO_OK) return rc;
   mark(2);
   k_scan<<<1, kScanThreads, 0, s>>>(L);
   mark(3);
-  if (E) k_output<<<E, kOutputThreads, 0, s>>>(L);
+  if (E) rc = launch_output(L, grid(output_blocks_per_sm()), s);
+  if (rc != VELO_OK) return rc;
   mark(4);
   return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;
 }

@@ -2,7 +2,8 @@
 //
 // The first stage reconstructs every event from the raw detector data
 // (Sec. "Data flow overview"); for the pixel tracker this starts with
-// clustering.  One CTA per event (1024 threads, one CTA per SM):
+// clustering.  One CTA per event at a time (1024 threads and one CTA per SM,
+// or 512 threads and two; persistent, events from a work queue):
 //   1. load and validate the event's words (coalesced, 4 B per thread);
 //   2. stable block radix sort by the 27-bit (module, row, col) key
 //      (4 passes of 8 bits) in shared memory;
@@ -25,12 +26,14 @@ namespace velo {
 
 namespace {
 
+template <int NT>
 struct ClusterSmem {
-  uint32_t cnt[kRadixCounters];
+  uint32_t cnt[radix_counters(NT)];
   uint32_t tmp[64];
   uint32_t mod_count[VELO_MAX_MODULES];
   uint32_t mod_off[kModOffStride];
   uint32_t flag;
+  uint32_t next;  // event taken from the work queue
   uint32_t pad[2];
 };
 
@@ -93,15 +96,12 @@ __device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offse
 
 }  // namespace
 
-uint32_t cluster_smem_bytes() { return (uint32_t)sizeof(ClusterSmem) + 2u * kClusterSmemPixels * 4u; }
-
-__global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
-  constexpr int NT = kClusterThreads;
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  ClusterSmem& S = *reinterpret_cast<ClusterSmem*>(smem_raw);
-  uint32_t* region = reinterpret_cast<uint32_t*>(smem_raw + sizeof(ClusterSmem));
+// The clustering of event e by one CTA of NT threads; `tier` = most words
+// kept in shared memory (the region holds 2 * tier words).
+template <int NT>
+__device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
+                                            const uint32_t tier) {
   const Workspace& W = L.ws;
-  const uint64_t e = blockIdx.x;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
 
@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
   __syncthreads();
 
   // 1. load + validate
-  const bool smem_tier = n <= kClusterSmemPixels;
+  const bool smem_tier = n <= tier;
   uint32_t* A = smem_tier ? region : W.sa + p0;
-  uint32_t* B = smem_tier ? region + kClusterSmemPixels : W.sb + p0;
+  uint32_t* B = smem_tier ? region + tier : W.sb + p0;
   if (offsets_ok) {
     for (uint32_t i = tid; i < n; i += NT) {
       const uint32_t w = __ldg(L.pix + p0 + i);
@@ -239,11 +239,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
   }
 
   // 5. integer charge sums per cluster, then the binary32 centroid.  With at
-  // most kClusterSmemPixels words, sum q(2c+1) <= 15 * 4095 * 23552 < 2^32, so
+  // most kNarrowPixels words, sum q(2c+1) <= 15 * 4095 * 23552 < 2^32, so
   // 32-bit sums (and a 32-bit division) are exact; larger events use 64 bits.
-  const bool narrow = n <= kClusterSmemPixels;
+  const bool narrow = n <= kNarrowPixels;
   unsigned long long* acc = W.acc + 3 * p0;
-  uint32_t* acc32 = reinterpret_cast<uint32_t*>(W.acc) + 3 * p0;
+  uint32_t* acc32 = reinterpret_cast<uint32_t*>(acc);  // inside this event's own 64-bit slice
   if (narrow) {
     for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc32[i] = 0u;
   } else {
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
 
   // the pixel arrays are dead from here on: the hit sort reuses the region
   // (keys, values, their ping-pong copies and the cluster x, y: 6 words per cluster)
-  const bool hit_smem = 6u * n_clusters <= 2u * kClusterSmemPixels;
+  const bool hit_smem = 6u * n_clusters <= 2u * tier;
   uint32_t* KA = hit_smem ? region : W.sa + p0;
   uint32_t* KB = hit_smem ? region + n_clusters : W.sb + p0;
   uint32_t* VA = hit_smem ? region + 2 * n_clusters : W.sc + p0;
@@ -325,6 +325,53 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cluster(Launch L) {
     W.ev_nclusters[e] = n_clusters;
     L.out.status[e] = VELO_EVT_OK;
   }
+}
+
+// Persistent: every CTA takes events from the work queue until it is empty,
+// so events of uneven size spread over the SMs as they finish.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_cluster(Launch L) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  ClusterSmem<NT>& S = *reinterpret_cast<ClusterSmem<NT>*>(smem_raw);
+  uint32_t* region = reinterpret_cast<uint32_t*>(smem_raw + sizeof(ClusterSmem<NT>));
+  for (;;) {
+    if (threadIdx.x == 0) S.next = atomicAdd(L.ws.queue + 0, 1u);
+    __syncthreads();
+    const uint32_t e = S.next;
+    __syncthreads();
+    if (e >= L.n_events) break;
+    cluster_one<NT>(L, e, S, region, L.cluster_tier);
+    __syncthreads();
+  }
+}
+
+uint32_t cluster_smem_bytes(int nt, uint32_t tier) {
+  const uint32_t head = nt == 512 ? (uint32_t)sizeof(ClusterSmem<512>) : (uint32_t)sizeof(ClusterSmem<1024>);
+  return head + 2u * tier * 4u;
+}
+
+uint32_t cluster_max_tier(int nt) {
+  const uint32_t head = cluster_smem_bytes(nt, 0);
+  const uint32_t cap = nt == 512 ? kSmemPerSm / 2 - 1024 : kSmemPerBlock;  // two CTAs per SM at 512 threads
+  return ((cap - head) / 8u) & ~255u;
+}
+
+int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
+  const uint32_t smem = cluster_smem_bytes(nt, L.cluster_tier);
+  if (nt == 512) {
+    if (!set_max_smem_once(reinterpret_cast<const void*>(k_cluster<512>), 0)) return VELO_ECUDA;
+    k_cluster<512><<<grid, 512, smem, s>>>(L);
+  } else {
+    if (!set_max_smem_once(reinterpret_cast<const void*>(k_cluster<1024>), 1)) return VELO_ECUDA;
+    k_cluster<1024><<<grid, 1024, smem, s>>>(L);
+  }
+  return VELO_OK;
+}
+
+int cluster_blocks_per_sm(int nt, uint32_t tier) {
+  return occupancy(nt == 512 ? reinterpret_cast<const void*>(k_cluster<512>)
+                             : reinterpret_cast<const void*>(k_cluster<1024>),
+                   nt, cluster_smem_bytes(nt, tier), nt == 512 ? 0 : 1);
 }
 
 }  // namespace velo

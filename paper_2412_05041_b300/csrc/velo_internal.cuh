@@ -1,23 +1,22 @@
 // Internal launch arguments and workspace layout of the VELO tracking library.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "velo.h"
 
 namespace velo {
 
-// Block shapes.
-constexpr int kClusterThreads = 1024;  // one CTA per event, one CTA per SM (shared-memory bound)
-constexpr int kTrackThreads = 256;     // one CTA per event, several CTAs per SM
+// Block shapes (the tunable ones are chosen per call, see velo_tuning_t).
 constexpr int kOutputThreads = 256;
 constexpr int kScanThreads = 1024;
+constexpr uint32_t kSmemPerSm = 228u * 1024u;    // shared memory of one SM
+constexpr uint32_t kSmemPerBlock = 227u * 1024u; // largest dynamic allocation of one CTA
 
-// Clustering keeps an event's sorted pixel words and their union-find
-// parents in shared memory when it has at most this many words; larger
-// events run the same code on their slice of the global workspace.
-constexpr uint32_t kClusterSmemPixels = 23552;
-constexpr uint32_t kRadixCounters = 257 * (kClusterThreads / 32);  // radix_counters(kClusterThreads)
+// Events of at most this many words sum their integer charges in 32 bits
+// (15 * 4095 * 23552 < 2^32); larger ones use 64 bits.
+constexpr uint32_t kNarrowPixels = 23552;
 constexpr uint32_t kModOffStride = 33;  // per-event module offsets, n_modules + 1 <= 33
 
 // Per-track metadata word: n_hits (8 bits) | active (1 bit) << 8 |
@@ -30,6 +29,7 @@ constexpr uint32_t kTrkActive = 1u << 8;
 // event has at most n_e clusters and n_e / 3 tracks, so slices never overlap.
 struct Workspace {
   uint32_t* flag;            // [1] offsets invalid
+  uint32_t* queue;           // [4] work-queue counters of the persistent kernels
   uint32_t* ev_nclusters;    // [E]
   uint32_t* ev_modoff;       // [E * 33] cluster-id (= sorted position) offsets per module
   uint32_t* ev_ntracks_all;  // [E] tracks built (kept or not)
@@ -76,6 +76,7 @@ struct Par {
 
 struct Launch {
   uint64_t n_events, n_pixels;
+  uint32_t cluster_tier;  // words per event kept in shared memory by the clustering kernel
   const uint64_t* off;
   const uint32_t* pix;
   Geo geo;
@@ -89,14 +90,22 @@ uint64_t workspace_bytes(uint64_t E, uint64_t P);
 // carve a workspace; returns false if too small
 bool carve_workspace(void* base, uint64_t bytes, uint64_t E, uint64_t P, Workspace* ws);
 
-// kernels
+// kernels and their launchers (persistent grids; velo_capi.cu sizes them)
 __global__ void k_validate_offsets(Launch L);
-__global__ void k_cluster(Launch L);
-__global__ void k_track(Launch L);
 __global__ void k_scan(Launch L);
-__global__ void k_output(Launch L);
+int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s);
+int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s);
+int launch_output(const Launch& L, uint32_t grid, cudaStream_t s);
+uint32_t cluster_smem_bytes(int nt, uint32_t tier);
+uint32_t cluster_max_tier(int nt);
+int cluster_blocks_per_sm(int nt, uint32_t tier);
+int track_blocks_per_sm(int nt);
+int output_blocks_per_sm();
 
-uint32_t cluster_smem_bytes();
-uint32_t track_smem_bytes();
+// host helpers (velo_capi.cu): raise a kernel's dynamic shared-memory limit
+// once per device (slot = a small id per kernel instance; occupancy with
+// slot < 0 leaves the limit alone), resident CTAs per SM
+bool set_max_smem_once(const void* func, int slot);
+int occupancy(const void* func, int threads, uint32_t smem, int slot);
 
 }  // namespace velo

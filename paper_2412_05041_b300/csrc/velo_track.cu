@@ -21,9 +21,9 @@
 // chi2/ndf (or, in the learned form, scored by the ghost-rejection network on
 // tensor cores), and ranked canonically by its smallest cluster id.
 //
-// One CTA of 256 threads per event; the event's hits stay in the global
-// workspace (sorted by module, pseudo-angle key, id; L1/L2 resident), the
-// per-step claims and used flags too.
+// One CTA of NT threads (128 or 256) per event at a time, persistent;
+// the event's hits stay in the global workspace (sorted by module,
+// pseudo-angle key, id; L1/L2 resident), the per-step claims and used flags too.
 #include "velo_device.cuh"
 #include "velo_fit.cuh"
 #include "velo_internal.cuh"
@@ -42,17 +42,25 @@ struct SeedArrays {
   unsigned long long best[kSeedChunk]; // smallest (bits(s), id0, id2) key of each middle hit
 };
 
+template <int NT>
 struct TrackSmem {
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   uint32_t tmp[64];
   unsigned long long tmp64[64];
+  uint32_t next;  // event taken from the work queue
   MlpWeights mlp;
   union {                                   // seeding (module loop) and scoring (fit phase) never overlap
     SeedArrays sd;
-    MlpTiles tiles[kTrackThreads / 32];
+    MlpTiles tiles[NT / 32];
   };
 };
+
+// the caller's output buffers hold the batch (capacity 0 = as velo_query_sizes)
+__device__ __forceinline__ bool output_fits(const velo_output_t& o, uint64_t nc, uint64_t nt, uint64_t nh) {
+  return (!o.cap_clusters || nc <= o.cap_clusters) && (!o.cap_tracks || nt <= o.cap_tracks) &&
+         (!o.cap_track_hits || nh <= o.cap_track_hits);
+}
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
 
@@ -92,13 +100,9 @@ __device__ __forceinline__ float cut_chi2ndf(uint32_t n, const float* st, float 
 
 }  // namespace
 
-uint32_t track_smem_bytes() { return (uint32_t)sizeof(TrackSmem); }
-
-__global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
-  constexpr int NT = kTrackThreads;
-  __shared__ TrackSmem S;
+template <int NT>
+__device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, TrackSmem<NT>& S) {
   const Workspace& W = L.ws;
-  const uint64_t e = blockIdx.x;
   const uint32_t tid = threadIdx.x;
   const Par& P = L.par;
   const uint32_t M = L.geo.n_modules;
@@ -139,7 +143,6 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
     used[i] = 0;
     first_of[i] = kNone;
   }
-  if (P.use_mlp) mlp_load(P.mlp, S.mlp, tid, NT);
   __syncthreads();
 
   uint32_t n_tr = 0;
@@ -390,14 +393,27 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(Launch L) {
   }
 }
 
+// Persistent: CTAs take events from the work queue until it is empty.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_track(Launch L) {
+  __shared__ TrackSmem<NT> S;
+  if (L.par.use_mlp) mlp_load(L.par.mlp, S.mlp, threadIdx.x, NT);  // network constants, once per CTA
+  for (;;) {
+    if (threadIdx.x == 0) S.next = atomicAdd(L.ws.queue + 1, 1u);
+    __syncthreads();
+    const uint32_t e = S.next;
+    __syncthreads();
+    if (e >= L.n_events) break;
+    track_one<NT>(L, e, S);
+    __syncthreads();
+  }
+}
+
 // Compaction: clusters and kept tracks of event e into the caller's CSR
 // arrays (offsets from k_scan); the states are recomputed by the same fit.
-__global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
+__device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, uint32_t* mod_off, float* mz) {
   constexpr int NT = kOutputThreads;
-  __shared__ uint32_t mod_off[kModOffStride];
-  __shared__ float mz[VELO_MAX_MODULES];
   const Workspace& W = L.ws;
-  const uint64_t e = blockIdx.x;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
   if (*(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK) return;
@@ -442,6 +458,23 @@ __global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
   }
 }
 
+__global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
+  __shared__ uint32_t mod_off[kModOffStride];
+  __shared__ float mz[VELO_MAX_MODULES];
+  __shared__ uint32_t next;
+  // nothing is written when the batch does not fit the caller's buffers
+  if (!output_fits(L.out, L.out.totals[0], L.out.totals[1], L.out.totals[2])) return;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(L.ws.queue + 2, 1u);
+    __syncthreads();
+    const uint32_t e = next;
+    __syncthreads();
+    if (e >= L.n_events) break;
+    output_one(L, e, mod_off, mz);
+    __syncthreads();
+  }
+}
+
 // One CTA: event offsets into the output CSR arrays and the batch totals.
 __global__ void __launch_bounds__(kScanThreads) k_scan(Launch L) {
   constexpr int NT = kScanThreads;
@@ -476,7 +509,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Launch L) {
   if (threadIdx.x == 0) {
     L.out.cluster_offsets[E] = rc;
     L.out.track_offsets[E] = rt;
-    L.out.track_hit_offsets[rt] = rh;
+    if (output_fits(L.out, rc, rt, rh)) L.out.track_hit_offsets[rt] = rh;
     L.out.totals[0] = rc;
     L.out.totals[1] = rt;
     L.out.totals[2] = rh;
@@ -495,12 +528,39 @@ __global__ void __launch_bounds__(kScanThreads) k_validate_offsets(Launch L) {
     bad |= (b < a) | (b - a >= (1ull << 30));
   }
   bad = __syncthreads_or(bad);
-  if (threadIdx.x == 0) *L.ws.flag = bad ? 1u : 0u;
+  if (threadIdx.x == 0) {
+    *L.ws.flag = bad ? 1u : 0u;
+    for (int q = 0; q < 4; ++q) L.ws.queue[q] = 0u;  // the persistent kernels' work queues
+  }
   if (bad) {
     for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.out.status[e] = VELO_EVT_BADWORD;
     if (L.out.pixel_cluster)
       for (uint64_t i = threadIdx.x; i < L.n_pixels; i += blockDim.x) L.out.pixel_cluster[i] = kNone;
   }
 }
+
+int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
+  switch (nt) {
+    case 128: k_track<128><<<grid, 128, 0, s>>>(L); break;
+    case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
+    default: return VELO_EINVAL;
+  }
+  return VELO_OK;
+}
+
+int track_blocks_per_sm(int nt) {
+  switch (nt) {
+    case 128: return occupancy(reinterpret_cast<const void*>(k_track<128>), 128, 0, -1);
+    case 256: return occupancy(reinterpret_cast<const void*>(k_track<256>), 256, 0, -1);
+    default: return 0;
+  }
+}
+
+int launch_output(const Launch& L, uint32_t grid, cudaStream_t s) {
+  k_output<<<grid, kOutputThreads, 0, s>>>(L);
+  return VELO_OK;
+}
+
+int output_blocks_per_sm() { return occupancy(reinterpret_cast<const void*>(k_output), kOutputThreads, 0, -1); }
 
 }  // namespace velo

@@ -1,0 +1,108 @@
+"""The batched form: persistent work-queue kernels over events of uneven
+occupancy, captured in one CUDA graph, block shapes chosen by the autotuner.
+Every block shape, the graph replay and the eager call give the same bytes,
+and sampled events equal the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2412_05041_b300 as velo
+import velogen
+from _compare import assert_same, to_numpy
+from paper_2412_05041_b300 import autotune
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    velo.build()
+    assert torch.cuda.is_available()
+
+
+def uneven_batch(n=300, seed=3):
+    """Pile-up 5.5 for 90 % of the events and 15 for 10 % (at random positions),
+    plus two heavy-ion-like events that exceed every shared-memory tier."""
+    b = velogen.generate(velogen.Config(seed=seed, n_events=n, heavy_frac=0.1, pv_mu_heavy=15.0))
+    hi = velogen.generate(velogen.Config(seed=11, n_events=2, hi_frac=1.0, hi_min_tracks=2000, hi_max_tracks=3000))
+    evs = [b.event(e) for e in range(n)]
+    evs.insert(n // 3, hi.event(0))
+    evs.insert(2 * n // 3, hi.event(1))
+    off = np.zeros(len(evs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(e) for e in evs])
+    return off, np.concatenate(evs).astype(np.uint32), b.geometry
+
+
+def dev(off, pix):
+    return (torch.from_numpy(off.view(np.int64)).cuda(), torch.from_numpy(pix.view(np.int32)).cuda())
+
+
+def test_every_block_shape_gives_the_same_bytes_and_the_oracle():
+    off, pix, geo = uneven_batch()
+    o, p = dev(off, pix)
+    ref = to_numpy(velo.reconstruct(o, p, geo, velo.default_params(), pixel_labels=True))
+    for t in autotune.candidates() + [velo.default_tuning(cluster_threads=1024, cluster_smem_pixels=4096),
+                                      velo.default_tuning(cluster_threads=512, cluster_smem_pixels=2048)]:
+        got = to_numpy(velo.reconstruct(o, p, geo, velo.default_params(), pixel_labels=True, tuning=t))
+        for k in ref:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{t.as_dict()} {k}")
+    sample = [0, 1, 100, 101, len(off) // 3 - 1, len(off) // 3, 2 * (len(off) - 1) // 3, len(off) - 2]
+    for e in sample:
+        one_off = np.array([0, off[e + 1] - off[e]], np.uint64)
+        r = oracle.reconstruct(one_off, pix[int(off[e]):int(off[e + 1])], geo, oracle.Params())
+        assert_same(ref, r, events=[e])
+
+
+def test_graph_replay_equals_eager_call():
+    off, pix, geo = uneven_batch(n=120, seed=7)
+    o, p = dev(off, pix)
+    eager = to_numpy(velo.reconstruct(o, p, geo, velo.default_params()))
+    G = velo.GraphReconstructor(o, p, geo, velo.default_params(), tuning=velo.default_tuning(track_threads=128))
+    for _ in range(2):
+        G.replay()
+        got = to_numpy(G.result())
+        for k in eager:
+            np.testing.assert_array_equal(got[k], eager[k], err_msg=k)
+    # a new batch of the same shape: the words of every event in another order
+    rng = np.random.default_rng(0)
+    pix2 = pix.copy()
+    for e in range(len(off) - 1):
+        a, b = int(off[e]), int(off[e + 1])
+        pix2[a:b] = pix2[a:b][rng.permutation(b - a)]
+    G.load(o, torch.from_numpy(pix2.view(np.int32)).cuda())
+    G.replay()
+    got = to_numpy(G.result())
+    for k in eager:
+        np.testing.assert_array_equal(got[k], eager[k], err_msg=k)
+
+
+def test_output_capacity_contract():
+    off, pix, geo = uneven_batch(n=60, seed=9)
+    o, p = dev(off, pix)
+    full = to_numpy(velo.reconstruct(o, p, geo, velo.default_params()))
+    nt = len(full["track_states"])
+    nc = len(full["cluster_x"])
+    R = velo.Reconstructor(geo, velo.default_params(), len(off) - 1, len(pix), cap_tracks=nt, cap_clusters=nc)
+    R.run(o, p)
+    got = to_numpy(R.result())
+    for k in full:
+        np.testing.assert_array_equal(got[k], full[k], err_msg=k)
+    small = velo.Reconstructor(geo, velo.default_params(), len(off) - 1, len(pix), cap_tracks=nt - 1)
+    small.track_states.fill_(7.0)
+    small.run(o, p)
+    with pytest.raises(velo.VeloError):
+        small.result()
+    assert int(small.totals[1]) == nt
+    assert bool((small.track_states == 7.0).all())  # nothing written
+
+
+def test_autotuner_picks_a_verified_shape(tmp_path, monkeypatch):
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tuning.json"))
+    off, pix, geo = uneven_batch(n=200, seed=5)
+    o, p = dev(off, pix)
+    best, table = autotune.tune(o, p, geo, velo.default_params(), reps=2)
+    assert len(table) == len(autotune.candidates())
+    assert best.as_dict() == min(table, key=lambda x: x[1])[0]
+    best2, _ = autotune.tune(o, p, geo, velo.default_params())  # from the cache
+    assert best2.as_dict() == best.as_dict()
