@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default block shapes instead of autotuned ones")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 100k-event uneven graph-launch measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the streaming (continuous batching) measurement")
     return ap.parse_args()
 
 
@@ -211,6 +214,78 @@ def cpu_baseline(cfg):
             "sample": f"first {n_done} of the 10k C2 events, all {cores} host threads, {t_total:.1f} s wall"}
 
 
+def run_batched(args, dev, vp):
+    """100k events of uneven occupancy (10 % at pile-up 15, at random positions)
+    in one CUDA-graph launch of the persistent kernels, block shapes autotuned
+    on a 5k-event sample of the same batch."""
+    import torch
+
+    import paper_2412_05041_b300 as velo
+    import velogen
+    from paper_2412_05041_b300 import autotune
+    cfg = velogen.C3
+    t0 = time.time()
+    b = velogen.generate(cfg)
+    gen_s = time.time() - t0
+    off = torch.from_numpy(b.offsets.view(np.int64)).to(dev)
+    pix = torch.from_numpy(b.pixels.view(np.int32)).to(dev)
+    E, P = b.n_events, pix.numel()
+    sizes = np.diff(b.offsets.astype(np.int64))
+    ns = 5000
+    best, table = autotune.tune(off[: ns + 1], pix[: int(b.offsets[ns])], b.geometry, vp, reps=2, use_cache=False)
+    G = velo.GraphReconstructor(off, pix, b.geometry, vp, tuning=best, cap_clusters=int(0.7 * P),
+                                cap_tracks=int(0.03 * P))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        G.replay()
+    torch.cuda.synchronize(dev)
+    K = max(3, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        G.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / K
+    res = G.result()
+    out = {"workload": "C3: 100k events, n_PV ~ Poisson(5.5) (90 %) / Poisson(15) (10 %), one CUDA-graph launch",
+           "value": E / (ms / 1000.0), "unit": UNIT, "ms_per_launch": ms, "replays": K, "events": E, "pixels": P,
+           "event_words_p50_p99_max": [int(np.percentile(sizes, 50)), int(np.percentile(sizes, 99)), int(sizes.max())],
+           "tracks": int(res["track_offsets"][-1]), "failed_events": int(res["n_failed"]), "tuning": best.as_dict(),
+           "tuning_table_ms": table, "generation_s": gen_s}
+    del G
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(args, dev, vp, tuning):
+    """Streaming requests of 64 events (pile-up 5.5 with 5 % heavy-ion-like events
+    of 2000-10000 tracks), 40 GB device-memory budget, 8 stream slots: first all
+    requests at once (throughput), then Poisson arrivals at 70 % of that rate
+    (latency from arrival to the result on the host)."""
+    import velogen
+    from paper_2412_05041_b300 import serve
+    n_req, per = 48, 64
+    b = velogen.generate(velogen.C5, n_events=n_req * per)
+    reqs = []
+    for i in range(n_req):
+        e0, e1 = i * per, (i + 1) * per
+        reqs.append(serve.Request(i, (b.offsets[e0:e1 + 1] - b.offsets[e0]).astype(np.uint64),
+                                  b.pixels[int(b.offsets[e0]):int(b.offsets[e1])].copy()))
+    S = serve.Server(b.geometry, vp, memory_budget=40 << 30, n_slots=8, device=dev, tuning=tuning)
+    S.run(reqs[:8])  # warm-up
+    sat = serve.Server(b.geometry, vp, memory_budget=40 << 30, n_slots=8, device=dev, tuning=tuning).run(reqs)
+    rate = 0.7 * sat["events_per_s"] / per
+    for r, t in zip(reqs, serve.poisson_arrivals(n_req, rate, seed=6)):
+        r.arrival, r.admitted, r.done = float(t), -1.0, -1.0
+    poi = serve.Server(b.geometry, vp, memory_budget=40 << 30, n_slots=8, device=dev, tuning=tuning).run(reqs)
+    heavy = int(sum(np.diff(b.offsets.astype(np.int64)) > 60000))
+    return {"workload": f"C5: {n_req} requests x {per} events, 5 % heavy-ion-like (2000-10000 tracks), "
+                        "40 GB budget, 8 streams", "heavy_events": heavy,
+            "saturated": sat, "poisson_at_70pct": poi, "value": poi["events_per_s"], "unit": UNIT,
+            "p50_latency_ms": poi["p50_latency_ms"], "p99_latency_ms": poi["p99_latency_ms"]}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -234,8 +309,14 @@ def run_ours(args):
     off = off_h.to(dev)
     pix = pix_h.to(dev)
     P = pix.numel()
-    R = velo.Reconstructor(b.geometry, vp, max_events=n_ev, max_pixels=P, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuning, tuning_table = None, None
+    if not args.no_autotune:
+        from paper_2412_05041_b300 import autotune
+        ns = min(3000, n_ev)
+        tuning, tuning_table = autotune.tune(off[: ns + 1], pix[: int(b.offsets[ns])], b.geometry, vp, reps=2,
+                                             use_cache=False)
+    R = velo.Reconstructor(b.geometry, vp, max_events=n_ev, max_pixels=P, device=dev, tuning=tuning)
 
     def barrier():
         if world > 1:
@@ -274,7 +355,7 @@ def run_ours(args):
     value = world * n_ev / (ms / 1000.0)
 
     # learned form: the same batch with the ghost-rejection network on tensor cores
-    learned = None
+    learned, RL = None, None
     model = os.path.join(ROOT, "paper_2412_05041_b300", "models", "ghost_mlp.bin")
     if os.path.exists(model) and not args.no_learned:
         from paper_2412_05041_b300 import mlp as vmlp
@@ -282,7 +363,7 @@ def run_ours(args):
         blob_dev = torch.from_numpy(blob).to(dev)
         lp = velo.default_params(**params_values(cfg.ms_theta))
         lp.use_mlp, lp.mlp_logit_min, lp.mlp = 1, thr, blob_dev.data_ptr()
-        RL = velo.Reconstructor(b.geometry, lp, max_events=n_ev, max_pixels=P, device=dev)
+        RL = velo.Reconstructor(b.geometry, lp, max_events=n_ev, max_pixels=P, device=dev, tuning=tuning)
         for _ in range(max(args.warmup, 0)):
             RL.run(off, pix, stream)
         l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -308,7 +389,7 @@ def run_ours(args):
     lat = []
     nb = min(1000, n_ev)
     off_b = torch.from_numpy(b.offsets[: nb + 1].view(np.int64)).to(dev)
-    Rb = velo.Reconstructor(b.geometry, vp, max_events=nb, max_pixels=int(b.offsets[nb]), device=dev)
+    Rb = velo.Reconstructor(b.geometry, vp, max_events=nb, max_pixels=int(b.offsets[nb]), device=dev, tuning=tuning)
     for _ in range(3):
         Rb.run(off_b, pix[: int(b.offsets[nb])], stream)
     for _ in range(30):
@@ -337,6 +418,22 @@ def run_ours(args):
             el = float(t.item())
         e2e = {"value": world * n_ev / el, "unit": UNIT, "h2d_bytes_per_step": int(8 * (n_ev + 1) + 4 * P),
                "d2h_bytes_per_step": int(H.bytes_out()), "ms_per_step": 1000 * el}
+
+    serving = None
+    if world == 1 and not args.no_serving:
+        try:
+            serving = run_serving(args, dev, vp, tuning)
+        except Exception as exc:
+            serving = {"error": repr(exc)[:300]}
+
+    batched = None
+    if world == 1 and not args.no_batched:
+        R = RL = Rb = None
+        torch.cuda.empty_cache()
+        try:
+            batched = run_batched(args, dev, vp)
+        except Exception as exc:  # report, do not lose the main line
+            batched = {"error": repr(exc)[:300]}
 
     if rank != 0:
         if world > 1:
@@ -373,6 +470,10 @@ def run_ours(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "learned": learned,
+        "tuning": None if tuning is None else tuning.as_dict(),
+        "tuning_table_ms": tuning_table,
+        "batched": batched,
+        "serving": serving,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfg)

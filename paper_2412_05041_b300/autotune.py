@@ -17,14 +17,13 @@ import torch
 from . import default_tuning, Tuning
 from .api import Reconstructor
 
+CTAS_PER_EVENT = 0xFFFFFFFF  # one CTA per event (VELO_CTAS_PER_EVENT)
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "velo_b300", "tuning.json")
 
 
 def candidates():
     out = []
-    for ct, tt, cps in itertools.product((1024, 512), (128, 256), (0, 1, 2)):
-        if ct == 512 and cps == 1:
-            continue
+    for ct, tt, cps in itertools.product((1024, 512), (128, 256), (0, 2, CTAS_PER_EVENT)):
         out.append(default_tuning(cluster_threads=ct, cluster_smem_pixels=0, track_threads=tt, ctas_per_sm=cps))
     return out
 

@@ -309,6 +309,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   const int sms = sm_count();
   if (sms <= 0) return VELO_ECUDA;
   auto grid = [&](int per_sm) -> uint32_t {  // persistent grid, never more CTAs than events
+    if (tu.ctas_per_sm == VELO_CTAS_PER_EVENT) return (uint32_t)E;  // one CTA per event, hardware-scheduled
     if (tu.ctas_per_sm) per_sm = per_sm > 0 ? (int)std::min<uint32_t>((uint32_t)per_sm, tu.ctas_per_sm) : 0;
     const uint64_t g = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)sms;
     return (uint32_t)std::min<uint64_t>(g, E);
