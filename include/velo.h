@@ -190,9 +190,10 @@ typedef struct velo_tuning {
   uint32_t cluster_smem_pixels;  /* words per event sorted in shared memory, 0 = the most that fits;
                                     larger events run on their global-memory slice */
   uint32_t track_threads;        /* 128 or 256 */
-  uint32_t ctas_per_sm;          /* grid of each event kernel: 0 = every CTA that fits, persistent;
-                                    k = at most k per SM, persistent; VELO_CTAS_PER_EVENT = one CTA
-                                    per event, scheduled by the hardware as CTAs finish */
+  uint32_t ctas_per_sm;          /* grid of the clustering and output kernels: 0 = every CTA that fits,
+                                    persistent; k = at most k per SM, persistent; VELO_CTAS_PER_EVENT =
+                                    one CTA per event, scheduled by the hardware as CTAs finish (the
+                                    tracking kernel always runs one CTA per event) */
 } velo_tuning_t;
 #define VELO_CTAS_PER_EVENT 0xFFFFFFFFu
 int velo_tuning_default(velo_tuning_t* t);

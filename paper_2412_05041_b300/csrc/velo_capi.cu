@@ -323,7 +323,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   if (E) rc = launch_cluster(L, (int)tu.cluster_threads, grid(cluster_blocks_per_sm((int)tu.cluster_threads, tier)), s);
   if (rc != VELO_OK) return rc;
   mark(1);
-  if (E) rc = launch_track(L, (int)tu.track_threads, grid(track_blocks_per_sm((int)tu.track_threads)), s);
+  if (E) rc = launch_track(L, (int)tu.track_threads, (uint32_t)E, s);  // one CTA per event
   if (rc != VELO_OK) return rc;
   mark(2);
   k_scan<<<1, kScanThreads, 0, s>>>(L);
