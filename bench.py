@@ -59,6 +59,26 @@ def dist_env():
     return rank, world, local
 
 
+def shard(rank: int, world: int, events_per_rank: int) -> tuple[int, int]:
+    """Events of one rank: a contiguous, disjoint range of the generator's event
+    stream (every event regenerates alone from its index), the same size on every
+    rank (weak scaling).  No collective is needed: events are independent."""
+    if not (0 <= rank < world):
+        raise ValueError("rank outside the world")
+    return rank * events_per_rank, events_per_rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (the step ends when every rank has finished)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def params_values(ms_theta):
     return dict(win_seed=0.04, win_fwd=0.04, max_slope=0.3, max_scatter_seed=0.01, max_scatter_fwd=0.02,
                 max_skipped=1, sigma_meas=0.0159, ms_theta=ms_theta, chi2ndf_max=10.0, chi2ndf_max_3hit=2.0)
@@ -302,7 +322,8 @@ def run_ours(args):
     velo.build()
     cfg = velogen.C2
     n_ev = args.events
-    b = velogen.generate(cfg, n_events=n_ev, first_event=rank * n_ev)
+    first, n_ev = shard(rank, world, n_ev)
+    b = velogen.generate(cfg, n_events=n_ev, first_event=first)
     vp = velo.default_params(**params_values(cfg.ms_theta))
     off_h = torch.from_numpy(b.offsets.view(np.int64)).pin_memory()
     pix_h = torch.from_numpy(b.pixels.view(np.int32)).pin_memory()
@@ -348,10 +369,7 @@ def run_ours(args):
     ms = t0.elapsed_time(t1) / K
     stage_ms = {s: float(np.mean([marks[k][i].elapsed_time(marks[k][i + 1]) for k in range(K)]))
                 for i, s in enumerate(STAGES)}
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     value = world * n_ev / (ms / 1000.0)
 
     # learned form: the same batch with the ghost-rejection network on tensor cores
@@ -412,10 +430,7 @@ def run_ours(args):
         for _ in range(ke):
             H.run(off_h, pix_h, stream)
         el = (time.perf_counter() - tt) / ke
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, world, dev)
         e2e = {"value": world * n_ev / el, "unit": UNIT, "h2d_bytes_per_step": int(8 * (n_ev + 1) + 4 * P),
                "d2h_bytes_per_step": int(H.bytes_out()), "ms_per_step": 1000 * el}
 
