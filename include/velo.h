@@ -220,14 +220,29 @@ int velo_result_view(const velo_result_t* result, velo_result_view_t* view);
 void velo_result_free(velo_result_t* result);
 
 /* Host-buffer form, for callers whose events sit in host memory: a context
- * owns device buffers for up to max_events / max_pixels (allocated once, by
- * velo_context_create).  velo_reconstruct_host copies the batch in, runs
- * velo_reconstruct_into, copies the results out into caller-owned HOST
- * buffers of capacities from velo_query_sizes, and synchronises `stream`
- * before it returns.  Only the used part of each output is copied back. */
+ * owns device buffers for up to max_events / max_pixels and its own streams
+ * (allocated once, by velo_context_create).  velo_reconstruct_host
+ * reconstructs a batch whose inputs and results live in HOST memory
+ * (results in caller-owned buffers of the capacities from velo_query_sizes,
+ * laid out exactly as velo_reconstruct_into's).  It cuts the batch into
+ * chunks of whole events, each reconstructed by velo_reconstruct_into in
+ * its own region of the context's buffers, so that the copies of one chunk
+ * overlap with the kernels of the others; the events are independent
+ * (Sec. "Data flow overview"), so the results do not depend on the
+ * chunking.  The chunks' offsets are moved to batch-wide values on the
+ * host.  Work starts after what `stream` holds at the call; the call
+ * returns once every result is in the host buffers.  Page-locked host
+ * buffers are needed for the overlap (pageable ones work, with the copies
+ * serialised).  Only the used part of each output is copied back.  Offsets
+ * that the device form rejects are passed to it unchanged, in one chunk, so
+ * every event then fails as there.  velo_context_set_pipeline sets the most
+ * chunks per call: 0 = automatic (about 16M pixel words per chunk, at most
+ * 8), 1 = one chunk (copy in, compute, copy out, no overlap), at most 64;
+ * VELO_EINVAL otherwise. */
 typedef struct velo_context velo_context_t;
 int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t** ctx);
 void velo_context_destroy(velo_context_t* ctx);
+int velo_context_set_pipeline(velo_context_t* ctx, uint32_t max_chunks);
 int velo_reconstruct_host(velo_context_t* ctx, const velo_events_t* host_events,
                           const velo_geometry_t* geometry, const velo_params_t* params,
                           const velo_output_t* host_out, void* stream);

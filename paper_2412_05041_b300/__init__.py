@@ -86,7 +86,7 @@ _lib = None
 EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "velo_reconstruct_into_marked",
            "velo_tuning_default", "velo_reconstruct_into_tuned", "velo_reconstruct",
            "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
-           "velo_reconstruct_host", "velo_reconstruct_static", "velo_mlp_infer", "velo_mlp_workspace_size",
+           "velo_context_set_pipeline", "velo_reconstruct_host", "velo_reconstruct_static", "velo_mlp_infer", "velo_mlp_workspace_size",
            "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_strerror", "velo_version")
 
 
@@ -112,6 +112,7 @@ def lib():
         L.velo_context_create.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(_P)]
         L.velo_context_destroy.argtypes = [_P]
         L.velo_context_destroy.restype = None
+        L.velo_context_set_pipeline.argtypes = [_P, ctypes.c_uint32]
         L.velo_reconstruct_host.argtypes = [_P, ctypes.POINTER(Events), ctypes.POINTER(Geometry),
                                             ctypes.POINTER(Params), ctypes.POINTER(Output), _P]
         L.velo_reconstruct_static.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Geometry),

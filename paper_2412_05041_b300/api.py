@@ -161,13 +161,17 @@ class GraphReconstructor(Reconstructor):
 
 class HostReconstructor:
     """Host-memory form (``velo_reconstruct_host``): a library context owns the
-    device buffers; inputs and outputs are pinned host tensors."""
+    device buffers; inputs and outputs are pinned host tensors.  A batch is cut
+    into up to `chunks` chunks of whole events (0 = the library's choice, 1 =
+    no overlap) whose copies overlap with the kernels of the others."""
 
-    def __init__(self, geometry, params=None, max_events: int = 1, max_pixels: int = 1, pixel_labels: bool = False):
+    def __init__(self, geometry, params=None, max_events: int = 1, max_pixels: int = 1, pixel_labels: bool = False,
+                 chunks: int = 0):
         self.geo = geometry_struct(geometry)
         self.params = params if params is not None else default_params()
         self.ctx = ctypes.c_void_p()
         check(lib().velo_context_create(max_events, max_pixels, ctypes.byref(self.ctx)), "velo_context_create")
+        self.set_chunks(chunks)
         s = query_sizes(max_events, max_pixels)
         E = max_events
 
@@ -187,6 +191,9 @@ class HostReconstructor:
                            _ptr(self.cluster_z), _ptr(self.pixel_cluster), _ptr(self.track_offsets),
                            _ptr(self.track_hit_offsets), _ptr(self.track_hits), _ptr(self.track_states),
                            _ptr(self.totals), None, 0, 0, 0)
+
+    def set_chunks(self, chunks: int) -> None:
+        check(lib().velo_context_set_pipeline(self.ctx, int(chunks)), "velo_context_set_pipeline")
 
     def __del__(self):
         if getattr(self, "ctx", None) and self.ctx.value:

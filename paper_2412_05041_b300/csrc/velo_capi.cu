@@ -203,15 +203,6 @@ struct velo_result {
   cudaStream_t stream;
 };
 
-struct velo_context {
-  uint64_t max_events, max_pixels;
-  velo_sizes_t sizes;
-  uint64_t* d_off;
-  uint32_t* d_pix;
-  velo_output_t d_out;
-  void* workspace;
-};
-
 extern "C" {
 
 int velo_version(void) { return 100; }
@@ -399,94 +390,5 @@ void velo_result_free(velo_result_t* r) {
   delete r;
 }
 
-int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t** ctx) {
-  if (!ctx) return VELO_EINVAL;
-  *ctx = nullptr;
-  velo_sizes_t sz;
-  if (velo_query_sizes(max_events, max_pixels, &sz) != VELO_OK) return VELO_EINVAL;
-  velo_context* c = new velo_context;
-  std::memset(c, 0, sizeof(*c));
-  c->max_events = max_events;
-  c->max_pixels = max_pixels;
-  c->sizes = sz;
-  bool ok = true;
-  auto alloc = [&](void** p, uint64_t bytes) {
-    if (cudaMalloc(p, bytes ? bytes : 256) != cudaSuccess) ok = false;
-  };
-  const uint64_t E = max_events;
-  alloc((void**)&c->d_off, 8 * (E + 1));
-  alloc((void**)&c->d_pix, 4 * max_pixels);
-  alloc((void**)&c->d_out.status, 4 * E);
-  alloc((void**)&c->d_out.cluster_offsets, 8 * (E + 1));
-  alloc((void**)&c->d_out.cluster_x, 4 * sz.cap_clusters);
-  alloc((void**)&c->d_out.cluster_y, 4 * sz.cap_clusters);
-  alloc((void**)&c->d_out.cluster_z, 4 * sz.cap_clusters);
-  alloc((void**)&c->d_out.pixel_cluster, 4 * max_pixels);
-  alloc((void**)&c->d_out.track_offsets, 8 * (E + 1));
-  alloc((void**)&c->d_out.track_hit_offsets, 8 * (sz.cap_tracks + 1));
-  alloc((void**)&c->d_out.track_hits, 4 * sz.cap_track_hits);
-  alloc((void**)&c->d_out.track_states, 4ull * VELO_STATE_STRIDE * (sz.cap_tracks ? sz.cap_tracks : 1));
-  alloc((void**)&c->d_out.totals, 8 * 4);
-  alloc((void**)&c->d_out.track_features, 4ull * VELO_N_FEATURES * (sz.cap_tracks ? sz.cap_tracks : 1));
-  alloc(&c->workspace, sz.workspace_bytes);
-  if (!ok) {
-    velo_context_destroy(c);
-    cudaGetLastError();
-    return VELO_ENOMEM;
-  }
-  *ctx = c;
-  return VELO_OK;
-}
-
-void velo_context_destroy(velo_context_t* c) {
-  if (!c) return;
-  void* ptrs[] = {c->d_off,           c->d_pix,           c->d_out.status,           c->d_out.cluster_offsets,
-                  c->d_out.cluster_x, c->d_out.cluster_y, c->d_out.cluster_z,        c->d_out.pixel_cluster,
-                  c->d_out.track_offsets, c->d_out.track_hit_offsets, c->d_out.track_hits, c->d_out.track_states,
-                  c->d_out.totals,    c->d_out.track_features, c->workspace};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  delete c;
-}
-
-int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo_geometry_t* geometry,
-                          const velo_params_t* params, const velo_output_t* ho, void* stream) {
-  if (!c || !ev || !ev->event_offsets || (ev->n_pixels && !ev->pixels)) return VELO_EINVAL;
-  if (!ho || !ho->status || !ho->cluster_offsets || !ho->track_offsets || !ho->track_hit_offsets || !ho->track_hits ||
-      !ho->track_states || !ho->totals)
-    return VELO_EINVAL;
-  if (ev->n_events > c->max_events || ev->n_pixels > c->max_pixels) return VELO_ECAPACITY;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const uint64_t E = ev->n_events, P = ev->n_pixels;
-  if (cudaMemcpyAsync(c->d_off, ev->event_offsets, 8 * (E + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return VELO_ECUDA;
-  if (P && cudaMemcpyAsync(c->d_pix, ev->pixels, 4 * P, cudaMemcpyHostToDevice, s) != cudaSuccess) return VELO_ECUDA;
-  velo_events_t dev = {E, P, c->d_off, c->d_pix};
-  velo_output_t dout = c->d_out;
-  if (!ho->pixel_cluster) dout.pixel_cluster = nullptr;
-  if (!ho->track_features) dout.track_features = nullptr;
-  int rc = velo_reconstruct_into(&dev, geometry, params, &dout, c->workspace, c->sizes.workspace_bytes, stream);
-  if (rc != VELO_OK) return rc;
-  bool ok = true;
-  auto d2h = [&](void* dst, const void* src, uint64_t bytes) {
-    if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ok = false;
-  };
-  d2h(ho->totals, dout.totals, 32);
-  d2h(ho->status, dout.status, 4 * E);
-  d2h(ho->cluster_offsets, dout.cluster_offsets, 8 * (E + 1));
-  d2h(ho->track_offsets, dout.track_offsets, 8 * (E + 1));
-  if (ho->pixel_cluster) d2h(ho->pixel_cluster, dout.pixel_cluster, 4 * P);
-  if (!ok || cudaStreamSynchronize(s) != cudaSuccess) return VELO_ECUDA;
-  const uint64_t nc = ho->totals[0], nt = ho->totals[1], nh = ho->totals[2];
-  if (ho->cluster_x) d2h(ho->cluster_x, dout.cluster_x, 4 * nc);
-  if (ho->cluster_y) d2h(ho->cluster_y, dout.cluster_y, 4 * nc);
-  if (ho->cluster_z) d2h(ho->cluster_z, dout.cluster_z, 4 * nc);
-  d2h(ho->track_hit_offsets, dout.track_hit_offsets, 8 * (nt + 1));
-  d2h(ho->track_hits, dout.track_hits, 4 * nh);
-  d2h(ho->track_states, dout.track_states, 4ull * VELO_STATE_STRIDE * nt);
-  if (ho->track_features) d2h(ho->track_features, dout.track_features, 4ull * VELO_N_FEATURES * nt);
-  if (!ok || cudaStreamSynchronize(s) != cudaSuccess) return VELO_ECUDA;
-  return VELO_OK;
-}
 
 }  // extern "C"

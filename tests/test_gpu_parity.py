@@ -180,6 +180,50 @@ def test_host_buffer_entry_point():
     assert_same(g2, oracle.reconstruct(b2.offsets, b2.pixels, b2.geometry, op0))
 
 
+def _host(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a).view(dt)).pin_memory()
+
+
+def test_host_form_chunks_agree_with_oracle():
+    """The pipelined host form cuts a batch into chunks of whole events; the
+    results (offsets moved to batch-wide values) must not depend on the cut."""
+    b = velogen.generate(velogen.C2, n_events=150, first_event=4000)
+    vp, op = params(5e-4)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    H = velo.HostReconstructor(b.geometry, vp, max_events=200, max_pixels=len(b.pixels), pixel_labels=True)
+    off, pix = _host(b.offsets, np.int64), _host(b.pixels, np.int32)
+    for chunks in (1, 2, 3, 7, 64, 0):
+        H.set_chunks(chunks)
+        g = H.run(off, pix)
+        assert_same(g, r)
+        assert_labels(g["pixel_cluster"].numpy(), r["pixel_cluster"], b.offsets, b.offsets)
+    # empty events, bad words and an overflowing module among good events, cut into chunks
+    offsets, pixels = edge_batch()
+    geo = velogen.Geometry()
+    re = oracle.reconstruct(offsets, pixels, geo, op)
+    He = velo.HostReconstructor(geo, vp, max_events=len(offsets) - 1, max_pixels=len(pixels), pixel_labels=True,
+                                chunks=4)
+    ge = He.run(_host(offsets, np.int64), _host(pixels, np.int32))
+    assert_same(ge, re)
+    assert_labels(ge["pixel_cluster"].numpy(), re["pixel_cluster"], offsets, offsets)
+    assert ge["n_failed"] == 2
+
+
+def test_host_form_bad_offsets_and_empty_batch():
+    b = velogen.generate(velogen.C2, n_events=6)
+    off = b.offsets.copy()
+    off[2], off[3] = off[3], off[2]  # not monotone: every event fails, as in the device form
+    vp, _ = params(5e-4)
+    H = velo.HostReconstructor(b.geometry, vp, max_events=6, max_pixels=len(b.pixels), pixel_labels=True, chunks=3)
+    g = to_numpy(H.run(_host(off, np.int64), _host(b.pixels, np.int32)))
+    assert (g["status"] == velo.EVT_BADWORD).all()
+    assert g["n_failed"] == 6 and len(g["cluster_x"]) == 0 and len(g["track_states"]) == 0
+    assert (g["pixel_cluster"] == -1).all()
+    g0 = to_numpy(H.run(_host(np.zeros(1, np.uint64), np.int64), torch.zeros(0, dtype=torch.int32)))
+    assert len(g0["status"]) == 0 and list(g0["cluster_offsets"]) == [0] and list(g0["track_offsets"]) == [0]
+    assert g0["n_failed"] == 0 and len(g0["track_hit_offsets"]) == 1
+
+
 class _DevArray:
     """Zero-copy torch view of a raw device pointer (CUDA array interface)."""
 
