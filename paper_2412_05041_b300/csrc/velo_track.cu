@@ -126,6 +126,9 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   const uint32_t tid = threadIdx.x;
   const Par P = L.par;  // by value: kept in registers, not re-read through a reference
   const uint32_t M = L.geo.n_modules;
+  // largest |x| or |y| of a hit (centroids lie on the sensor: x0 .. x0 + pitch n_cols)
+  const float coord_max = fmaxf(fmaxf(fabsf(L.geo.x0), fabsf(L.geo.x0 + L.geo.pitch * (float)L.geo.n_cols)),
+                                fmaxf(fabsf(L.geo.y0), fabsf(L.geo.y0 + L.geo.pitch * (float)L.geo.n_rows)));
 
   if (*(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK) {
     if (tid == 0) {
@@ -249,6 +252,22 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const float alpha = dz12 / dz02, one_m_alpha = 1.0f - alpha;
     const bool seed_narrow = one_m_alpha > 0.05f && one_m_alpha < 0.95f;
     const float seed_reach = seed_narrow ? sqrtf(P.max_scatter_seed) / one_m_alpha * 1.01f + 1e-3f : 0.0f;
+    // Division-free pre-test of the scatter cut.  With the slope
+    // tx' = (x0 - x2) * rcp(dz02) instead of the exact quotient, every binary32
+    // step of the exact chain (quotient, product with dz12, two sums) moves by at
+    // most a few units of roundoff u = 2^-24 of its operands, so for a triplet
+    // that passes the exact cuts |dx' - dx|, |dy' - dy| <= 8u (S |dz12| + 2 X +
+    // 2 r + 1) =: err, with S the slope cut, X the largest |coordinate| of a hit
+    // on the sensor and r = sqrt(scatter cut); its dx'^2 + dy'^2 is then below
+    // (r + 1.5 err)^2 (with margin for the roundoff of the test itself).  A
+    // candidate is dropped early only when it exceeds that bound, i.e. when the
+    // exact arithmetic (still run for every other candidate) rejects it too, so
+    // the result is unchanged.
+    const float rcp_dz02 = __frcp_rn(dz02);
+    const float pre_err =
+        8.0f * 5.9604645e-8f * (P.max_slope * fabsf(dz12) + 2.0f * coord_max + 2.0f * sqrtf(P.max_scatter_seed) + 1.0f);
+    const float pre_r = sqrtf(P.max_scatter_seed) * (1.0f + 1e-6f) + 1.5f * pre_err;
+    const float pre_sc = pre_r * pre_r * (1.0f + 1e-5f);
     for (uint32_t cbase = mlo; cbase < mhi; cbase += kSeedChunk) {
       const uint32_t cn = min(kSeedChunk, mhi - cbase);
       constexpr int PER = kSeedChunk / NT;
@@ -305,7 +324,13 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           for (uint32_t q2 = s2; q2 < e2; ++q2) {
             if (dmod4(hk[q2], k1) > P.win_seed) continue;
             const float x2 = hx[q2], y2 = hy[q2];
-            const float tx = fd(fs(x0, x2), dz02), ty = fd(fs(y0, y2), dz02);
+            const float dx02 = fs(x0, x2), dy02 = fs(y0, y2);
+            {
+              const float ex = fs(fa(x2, fm(fm(dx02, rcp_dz02), dz12)), x1);
+              const float ey = fs(fa(y2, fm(fm(dy02, rcp_dz02), dz12)), y1);
+              if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) continue;
+            }
+            const float tx = fd(dx02, dz02), ty = fd(dy02, dz02);
             if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
             const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
             const float dx = fs(xp, x1), dy = fs(yp, y1);
@@ -431,8 +456,12 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 // One CTA per event, scheduled by the hardware as CTAs finish (this kernel
 // measured 20 % faster this way than as a persistent loop over a work queue: the
 // loop raised its register pressure), which balances uneven events as well.
+// The module loop is latency-bound, so resident warps pay more than
+// registers: 6 CTAs of 256 threads per SM (40 registers, a few bytes
+// spilled) measured 6 % faster than 5 (48 registers) and 8 % faster than 4
+// (64); at 7 (32 registers) the spills cost more than the extra CTA gains.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_track(Launch L) {
+__global__ void __launch_bounds__(NT, 1536 / NT) k_track(Launch L) {
   __shared__ TrackSmem<NT> S;
   if (L.par.use_mlp) mlp_load(L.par.mlp, S.mlp, threadIdx.x, NT);  // network constants
   track_one<NT>(L, blockIdx.x, S);
