@@ -96,42 +96,19 @@ __device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offse
 
 }  // namespace
 
-// The clustering of event e by one CTA of NT threads; `tier` = most words
-// kept in shared memory (the region holds 2 * tier words).
-template <int NT>
-__device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
-                                            const uint32_t tier) {
+// Phases 2-5 on the event's n pixel words in A (B: the second buffer), in
+// shared memory when PS (so that the sorts, the union-find and its atomics
+// compile to shared-memory instructions), else in the event's global slice.
+// Returns the cluster count, or kNone after failing the event.
+template <int NT, bool PS>
+__device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S,
+                                                 uint32_t* region, const uint32_t tier, const uint64_t p0,
+                                                 const uint32_t n) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
-
-  const bool offsets_ok = *(const volatile uint32_t*)W.flag == 0u;
-  uint64_t p0 = 0, p1 = 0;
-  if (offsets_ok) {
-    p0 = L.off[e];
-    p1 = L.off[e + 1];
-  }
-  const uint32_t n = (uint32_t)(p1 - p0);
-  if (tid == 0) S.flag = offsets_ok ? 0u : 1u;
-  if (tid < VELO_MAX_MODULES) S.mod_count[tid] = 0;
-  __syncthreads();
-
-  // 1. load + validate
-  const bool smem_tier = n <= tier;
-  uint32_t* A = smem_tier ? region : W.sa + p0;
-  uint32_t* B = smem_tier ? region + tier : W.sb + p0;
-  if (offsets_ok) {
-    for (uint32_t i = tid; i < n; i += NT) {
-      const uint32_t w = __ldg(L.pix + p0 + i);
-      if (!word_valid(w, L.geo)) S.flag = 1u;
-      A[i] = w;
-    }
-  }
-  __syncthreads();
-  if (S.flag) {
-    fail_event(L, e, VELO_EVT_BADWORD, offsets_ok, p0, n);
-    return;
-  }
+  uint32_t* A = PS ? region : W.sa + p0;
+  uint32_t* B = PS ? region + tier : W.sb + p0;
 
   // 2. sort by (module, row, col); 4 passes A->B->A->B->A
   radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
@@ -143,20 +120,68 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
                         [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 24; }, S.cnt, S.tmp);
 
-  // 3. union-find over 8-connected neighbours
-  for (uint32_t i = tid; i < n; i += NT) B[i] = i;
-  __syncthreads();
-  bool ok = true;
+  // 3. union-find over 8-connected neighbours.  Every earlier neighbour of
+  // word i has a key in [lo_all, k]: duplicates (k), the left neighbour
+  // (k - 1) and, if r > 0, the previous row's columns c-1 .. c+1 ([lo_k,
+  // hi_k]).  Those keys sit just before i in the sorted array, so a backward
+  // scan that stops below lo_all sees all of them; the words of a sparse
+  // event are a few rows apart, so it usually stops within a few steps.
+  // Pass a links every word, without atomics, to its smallest earlier
+  // neighbour (parent < child: a forest).  That is all a word needs when its
+  // earlier neighbours are connected among themselves: each edge between two
+  // of them is taken care of by the later one (by induction on the sorted
+  // position, every word ends in one component with all its earlier
+  // neighbours).  Among the left (L), up-left (UL), up (U) and up-right (UR)
+  // positions only L-UR and UL-UR are not adjacent, so the earlier
+  // neighbours fail to be connected only when UR is there without U but with
+  // L or UL (a duplicate of the word itself touches them all).  Those words,
+  // and words whose scan ran past 16 steps, are flagged in bit 31 of their
+  // word (never set in a valid word; every reader masks it) and, in pass b,
+  // united with each of their earlier neighbours (the full search past 16
+  // steps), linking the larger root under the smaller with atomicMin.  Every
+  // root of pass a has no earlier neighbour, and each union keeps the smaller
+  // root, so every component ends with its smallest sorted position, i.e. its
+  // smallest (module, row, col), as root -- whatever the thread order.
   for (uint32_t i = tid; i < n; i += NT) {
     const uint32_t k = A[i] & kKeyMask;
     const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
-    // Every earlier neighbour has a key in [lo_all, k]: duplicates (k), the
-    // left neighbour (k - 1) and, if r > 0, the previous row's columns c-1 ..
-    // c+1 ([lo_k, hi_k]).  Those keys sit just before i in the sorted array,
-    // so a backward scan that stops below lo_all sees all of them; the words
-    // of a sparse event are a few rows apart, so it usually stops within a
-    // few steps.  Past 16 steps the full search below takes over (unions are
-    // idempotent, so visiting a neighbour twice is harmless).
+    const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
+    const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
+    const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
+    bool done = false, dup = false, left = false, up_left = false, up = false, up_right = false;
+    uint32_t nb_min = i;
+    int64_t j = (int64_t)i - 1;
+    for (int steps = 0; steps < 16; ++steps, --j) {
+      if (j < 0) {
+        done = true;
+        break;
+      }
+      const uint32_t kj = A[j] & kKeyMask;
+      if (kj < lo_all) {
+        done = true;
+        break;
+      }
+      const bool is_dup = kj == k, is_left = c > 0u && kj == k - 1u;
+      const bool is_prev = r > 0u && kj >= lo_k && kj <= hi_k;
+      if (is_dup || is_left || is_prev) nb_min = (uint32_t)j;  // scanning down: the last one found is the smallest
+      dup |= is_dup;
+      left |= is_left;
+      if (is_prev) {
+        const uint32_t pc = kj & 2047u;  // previous-row column c-1, c or c+1
+        up_left |= pc + 1u == c;
+        up |= pc == c;
+        up_right |= pc == c + 1u;
+      }
+    }
+    B[i] = nb_min;
+    if (!done || (up_right && !up && (left || up_left) && !dup)) A[i] |= 0x80000000u;
+  }
+  __syncthreads();
+  bool ok = true;
+  for (uint32_t i = tid; i < n; i += NT) {
+    if (!(A[i] >> 31)) continue;
+    const uint32_t k = A[i] & kKeyMask;
+    const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
     const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
     const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
     const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
@@ -175,7 +200,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
       if (kj == k || (c > 0u && kj == k - 1u) || (r > 0u && kj >= lo_k && kj <= hi_k))
         ok &= uf_unite(B, i, (uint32_t)j);
     }
-    if (!done) {
+    if (!done) {  // past 16 steps (unions are idempotent: a neighbour seen twice is harmless)
       // duplicates of k and the left neighbour (k - 1) are the words just before i
       for (int64_t jj = (int64_t)i - 1; jj >= 0; --jj) {
         const uint32_t kj = A[jj] & kKeyMask;
@@ -192,7 +217,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   __syncthreads();
   if (S.flag) {
     fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
-    return;
+    return kNone;
   }
   for (uint32_t i = tid; i < n; i += NT) B[i] = uf_find(B, i);
   __syncthreads();
@@ -226,7 +251,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   __syncthreads();
   if (S.flag) {
     fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
-    return;
+    return kNone;
   }
 
   // optional per-word labels in input order
@@ -266,16 +291,28 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
     }
   }
   __syncthreads();
+  return n_clusters;
+}
 
+// Centroids, pseudo-angle keys and the hit sort of the event's n_clusters
+// clusters (charge sums in the workspace), through shared memory when HS.
+template <int NT, bool HS>
+__device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
+                                           const uint64_t p0, const uint32_t n, const uint32_t n_clusters) {
+  const Workspace& W = L.ws;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t M = L.geo.n_modules;
+  const bool narrow = n <= kNarrowPixels;
+  const unsigned long long* acc = W.acc + 3 * p0;
+  const uint32_t* acc32 = reinterpret_cast<const uint32_t*>(acc);
   // the pixel arrays are dead from here on: the hit sort reuses the region
   // (keys, values, their ping-pong copies and the cluster x, y: 6 words per cluster)
-  const bool hit_smem = 6u * n_clusters <= 2u * tier;
-  uint32_t* KA = hit_smem ? region : W.sa + p0;
-  uint32_t* KB = hit_smem ? region + n_clusters : W.sb + p0;
-  uint32_t* VA = hit_smem ? region + 2 * n_clusters : W.sc + p0;
-  uint32_t* VB = hit_smem ? region + 3 * n_clusters : W.sd + p0;
-  float* cx = hit_smem ? reinterpret_cast<float*>(region + 4 * n_clusters) : W.cl_x + p0;
-  float* cy = hit_smem ? reinterpret_cast<float*>(region + 5 * n_clusters) : W.cl_y + p0;
+  uint32_t* KA = HS ? region : W.sa + p0;
+  uint32_t* KB = HS ? region + n_clusters : W.sb + p0;
+  uint32_t* VA = HS ? region + 2 * n_clusters : W.sc + p0;
+  uint32_t* VB = HS ? region + 3 * n_clusters : W.sd + p0;
+  float* cx = HS ? reinterpret_cast<float*>(region + 4 * n_clusters) : W.cl_x + p0;
+  float* cy = HS ? reinterpret_cast<float*>(region + 5 * n_clusters) : W.cl_y + p0;
   const Geo& g = L.geo;
   for (uint32_t id = tid; id < n_clusters; id += NT) {
     float u, v;
@@ -325,6 +362,47 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
     W.ev_nclusters[e] = n_clusters;
     L.out.status[e] = VELO_EVT_OK;
   }
+}
+
+// The clustering of event e by one CTA of NT threads; `tier` = most words
+// kept in shared memory (the region holds 2 * tier words).
+template <int NT>
+__device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
+                                            const uint32_t tier) {
+  const Workspace& W = L.ws;
+  const uint32_t tid = threadIdx.x;
+
+  const bool offsets_ok = *(const volatile uint32_t*)W.flag == 0u;
+  uint64_t p0 = 0, p1 = 0;
+  if (offsets_ok) {
+    p0 = L.off[e];
+    p1 = L.off[e + 1];
+  }
+  const uint32_t n = (uint32_t)(p1 - p0);
+  if (tid == 0) S.flag = offsets_ok ? 0u : 1u;
+  if (tid < VELO_MAX_MODULES) S.mod_count[tid] = 0;
+  __syncthreads();
+
+  // 1. load + validate
+  const bool smem_tier = n <= tier;
+  uint32_t* A = smem_tier ? region : W.sa + p0;
+  if (offsets_ok) {
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t w = __ldg(L.pix + p0 + i);
+      if (!word_valid(w, L.geo)) S.flag = 1u;
+      A[i] = w;
+    }
+  }
+  __syncthreads();
+  if (S.flag) {
+    fail_event(L, e, VELO_EVT_BADWORD, offsets_ok, p0, n);
+    return;
+  }
+  const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n)
+                                        : pixel_phases<NT, false>(L, e, S, region, tier, p0, n);
+  if (n_clusters == kNone) return;
+  if (6u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters);
+  else hit_phases<NT, false>(L, e, S, region, p0, n, n_clusters);
 }
 
 // Persistent: every CTA takes events from the work queue until it is empty,

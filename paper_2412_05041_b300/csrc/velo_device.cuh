@@ -48,16 +48,31 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* tmp) {
 }
 
 // ---------------------------------------------------------------- radix sort
+// Lanes of the warp whose value d (< 512) equals this lane's: nine ballots,
+// one per bit (on this GPU cheaper than the match instruction).
+__device__ __forceinline__ uint32_t warp_peers9(uint32_t d) {
+  uint32_t m = kFull;
+#pragma unroll
+  for (int bit = 0; bit < 9; ++bit) {
+    const uint32_t set = (d >> bit) & 1u;
+    const uint32_t bb = __ballot_sync(kFull, set);
+    m &= set ? bb : ~bb;
+  }
+  return m;
+}
+
 // One stable LSD pass of a block-wide radix sort with 8-bit digits.
 // The n elements are cut into one contiguous chunk per warp; every warp
 // histograms its chunk into its own row of cnt (NW rows of 257 counters in
-// shared memory: the pad word makes both the per-warp access, lanes on
-// different digits, and the scan's access, one digit across warps, hit 32
-// different banks), one exclusive scan in (digit, warp) order gives each
-// (digit, warp) its first output slot, and every warp then scatters its chunk
-// in index order (rank among equal digits from __match_any_sync), so equal
-// digits keep their relative order.  a/b (and va/vb) may live in shared or
-// global memory.  cnt: radix_counters(NT) words.
+// shared memory, shared atomics; the pad word makes both the per-warp
+// access, lanes on different digits, and the scan's access, one digit across
+// warps, hit 32 different banks), one exclusive scan in (digit, warp) order
+// gives each (digit, warp) its first output slot, and every warp then
+// scatters its chunk in index order: among the lanes of one step with equal
+// digits the lowest lane reads and advances the digit's slot and broadcasts
+// it, and each lane adds its rank among those lanes, so equal digits keep
+// their relative order.  a/b (and va/vb) may live in shared or global
+// memory.  cnt: radix_counters(NT) words.
 constexpr uint32_t kRadixRow = 257;  // 256 digit counters + 1 pad word per warp
 __host__ __device__ constexpr uint32_t radix_counters(int nt) { return kRadixRow * (uint32_t)(nt / 32); }
 
@@ -72,15 +87,7 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
   __syncthreads();
   const uint32_t chunk = (n + NW - 1) / NW;
   const uint32_t s = min(n, w * chunk), e = min(n, s + chunk);
-  for (uint32_t base = s; base < e; base += 32) {
-    const uint32_t i = base + lane;
-    const bool valid = i < e;
-    uint32_t d = NB;
-    if (valid) d = digit(a[i], HAS_VAL ? va[i] : 0u);
-    const uint32_t peers = __match_any_sync(kFull, d);
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) row[d] += __popc(peers);
-    __syncwarp();
-  }
+  for (uint32_t i = s + lane; i < e; i += 32) atomicAdd(row + digit(a[i], HAS_VAL ? va[i] : 0u), 1u);
   __syncthreads();
   // exclusive scan of the 256*NW counters in (digit, warp) order; thread t
   // owns the 8 consecutive entries j = 8t .. 8t+7 (digit j / NW, warp j % NW)
@@ -112,15 +119,20 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
       if (HAS_VAL) v = va[i];
       d = digit(k, v);
     }
-    const uint32_t peers = __match_any_sync(kFull, d);
+    const uint32_t peers = warp_peers9(d);
+    const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+    uint32_t first = 0;
+    if (valid && lane == leader) {
+      first = row[d];
+      row[d] = first + __popc(peers);
+    }
+    first = __shfl_sync(kFull, first, leader);
     if (valid) {
-      const uint32_t pos = row[d] + __popc(peers & lt);
+      const uint32_t pos = first + __popc(peers & lt);
       b[pos] = k;
       if (HAS_VAL) vb[pos] = v;
     }
-    __syncwarp();
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) row[d] += __popc(peers);
-    __syncwarp();
+    __syncwarp();  // the counter updates are seen by the next step's leaders
   }
   __syncthreads();
 }
