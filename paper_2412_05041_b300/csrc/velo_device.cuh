@@ -210,4 +210,54 @@ __device__ __forceinline__ Ranges window_ranges(const float* keys, uint32_t lo, 
   return r;
 }
 
+// Bucketed index of one module's sorted keys, so that a search bisects one
+// bucket of a few hits instead of the module: bucket b holds the keys in
+// [b/16, (b+1)/16) (the last one also a key rounded up to 4), tab[b] is the
+// first module-local index of a key in bucket b or later, tab[64] the count.
+// Keys below v sit in v's bucket or earlier and keys of later buckets are
+// above v, so the first key >= v (or > v) lies in [tab[b], tab[b+1]] and the
+// answer is the one the bisection of the whole module gives.
+constexpr uint32_t kKeyBuckets = 64;
+__device__ __forceinline__ uint32_t key_bucket(float v) {
+  const float t = v * 16.0f;  // exact: a power of two
+  return t <= 0.0f ? 0u : (t >= 63.0f ? 63u : (uint32_t)t);
+}
+
+struct KeyIndex {
+  const float* keys;    // the event's sorted keys (positions index them)
+  uint32_t lo;          // first position of the module
+  const uint16_t* tab;  // kKeyBuckets + 1 module-local indices
+};
+
+__device__ __forceinline__ Ranges window_ranges(const KeyIndex& I, float k, float w) {
+  const float eps = 1e-5f;
+  const float a = k - w - eps, b = k + w + eps;
+  const uint32_t lo = I.lo, hi = I.lo + I.tab[kKeyBuckets];
+  auto lb = [&](float v) {
+    const uint32_t q = key_bucket(v);
+    return lo + lower_bound_by(I.tab[q], I.tab[q + 1], [&](uint32_t x) { return I.keys[lo + x] < v; });
+  };
+  auto ub = [&](float v) {
+    const uint32_t q = key_bucket(v);
+    return lo + lower_bound_by(I.tab[q], I.tab[q + 1], [&](uint32_t x) { return I.keys[lo + x] <= v; });
+  };
+  Ranges r;
+  if (a < 0.0f) {
+    r.a0 = lo;
+    r.a1 = ub(b);
+    r.b0 = max(lb(a + 4.0f), r.a1);
+    r.b1 = hi;
+  } else if (b >= 4.0f) {
+    r.a0 = lo;
+    r.a1 = ub(b - 4.0f);
+    r.b0 = max(lb(a), r.a1);
+    r.b1 = hi;
+  } else {
+    r.a0 = lb(a);
+    r.a1 = ub(b);
+    r.b0 = r.b1 = r.a1;
+  }
+  return r;
+}
+
 }  // namespace velo

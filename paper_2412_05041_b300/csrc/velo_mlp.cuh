@@ -10,7 +10,8 @@
 //   h2_j = relu(sum_k bf16(W2[j][k]) h1_k + b2_j)             float32
 //   logit = sum_j W3[j] h2_j + b3                             float32
 // The two hidden layers run as mma.sync.m16n8k16 bf16 -> f32 on one warp's 32
-// candidates (two 16-row tiles; layer 1 = 8 MMAs, layer 2 = 16 MMAs).  The
+// candidates (two 16-row tiles, one after the other through the same staging
+// tiles; layer 1 = 8 MMAs, layer 2 = 16 MMAs).  The
 // contraction is 32 x 12 x 32 per warp: a few hundred FLOPs per candidate, so
 // latency, not tensor throughput, bounds it and the warp-synchronous MMA is
 // the right size of tool; the accumulation order inside an MMA is the
@@ -37,10 +38,10 @@ struct MlpWeights {
   float b3;
 };
 
-// Per-warp staging tiles.
+// Per-warp staging tiles (one 16-candidate m-tile at a time).
 struct MlpTiles {
-  __nv_bfloat16 x[32 * kKPad];  // 32 candidates x 16 inputs
-  __nv_bfloat16 h[32 * kHid];   // 32 candidates x 32 first-layer outputs
+  __nv_bfloat16 x[16 * kKPad];  // 16 candidates x 16 inputs
+  __nv_bfloat16 h[16 * kHid];   // 16 candidates x 32 first-layer outputs
 };
 
 // blob (float32): mean[12], inv_std[12], W1[32][12], b1[32], W2[32][32], b2[32], W3[32], b3
@@ -86,43 +87,44 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
 // must call it (lanes without a candidate pass zeros and ignore the result).
 __device__ __forceinline__ float mlp_logit_warp(const float* f, const MlpWeights& W, MlpTiles& T) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-  for (int k = 0; k < kKPad; ++k)
-    T.x[lane * kKPad + k] =
-        __float2bfloat16_rn(k < kFeat ? __fmul_rn(__fsub_rn(f[k], W.mean[k]), W.istd[k]) : 0.0f);
-  __syncwarp();
-  // layer 1: rows = candidates (two m-tiles), cols = hidden units (four n-tiles), one k-step
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const __nv_bfloat16* xr0 = T.x + (mt * 16 + g) * kKPad;
-    const __nv_bfloat16* xr8 = T.x + (mt * 16 + g + 8) * kKPad;
-    const uint32_t a0 = pack_bf16(xr0[2 * t4], xr0[2 * t4 + 1]);
-    const uint32_t a1 = pack_bf16(xr8[2 * t4], xr8[2 * t4 + 1]);
-    const uint32_t a2 = pack_bf16(xr0[2 * t4 + 8], xr0[2 * t4 + 9]);
-    const uint32_t a3 = pack_bf16(xr8[2 * t4 + 8], xr8[2 * t4 + 9]);
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const __nv_bfloat16* wr = W.w1 + (nt * 8 + g) * kKPad;  // B[k][n] = W1[n][k]
-      const uint32_t b0 = pack_bf16(wr[2 * t4], wr[2 * t4 + 1]);
-      const uint32_t b1 = pack_bf16(wr[2 * t4 + 8], wr[2 * t4 + 9]);
-      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      mma_bf16(c, a0, a1, a2, a3, b0, b1);
-      const int col = nt * 8 + 2 * t4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int row = mt * 16 + g + (q >= 2 ? 8 : 0), cc = col + (q & 1);
-        const float a = __fadd_rn(c[q], W.b1[cc]);
-        T.h[row * kHid + cc] = __float2bfloat16_rn(a > 0.0f ? a : 0.0f);
-      }
-    }
-  }
-  __syncwarp();
-  // layer 2 (two k-steps) and layer 3 on the accumulators
   float part[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};  // [m-tile][row g / row g+8]
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const __nv_bfloat16* hr0 = T.h + (mt * 16 + g) * kHid;
-    const __nv_bfloat16* hr8 = T.h + (mt * 16 + g + 8) * kHid;
+  for (int mt = 0; mt < 2; ++mt) {  // candidates 16 mt .. 16 mt + 15 (lanes of that half)
+    if ((lane >> 4) == mt) {
+#pragma unroll
+      for (int k = 0; k < kKPad; ++k)
+        T.x[(lane & 15) * kKPad + k] =
+            __float2bfloat16_rn(k < kFeat ? __fmul_rn(__fsub_rn(f[k], W.mean[k]), W.istd[k]) : 0.0f);
+    }
+    __syncwarp();
+    // layer 1: rows = candidates, cols = hidden units (four n-tiles), one k-step
+    {
+      const __nv_bfloat16* xr0 = T.x + g * kKPad;
+      const __nv_bfloat16* xr8 = T.x + (g + 8) * kKPad;
+      const uint32_t a0 = pack_bf16(xr0[2 * t4], xr0[2 * t4 + 1]);
+      const uint32_t a1 = pack_bf16(xr8[2 * t4], xr8[2 * t4 + 1]);
+      const uint32_t a2 = pack_bf16(xr0[2 * t4 + 8], xr0[2 * t4 + 9]);
+      const uint32_t a3 = pack_bf16(xr8[2 * t4 + 8], xr8[2 * t4 + 9]);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const __nv_bfloat16* wr = W.w1 + (nt * 8 + g) * kKPad;  // B[k][n] = W1[n][k]
+        const uint32_t b0 = pack_bf16(wr[2 * t4], wr[2 * t4 + 1]);
+        const uint32_t b1 = pack_bf16(wr[2 * t4 + 8], wr[2 * t4 + 9]);
+        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        mma_bf16(c, a0, a1, a2, a3, b0, b1);
+        const int col = nt * 8 + 2 * t4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = g + (q >= 2 ? 8 : 0), cc = col + (q & 1);
+          const float a = __fadd_rn(c[q], W.b1[cc]);
+          T.h[row * kHid + cc] = __float2bfloat16_rn(a > 0.0f ? a : 0.0f);
+        }
+      }
+    }
+    __syncwarp();
+    // layer 2 (two k-steps) and layer 3 on the accumulators
+    const __nv_bfloat16* hr0 = T.h + g * kHid;
+    const __nv_bfloat16* hr8 = T.h + (g + 8) * kHid;
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -147,6 +149,7 @@ __device__ __forceinline__ float mlp_logit_warp(const float* f, const MlpWeights
         part[mt][q >> 1] = __fadd_rn(part[mt][q >> 1], __fmul_rn(W.w3[cc], h2));
       }
     }
+    __syncwarp();  // the tiles are rewritten for the next m-tile
   }
   // sum the four lanes of a group (each holds 8 of the 32 hidden units of its rows)
 #pragma unroll

@@ -36,14 +36,23 @@ namespace {
 constexpr uint32_t kSeedChunk = 512;  // middle hits per seeding chunk (a multiple of the block size)
 
 struct SeedArrays {
-  uint4 r0[kSeedChunk];                // h0 window (two index ranges) of each middle hit
-  uint4 r2[kSeedChunk];                // h2 window
+  uint2 r0[kSeedChunk];                // h0 window: two module-local index ranges, 16-bit ends packed
+  uint2 r2[kSeedChunk];                // h2 window
   uint32_t ioff[kSeedChunk];           // first work item of each middle hit
   unsigned long long best[kSeedChunk]; // smallest (bits(s), id0, id2) key of each middle hit
 };
 
+// module-local ranges (< 2^16: a module holds at most VELO_MAX_MODULE_CLUSTERS hits)
+__device__ __forceinline__ uint2 pack_ranges(const Ranges& r, uint32_t lo) {
+  return make_uint2((r.a0 - lo) | (r.a1 - lo) << 16, (r.b0 - lo) | (r.b1 - lo) << 16);
+}
+__device__ __forceinline__ Ranges unpack_ranges(uint2 v, uint32_t lo) {
+  return Ranges{lo + (v.x & 0xFFFFu), lo + (v.x >> 16), lo + (v.y & 0xFFFFu), lo + (v.y >> 16)};
+}
+
 template <int NT>
 struct TrackSmem {
+  uint16_t ktab[3][kKeyBuckets + 1];  // bucketed key index of the modules a step reads, module j in j % 3
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   uint32_t tmp[64];
@@ -104,13 +113,13 @@ constexpr uint32_t kNarrowAbove = 16;
 // the window `win`, the ranges around the point's own key replace
 // the window's; the exact window and cut tests still run on every candidate,
 // so only hits that would fail them are skipped.
-__device__ __forceinline__ Ranges narrowed_ranges(const float* keys, uint32_t lo, uint32_t hi, float win,
-                                                  const Ranges& wide, float xc, float yc, float reach) {
+__device__ __forceinline__ Ranges narrowed_ranges(const KeyIndex& I, float win, const Ranges& wide, float xc, float yc,
+                                                  float reach) {
   const float r = sqrtf(xc * xc + yc * yc);
   if (!(r > 2.0f * reach)) return wide;
   const float half = 1.5708f * reach / r * 1.01f + 1e-4f;
   if (!(half < win)) return wide;
-  return window_ranges(keys, lo, hi, pseudo_angle(xc, yc), half);
+  return window_ranges(I, pseudo_angle(xc, yc), half);
 }
 
 // chi2/ndf of the cut: straight-line chi2 without scattering, Kalman chi2 with it
@@ -166,10 +175,28 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     used[i] = 0;
     first_of[i] = kNone;
   }
+  __syncthreads();  // mod_off
+  // bucketed key index of module j into slot j % 3: entries past the last
+  // bucket hold the count, every hit fills the buckets from its predecessor's
+  // (exclusive) to its own
+  auto index_module = [&](uint32_t j) {
+    const uint32_t lo = S.mod_off[j], n = S.mod_off[j + 1] - lo;
+    uint16_t* tab = S.ktab[j % 3u];
+    for (uint32_t q = tid; q <= kKeyBuckets; q += NT) tab[q] = (uint16_t)n;
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t b = key_bucket(hk[lo + i]), b0 = i ? key_bucket(hk[lo + i - 1]) + 1u : 0u;
+      for (uint32_t q = b0; q <= b; ++q) tab[q] = (uint16_t)i;
+    }
+  };
+  index_module(M - 1);
+  __syncthreads();
+  index_module(M - 2);
   __syncthreads();
 
   uint32_t n_tr = 0;
   for (int m = (int)M - 2; m >= 0; --m) {
+    if (m >= 1) index_module((uint32_t)m - 1u);  // its slot held module m + 2, done with at step m + 1
     const uint32_t clo = S.mod_off[m > 0 ? m - 1 : 0], chi = S.mod_off[min((uint32_t)m + 2u, M)];
     for (uint32_t pos = clo + tid; pos < chi; pos += NT) claim[pos] = ~0ull;
     __syncthreads();
@@ -194,9 +221,9 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           const float tx = fd(fs(xa, xb), dzab), ty = fd(fs(ya, yb), dzab);
           const float dzm = fs(zm, za);
           const float xp = fa(xa, fm(tx, dzm)), yp = fa(ya, fm(ty, dzm));
-          Ranges R = window_ranges(hk, mlo, mhi, ka, P.win_fwd);
-          if ((R.a1 - R.a0) + (R.b1 - R.b0) > kNarrowAbove)
-            R = narrowed_ranges(hk, mlo, mhi, P.win_fwd, R, xp, yp, fwd_reach);
+          const KeyIndex Im{hk, mlo, S.ktab[m % 3]};
+          Ranges R = window_ranges(Im, ka, P.win_fwd);
+          if ((R.a1 - R.a0) + (R.b1 - R.b0) > kNarrowAbove) R = narrowed_ranges(Im, P.win_fwd, R, xp, yp, fwd_reach);
           unsigned long long best = ~0ull;
           for (int part = 0; part < 2; ++part) {
             const uint32_t s = part ? R.b0 : R.a0, en = part ? R.b1 : R.a1;
@@ -281,10 +308,9 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           S.sd.best[i] = ~0ull;
           if (!used[p1]) {
             const float k1 = hk[p1];
-            const Ranges R0 = window_ranges(hk, lo0, hi0, k1, P.win_seed);
-            S.sd.r0[i] = make_uint4(R0.a0, R0.a1, R0.b0, R0.b1);
-            const Ranges R2 = window_ranges(hk, lo2, hi2, k1, P.win_seed);
-            S.sd.r2[i] = make_uint4(R2.a0, R2.a1, R2.b0, R2.b1);
+            const Ranges R0 = window_ranges(KeyIndex{hk, lo0, S.ktab[(m + 1) % 3]}, k1, P.win_seed);
+            S.sd.r0[i] = pack_ranges(R0, lo0);
+            S.sd.r2[i] = pack_ranges(window_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, k1, P.win_seed), lo2);
             c = (R0.a1 - R0.a0) + (R0.b1 - R0.b0);
           }
         }
@@ -305,18 +331,17 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         // share the offset of the next one, so that i owns item j)
         const uint32_t i = lower_bound_by(0u, cn, [&](uint32_t x) { return S.sd.ioff[x] <= j; }) - 1u;
         const uint32_t p1 = cbase + i;
-        const uint4 R0 = S.sd.r0[i];
-        const uint32_t kk = j - S.sd.ioff[i], na = R0.y - R0.x;
-        const uint32_t q0 = kk < na ? R0.x + kk : R0.z + (kk - na);
+        const Ranges R0 = unpack_ranges(S.sd.r0[i], lo0);
+        const uint32_t kk = j - S.sd.ioff[i], na = R0.a1 - R0.a0;
+        const uint32_t q0 = kk < na ? R0.a0 + kk : R0.b0 + (kk - na);
         if (used[q0]) continue;
         const float k1 = hk[p1];
         if (dmod4(hk[q0], k1) > P.win_seed) continue;
         const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
         const unsigned long long lid0 = hid[q0] - lo0;
-        const uint4 R2w = S.sd.r2[i];
-        Ranges R2{R2w.x, R2w.y, R2w.z, R2w.w};
+        Ranges R2 = unpack_ranges(S.sd.r2[i], lo2);
         if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
-          R2 = narrowed_ranges(hk, lo2, hi2, P.win_seed, R2, (x1 - alpha * x0) / one_m_alpha,
+          R2 = narrowed_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2, (x1 - alpha * x0) / one_m_alpha,
                                (y1 - alpha * y0) / one_m_alpha, seed_reach);
         unsigned long long best = ~0ull;
         for (int part2 = 0; part2 < 2; ++part2) {
