@@ -8,15 +8,17 @@
 //   2. stable block radix sort by the 27-bit (module, row, col) key
 //      (4 passes of 8 bits) in shared memory;
 //   3. union-find over 8-connected neighbours found in the sorted array
-//      (the left neighbour and duplicates sit just before a word, the
-//      previous row by binary search); a union links the larger root under
-//      the smaller with atomicMin, so every root ends as the smallest sorted
-//      position of its component, i.e. its smallest (module, row, col);
+//      (they sit just before a word): every word links to its smallest
+//      earlier neighbour, and the few whose earlier neighbours are not
+//      adjacent to one another unite with atomicMin, so every root ends as
+//      the smallest sorted position of its component, i.e. its smallest
+//      (module, row, col);
 //   4. cluster id = exclusive scan of root flags (canonical, order-free);
 //   5. integer charge sums per cluster with atomics (exact, so the order of
 //      the additions does not matter) and the binary32 centroid;
 //   6. pseudo-angle key and a stable block radix sort of the hits by
-//      (module, key, id): 4 passes over the key bits + 1 over the module.
+//      (module, key, id): 3 passes over (module, 19-bit fixed-point key),
+//      then the rare runs of equal fixed-point keys by insertion.
 // Events larger than the shared-memory tier run the same code on their
 // slice of the global workspace (generic pointers).
 #include "velo_device.cuh"
@@ -66,6 +68,13 @@ __device__ __forceinline__ bool uf_unite(uint32_t* parent, uint32_t a, uint32_t 
     a = old;
   }
   return false;
+}
+
+// 19-bit fixed-point value of a pseudo-angle key in [0, 4] (a key can round
+// up to 4): never decreases as the key grows (scaling by 2^17 is exact).
+__device__ __forceinline__ uint32_t hit_key_fixed(float key) {
+  const float t = key * 131072.0f;
+  return t >= 524287.0f ? 524287u : (uint32_t)t;
 }
 
 __device__ __forceinline__ bool word_valid(uint32_t w, const Geo& g) {
@@ -306,14 +315,17 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   const unsigned long long* acc = W.acc + 3 * p0;
   const uint32_t* acc32 = reinterpret_cast<const uint32_t*>(acc);
   // the pixel arrays are dead from here on: the hit sort reuses the region
-  // (keys, values, their ping-pong copies and the cluster x, y: 6 words per cluster)
+  // (sort keys, values, their ping-pong copies, the cluster x, y and
+  // pseudo-angle key: 7 words per cluster)
   uint32_t* KA = HS ? region : W.sa + p0;
   uint32_t* KB = HS ? region + n_clusters : W.sb + p0;
   uint32_t* VA = HS ? region + 2 * n_clusters : W.sc + p0;
   uint32_t* VB = HS ? region + 3 * n_clusters : W.sd + p0;
   float* cx = HS ? reinterpret_cast<float*>(region + 4 * n_clusters) : W.cl_x + p0;
   float* cy = HS ? reinterpret_cast<float*>(region + 5 * n_clusters) : W.cl_y + p0;
+  float* ck = HS ? reinterpret_cast<float*>(region + 6 * n_clusters) : W.h_key + p0;
   const Geo& g = L.geo;
+  const uint32_t* mo = S.mod_off;
   for (uint32_t id = tid; id < n_clusters; id += NT) {
     float u, v;
     if (narrow) {
@@ -331,29 +343,51 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
     }
     const float x = __fadd_rn(g.x0, __fmul_rn(g.pitch, u));
     const float y = __fadd_rn(g.y0, __fmul_rn(g.pitch, v));
+    const float key = pseudo_angle(x, y);
     cx[id] = x;
     cy[id] = y;
-    KA[id] = __float_as_uint(pseudo_angle(x, y));
+    ck[id] = key;
+    KA[id] = module_of(mo, M, id) << 19 | hit_key_fixed(key);
     VA[id] = id;
   }
   __syncthreads();
 
-  // 6. hits sorted by (module, key, id): key bits LSD (ids enter ascending,
-  // so equal keys stay in id order), then a stable pass on the module.
+  // 6. hits sorted by (module, key, id).  The ids enter in ascending order,
+  // and three stable LSD passes sort them by (module, fixed-point key): the
+  // fixed-point value never decreases with the key, so only hits of one
+  // module with equal fixed-point keys can still be out of (key, id) order;
+  // those runs (rare: a few per event) are put in order by insertion.
   radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k & 255u; }, S.cnt, S.tmp);
   radix_pass<NT, true>(KB, KA, VB, VA, n_clusters, [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.cnt,
                        S.tmp);
-  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.cnt,
-                       S.tmp);
-  radix_pass<NT, true>(KB, KA, VB, VA, n_clusters, [](uint32_t k, uint32_t) { return k >> 24; }, S.cnt, S.tmp);
-  const uint32_t* mo = S.mod_off;
-  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters,
-                       [mo, M](uint32_t, uint32_t id) { return module_of(mo, M, id); }, S.cnt, S.tmp);
+  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k >> 16; }, S.cnt, S.tmp);
+  for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
+    const uint32_t c = KB[pos];
+    if ((pos > 0 && KB[pos - 1] == c) || pos + 1 >= n_clusters || KB[pos + 1] != c) continue;
+    uint32_t end = pos + 2;  // this thread owns the run [pos, end)
+    while (end < n_clusters && KB[end] == c) ++end;
+    for (uint32_t a = pos + 1; a < end; ++a) {
+      const uint32_t id = VB[a];
+      const unsigned long long kv = (unsigned long long)__float_as_uint(ck[id]) << 32 | id;
+      uint32_t b = a;
+      for (; b > pos; --b) {
+        const uint32_t o = VB[b - 1];
+        if (((unsigned long long)__float_as_uint(ck[o]) << 32 | o) <= kv) break;
+        VB[b] = o;
+      }
+      VB[b] = id;
+    }
+  }
+  __syncthreads();
+  // the keys in sorted order through KA (dead after the last pass): in the
+  // global tier ck is h_key itself, read by id
+  for (uint32_t pos = tid; pos < n_clusters; pos += NT) KA[pos] = __float_as_uint(ck[VB[pos]]);
+  __syncthreads();
   for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
     const uint32_t id = VB[pos];
     W.h_x[p0 + pos] = cx[id];
     W.h_y[p0 + pos] = cy[id];
-    W.h_key[p0 + pos] = __uint_as_float(KB[pos]);
+    W.h_key[p0 + pos] = __uint_as_float(KA[pos]);
     W.h_id[p0 + pos] = id;
     W.h_pos[p0 + id] = pos;
   }
@@ -401,7 +435,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n)
                                         : pixel_phases<NT, false>(L, e, S, region, tier, p0, n);
   if (n_clusters == kNone) return;
-  if (6u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters);
+  if (7u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters);
   else hit_phases<NT, false>(L, e, S, region, p0, n, n_clusters);
 }
 

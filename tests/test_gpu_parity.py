@@ -125,6 +125,28 @@ def test_edge_cases():
     assert g["n_failed"] == 2
 
 
+def test_equal_keys_order_by_id():
+    """Clusters on a diagonal of the sensor share one pseudo-angle exactly (0.5
+    above the beam, 2.5 below): the hits must come out in (module, key, id)
+    order, equal keys by cluster id, as in the oracle."""
+    words = []
+    for m in (4, 5, 9):
+        for i in range(60):
+            rc = 800 + 3 * i  # x = y > 0: key 0.5
+            words.append(_word(1 + i % 15, m, rc, rc))
+            rc = 100 + 3 * i  # x = y < 0: key 2.5
+            words.append(_word(2, m, rc, rc))
+    rng = np.random.default_rng(3)
+    words = np.array(words, np.uint32)[rng.permutation(len(words))]
+    offsets = np.array([0, len(words)], np.uint64)
+    vp, op = params(5e-4)
+    geo = velogen.Geometry()
+    g = gpu_run(offsets, words, geo, vp)
+    r = oracle.reconstruct(offsets, words, geo, op)
+    assert_same(g, r)
+    assert_labels(g["pixel_cluster"].cpu().numpy(), r["pixel_cluster"], offsets, offsets)
+
+
 def test_bad_offsets_fail_every_event():
     b = velogen.generate(velogen.C2, n_events=4)
     off = b.offsets.copy()
