@@ -48,12 +48,13 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* tmp) {
 }
 
 // ---------------------------------------------------------------- radix sort
-// Lanes of the warp whose value d (< 512) equals this lane's: nine ballots,
-// one per bit (on this GPU cheaper than the match instruction).
-__device__ __forceinline__ uint32_t warp_peers9(uint32_t d) {
+// Lanes of the warp whose value d (< 2^BITS) equals this lane's: one ballot
+// per bit (on this GPU cheaper than the match instruction).
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
   uint32_t m = kFull;
 #pragma unroll
-  for (int bit = 0; bit < 9; ++bit) {
+  for (int bit = 0; bit < BITS; ++bit) {
     const uint32_t set = (d >> bit) & 1u;
     const uint32_t bb = __ballot_sync(kFull, set);
     m &= set ? bb : ~bb;
@@ -119,7 +120,8 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
       if (HAS_VAL) v = va[i];
       d = digit(k, v);
     }
-    const uint32_t peers = warp_peers9(d);
+    // full steps (warp-uniform) have no idle lane, whose digit NB needs a ninth bit
+    const uint32_t peers = base + 32u <= e ? warp_peers<8>(d) : warp_peers<9>(d);
     const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
     uint32_t first = 0;
     if (valid && lane == leader) {
