@@ -56,12 +56,17 @@ struct TrackSmem {
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   uint32_t tmp[64];
+  SeedArrays sd;
+};
+
+constexpr int kFitThreads = 256;
+
+struct FitSmem {
+  uint32_t mod_off[kModOffStride];
+  float z[VELO_MAX_MODULES];
   unsigned long long tmp64[64];
   MlpWeights mlp;
-  union {                                   // seeding (module loop) and scoring (fit phase) never overlap
-    SeedArrays sd;
-    MlpTiles tiles[NT / 32];
-  };
+  MlpTiles tiles[kFitThreads / 32];
 };
 
 // the caller's output buffers hold the batch (capacity 0 = as velo_query_sizes)
@@ -419,12 +424,61 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     __syncthreads();
   }
 
+  if (tid == 0) W.ev_ntracks_all[e] = n_tr;
+}
+
+
+// One CTA per event, scheduled by the hardware as CTAs finish (this kernel
+// measured 20 % faster this way than as a persistent loop over a work queue: the
+// loop raised its register pressure), which balances uneven events as well.
+// The module loop is latency-bound, so resident warps pay more than
+// registers: with the fit in a kernel of its own (k_fit), 8 CTAs of 256
+// threads per SM (32 registers, a few bytes spilled) measured 8 % faster
+// than 6 (40 registers), which was 6 % faster than 5 and 8 % faster than 4.
+template <int NT>
+__global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
+  __shared__ TrackSmem<NT> S;
+  track_one<NT>(L, blockIdx.x, S);
+}
+
+// Fit, cut and canonical rank of the tracks of event e (one CTA per event):
+// every track is fitted (straight line + simplified Kalman), kept by its
+// chi2/ndf (or scored by the ghost-rejection network on tensor cores), and
+// the kept ones are ranked by their smallest cluster id.  A kernel of its
+// own, so that the module loop runs with fewer registers and more CTAs.
+__global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
+  __shared__ FitSmem S;
+  const Workspace& W = L.ws;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t e = blockIdx.x;
+  const Par P = L.par;
+  const uint32_t M = L.geo.n_modules;
+  if (P.use_mlp) mlp_load(P.mlp, S.mlp, tid, kFitThreads);  // network constants
+  if (*(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK) {
+    if (tid == 0) {
+      W.ev_ntracks[e] = 0;
+      W.ev_nhits[e] = 0;
+    }
+    return;
+  }
+  const uint64_t p0 = L.off[e];
+  const uint64_t tb = p0 / 3;
+  const uint32_t H = W.ev_nclusters[e];
+  const uint32_t n_tr = W.ev_ntracks_all[e];
+  if (tid < kModOffStride) S.mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
+  if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
+  __syncthreads();
+  const uint32_t* hid = W.h_id + p0;
+  uint32_t* first_of = W.sd + p0;
+  const uint32_t* meta = W.trk_meta + tb;
+  const uint32_t* ta = W.trk_a + tb;
+
   // ---- fit, cut, canonical rank (by smallest cluster id) of every track
   uint32_t* rank = W.trk_rank + tb;
   uint32_t* hoff = W.trk_hoff + tb;
   // every thread takes part in every round (the learned rule scores a warp's
   // 32 candidates with warp-wide tensor-core instructions)
-  for (uint32_t base = 0; base < n_tr; base += NT) {
+  for (uint32_t base = 0; base < n_tr; base += kFitThreads) {
     const uint32_t t = base + tid;
     const bool valid = t < n_tr;
     float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
@@ -455,7 +509,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   }
   __syncthreads();
   unsigned long long run = 0;
-  for (uint32_t base = 0; base < H; base += NT) {
+  for (uint32_t base = 0; base < H; base += kFitThreads) {
     const uint32_t id = base + tid;
     uint32_t t = kNone;
     unsigned long long v = 0;
@@ -464,7 +518,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       if (t != kNone) v = (1ull << 32) | (meta[t] & 255u);
     }
     unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(v, &tot, S.tmp64) + run;
+    const unsigned long long ex = block_exclusive_scan<kFitThreads, unsigned long long>(v, &tot, S.tmp64) + run;
     if (t != kNone) {
       rank[t] = (uint32_t)(ex >> 32);
       hoff[t] = (uint32_t)ex;
@@ -472,24 +526,9 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     run += tot;
   }
   if (tid == 0) {
-    W.ev_ntracks_all[e] = n_tr;
     W.ev_ntracks[e] = (uint32_t)(run >> 32);
     W.ev_nhits[e] = (uint32_t)run;
   }
-}
-
-// One CTA per event, scheduled by the hardware as CTAs finish (this kernel
-// measured 20 % faster this way than as a persistent loop over a work queue: the
-// loop raised its register pressure), which balances uneven events as well.
-// The module loop is latency-bound, so resident warps pay more than
-// registers: 6 CTAs of 256 threads per SM (40 registers, a few bytes
-// spilled) measured 6 % faster than 5 (48 registers) and 8 % faster than 4
-// (64); at 7 (32 registers) the spills cost more than the extra CTA gains.
-template <int NT>
-__global__ void __launch_bounds__(NT, 1536 / NT) k_track(Launch L) {
-  __shared__ TrackSmem<NT> S;
-  if (L.par.use_mlp) mlp_load(L.par.mlp, S.mlp, threadIdx.x, NT);  // network constants
-  track_one<NT>(L, blockIdx.x, S);
 }
 
 // Compaction: clusters and kept tracks of event e into the caller's CSR
@@ -628,6 +667,7 @@ int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
     default: return VELO_EINVAL;
   }
+  k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
 }
 
