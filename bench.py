@@ -493,7 +493,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (event sharding)"},
         "p50_batch_latency_ms": float(np.percentile(lat, 50)), "p99_batch_latency_ms": float(np.percentile(lat, 99)),
         "latency_batch_events": nb,
-        "gpu_launches": 6 * K,  # validate, cluster, track, fit, scan, output per step
+        "gpu_launches": 7 * K,  # validate, cluster, track, track (heavy events), fit, scan, output per step
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": e2e,

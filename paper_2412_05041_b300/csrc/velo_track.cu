@@ -33,13 +33,24 @@ namespace velo {
 
 namespace {
 
-constexpr uint32_t kSeedChunk = 512;  // middle hits per seeding chunk (a multiple of the block size)
+// middle hits per seeding chunk (a multiple of the block size)
+template <int NT>
+__host__ __device__ constexpr uint32_t seed_chunk() {
+  return NT > 512 ? (uint32_t)NT : 512u;
+}
 
+// Events with at least this many clusters (heavy-ion-like: some 2000 tracks
+// and more) are tracked by CTAs of kWideThreads threads, the others by the
+// tuned block size; a step of such an event keeps 1024 threads busy.
+constexpr uint32_t kWideClusters = 20000;
+constexpr int kWideThreads = 1024;
+
+template <uint32_t C>
 struct SeedArrays {
-  uint2 r0[kSeedChunk];                // h0 window: two module-local index ranges, 16-bit ends packed
-  uint2 r2[kSeedChunk];                // h2 window
-  uint32_t ioff[kSeedChunk];           // first work item of each middle hit
-  unsigned long long best[kSeedChunk]; // smallest (bits(s), id0, id2) key of each middle hit
+  uint2 r0[C];                // h0 window: two module-local index ranges, 16-bit ends packed
+  uint2 r2[C];                // h2 window
+  uint32_t ioff[C];           // first work item of each middle hit
+  unsigned long long best[C]; // smallest (bits(s), id0, id2) key of each middle hit
 };
 
 // module-local ranges (< 2^16: a module holds at most VELO_MAX_MODULE_CLUSTERS hits)
@@ -56,7 +67,7 @@ struct TrackSmem {
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   uint32_t tmp[64];
-  SeedArrays sd;
+  SeedArrays<seed_chunk<NT>()> sd;
 };
 
 constexpr int kFitThreads = 256;
@@ -134,7 +145,9 @@ __device__ __forceinline__ float cut_chi2ndf(uint32_t n, const float* st, float 
 
 }  // namespace
 
-template <int NT>
+// WIDE: this instance tracks the events of kWideClusters clusters or more
+// (and only those); the other instance every other event.
+template <int NT, bool WIDE>
 __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, TrackSmem<NT>& S) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
@@ -145,13 +158,14 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
                                 fmaxf(fabsf(L.geo.y0), fabsf(L.geo.y0 + L.geo.pitch * (float)L.geo.n_rows)));
 
   if (*(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK) {
-    if (tid == 0) {
+    if (!WIDE && tid == 0) {
       W.ev_ntracks_all[e] = 0;
       W.ev_ntracks[e] = 0;
       W.ev_nhits[e] = 0;
     }
     return;
   }
+  if ((W.ev_nclusters[e] >= kWideClusters) != WIDE) return;
   const uint64_t p0 = L.off[e];
   const uint64_t tb = p0 / 3;
   const uint32_t H = W.ev_nclusters[e];
@@ -271,7 +285,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 
     // ---- seeding with the middle hit on m.  The (h0, h2) pairs of all middle
     // hits are spread evenly over the block: one work item per (h1, h0
-    // candidate), each looping over h1's h2 window, in chunks of kSeedChunk
+    // candidate), each looping over h1's h2 window, in chunks of kChunk
     // middle hits; per h1 the smallest pair key wins (shared 64-bit atomicMin).
     const uint32_t lo0 = S.mod_off[m + 1], hi0 = S.mod_off[m + 2];
     const uint32_t lo2 = S.mod_off[m - 1], hi2 = mlo;
@@ -300,9 +314,10 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         8.0f * 5.9604645e-8f * (P.max_slope * fabsf(dz12) + 2.0f * coord_max + 2.0f * sqrtf(P.max_scatter_seed) + 1.0f);
     const float pre_r = sqrtf(P.max_scatter_seed) * (1.0f + 1e-6f) + 1.5f * pre_err;
     const float pre_sc = pre_r * pre_r * (1.0f + 1e-5f);
-    for (uint32_t cbase = mlo; cbase < mhi; cbase += kSeedChunk) {
-      const uint32_t cn = min(kSeedChunk, mhi - cbase);
-      constexpr int PER = kSeedChunk / NT;
+    constexpr uint32_t kChunk = seed_chunk<NT>();
+    for (uint32_t cbase = mlo; cbase < mhi; cbase += kChunk) {
+      const uint32_t cn = min(kChunk, mhi - cbase);
+      constexpr int PER = kChunk / NT;
       uint32_t cnt[PER], sum = 0;
 #pragma unroll
       for (int k = 0; k < PER; ++k) {  // thread tid owns middle hits PER*tid .. PER*tid+PER-1
@@ -438,7 +453,17 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 template <int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   __shared__ TrackSmem<NT> S;
-  track_one<NT>(L, blockIdx.x, S);
+  track_one<NT, false>(L, blockIdx.x, S);
+}
+
+// The heavy events: a small grid of kWideThreads-thread CTAs strides over
+// the batch and tracks the events of kWideClusters clusters or more.
+__global__ void __launch_bounds__(kWideThreads, 2048 / kWideThreads) k_track_wide(Launch L) {
+  __shared__ TrackSmem<kWideThreads> S;
+  for (uint64_t e = blockIdx.x; e < L.n_events; e += gridDim.x) {
+    track_one<kWideThreads, true>(L, e, S);
+    __syncthreads();  // shared memory is reused by the next event
+  }
 }
 
 // Fit, cut and canonical rank of the tracks of event e (one CTA per event):
@@ -667,6 +692,7 @@ int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
     default: return VELO_EINVAL;
   }
+  k_track_wide<<<std::min<uint32_t>(grid, 1024u), kWideThreads, 0, s>>>(L);
   k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
 }
