@@ -159,7 +159,7 @@ def measured_peaks():
 
 # host-only sources (the host-buffer pipeline, the static-scratch entry point)
 # change no kernel and no launch, so they do not invalidate a profile
-HOST_ONLY_SOURCES = ("velo_host.cu", "velo_static.cu")
+HOST_ONLY_SOURCES = ("velo_host.cu", "velo_static.cu", "velo_peak.cu")
 
 
 def kernel_source_hash():
@@ -186,6 +186,29 @@ def profiled_traffic(kernel: str):
     if not m_src or not m_b or m_src.group(1) != kernel_source_hash():
         return None
     return float(m_b.group(1))
+
+
+def profiled_metric(kernel: str, name: str):
+    """A metric of the committed ncu summary of `kernel` (current sources only)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_c2.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    m = re.search(r"\|\s*" + re.escape(name) + r"\s*\|\s*([0-9.eE+,-]+)\s*\|", txt)
+    if not m_src or not m or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1).replace(",", ""))
+
+
+def fp32_peak_tflops():
+    """The FP32 FMA rate of this GPU, measured by the library's microbenchmark."""
+    import ctypes
+
+    import paper_2412_05041_b300 as velo
+    v = ctypes.c_double(0.0)
+    velo.check(velo.lib().velo_measure_fp32_peak(ctypes.byref(v), None), "velo_measure_fp32_peak")
+    return v.value / 1e12
 
 
 # ------------------------------------------------------------------ arms
@@ -237,8 +260,14 @@ def cpu_baseline(cfg):
         t_total += time.perf_counter() - t0
         n_done += per
         first += per
+    # the same on one host thread
+    b1 = velogen.generate(cfg, n_events=48)
+    t0 = time.perf_counter()
+    oracle.reconstruct(b1.offsets, b1.pixels, b1.geometry, op, n_threads=1)
+    t1 = time.perf_counter() - t0
     return {"value": n_done / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n_done} of the 10k C2 events, all {cores} host threads, {t_total:.1f} s wall"}
+            "sample": f"first {n_done} of the 10k C2 events, all {cores} host threads, {t_total:.1f} s wall",
+            "one_thread": {"value": 48 / t1, "unit": UNIT, "sample": f"first 48 C2 events, 1 thread, {t1:.1f} s"}}
 
 
 def run_batched(args, dev, vp):
@@ -484,6 +513,15 @@ def run_ours(args):
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None if traffic is None else traffic * n_ev,
             "peak_source": f"{peak_kind} hbm_gbs (copy)", "stage_ms": stage_ms}
+    # second ceiling: the plain FP32 pipe (measured on this GPU), with the busy
+    # fractions of the dominant kernel's FMA and ALU pipes from its ncu summary
+    fma = profiled_metric(dom, "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active")
+    alu = profiled_metric(dom, "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active")
+    issue = profiled_metric(dom, "smsp__issue_active.avg.pct_of_peak_sustained_active")
+    roof["alu_ceiling"] = {"fp32_peak_tflops": fp32_peak_tflops(), "peak_source": "measured (velo_measure_fp32_peak)",
+                           "fma_pipe_frac": None if fma is None else fma / 100.0,
+                           "alu_pipe_frac": None if alu is None else alu / 100.0,
+                           "issue_active_frac": None if issue is None else issue / 100.0}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -290,6 +290,15 @@ int velo_mlp_adam_step(float* w, const float* grad, float* m, float* v, uint32_t
                        float beta2, float eps, uint32_t step, void* stream);
 
 /* Name of a VELO_* return code. */
+/* Measurement helper, not part of the method: the FP32 multiply-add rate of
+ * the current device (flops/s, 2 per FMA), from a kernel of independent FMA
+ * chains on every SM timed with CUDA events on `stream` (best of three
+ * launches after one warm-up; synchronises `stream`).  The reconstruction
+ * has no dense contraction, so this plain-ALU ceiling is its second
+ * roofline after HBM bandwidth.  VELO_EINVAL for a NULL output, VELO_ECUDA
+ * if a CUDA call fails. */
+int velo_measure_fp32_peak(double* flops_per_s, void* stream);
+
 const char* velo_strerror(int code);
 
 /* Library version (major * 10000 + minor * 100 + patch). */

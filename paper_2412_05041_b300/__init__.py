@@ -87,7 +87,7 @@ EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "
            "velo_tuning_default", "velo_reconstruct_into_tuned", "velo_reconstruct",
            "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
            "velo_context_set_pipeline", "velo_reconstruct_host", "velo_reconstruct_static", "velo_mlp_infer", "velo_mlp_workspace_size",
-           "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_strerror", "velo_version")
+           "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_measure_fp32_peak", "velo_strerror", "velo_version")
 
 
 def lib():
@@ -122,6 +122,7 @@ def lib():
         L.velo_mlp_loss_grad.argtypes = [_P, _P, ctypes.c_uint64, _P, _P, _P, _P, ctypes.c_uint64, _P]
         L.velo_mlp_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, ctypes.c_float, ctypes.c_uint32, _P]
+        L.velo_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _P]
         L.velo_strerror.restype = ctypes.c_char_p
         L.velo_strerror.argtypes = [ctypes.c_int]
         _lib = L

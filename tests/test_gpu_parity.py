@@ -298,3 +298,13 @@ def test_mc_quality_matches_oracle():
     g = to_numpy(gpu_run(b.offsets, b.pixels, b.geometry, vp))
     m = mc.evaluate_batch(b, g)
     assert m["efficiency"] >= 0.99 and m["ghost_rate"] <= 0.05
+
+
+def test_fp32_peak_measurement():
+    """The FP32 ceiling helper returns a rate in the range a B300-class GPU can
+    reach (148 SMs x 128 FMA lanes x 2 flops at 1-2.1 GHz: 38-80 TFLOP/s)."""
+    import ctypes
+    v = ctypes.c_double(0.0)
+    assert velo.lib().velo_measure_fp32_peak(ctypes.byref(v), None) == velo.OK
+    assert 10e12 < v.value < 200e12
+    assert velo.lib().velo_measure_fp32_peak(None, None) == velo.EINVAL
