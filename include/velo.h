@@ -236,8 +236,8 @@ void velo_result_free(velo_result_t* result);
  * serialised).  Only the used part of each output is copied back.  Offsets
  * that the device form rejects are passed to it unchanged, in one chunk, so
  * every event then fails as there.  velo_context_set_pipeline sets the most
- * chunks per call: 0 = automatic (about 16M pixel words per chunk, at most
- * 8), 1 = one chunk (copy in, compute, copy out, no overlap), at most 64;
+ * chunks per call: 0 = automatic (about 12.6M pixel words per chunk, at most
+ * 12), 1 = one chunk (copy in, compute, copy out, no overlap), at most 64;
  * VELO_EINVAL otherwise. */
 typedef struct velo_context velo_context_t;
 int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t** ctx);
