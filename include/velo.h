@@ -257,7 +257,7 @@ int velo_reconstruct_host(velo_context_t* ctx, const velo_events_t* host_events,
  * loads the library holds it until the process exits); the caller passes
  * device inputs and outputs exactly as for velo_reconstruct_into.  A batch
  * whose scratch need (velo_query_sizes' workspace_bytes) exceeds
- * VELO_STATIC_SCRATCH_BYTES -- about 850k pixel words, some 65 pile-up-5.5
+ * VELO_STATIC_SCRATCH_BYTES -- about 620k pixel words, some 50 pile-up-5.5
  * events -- is rejected with VELO_ECAPACITY before any device work.  Calls
  * no cudaMalloc, cudaFree or allocating routine.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, that device

@@ -56,6 +56,7 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   ws->trk_rank = c.take<uint32_t>(T);
   ws->trk_hoff = c.take<uint32_t>(T);
   ws->trk_logit = c.take<float>(T);
+  ws->trk_state = c.take<float>(T * VELO_STATE_STRIDE);
 }
 
 bool geometry_ok(const velo_geometry_t* g) {

@@ -57,6 +57,7 @@ struct Workspace {
   uint32_t* trk_rank;        // canonical rank among kept tracks, kNone if dropped
   uint32_t* trk_hoff;        // first hit of the track among the event's kept hits
   float* trk_logit;          // the network's logit (learned rejection)
+  float* trk_state;          // VELO_STATE_STRIDE floats per track: the fit's state, written by k_fit
 };
 
 struct Geo {

@@ -73,6 +73,7 @@ struct TrackSmem {
 constexpr int kFitThreads = 256;
 
 struct FitSmem {
+  uint32_t hit_fill;  // hit ids of the event's tracks staged so far
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   unsigned long long tmp64[64];
@@ -492,9 +493,14 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
   const uint32_t n_tr = W.ev_ntracks_all[e];
   if (tid < kModOffStride) S.mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
   if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
+  if (tid == 0) S.hit_fill = 0;
   __syncthreads();
   const uint32_t* hid = W.h_id + p0;
   uint32_t* first_of = W.sd + p0;
+  // for k_output: every track's state and its hit ids (in z order) at a slot of
+  // the event's word slice of sa (dead after the module loop; the tracks hold
+  // at most n hits), the slot's start in trk_pick
+  uint32_t* hit_stage = W.sa + p0;
   const uint32_t* meta = W.trk_meta + tb;
   const uint32_t* ta = W.trk_a + tb;
 
@@ -508,11 +514,11 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
     const bool valid = t < n_tr;
     float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
     float f[VELO_N_FEATURES];
-    uint32_t mods[VELO_MAX_MODULES];
+    uint32_t mods[VELO_MAX_MODULES], ids[VELO_MAX_MODULES];
     uint32_t n = 0;
     bool keep = false;
     if (valid) {
-      n = gather_track(W, p0, tb, t, S.mod_off, S.z, M, xs, ys, zs, mods, nullptr);
+      n = gather_track(W, p0, tb, t, S.mod_off, S.z, M, xs, ys, zs, mods, ids);
       fit_track(n, xs, ys, zs, P.sigma, P.ms_theta, st);
       keep = keep_track(n, st, P.ms_theta, P.chi2ndf_max, P.chi2ndf_max_3hit);
     }
@@ -529,7 +535,16 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
     }
     if (valid) {
       rank[t] = kNone;
-      if (keep) first_of[hid[ta[t]]] = t;
+      if (keep) {
+        first_of[hid[ta[t]]] = t;
+        if (P.use_mlp) st[19] = W.trk_logit[tb + t];
+        float* so = W.trk_state + (tb + t) * VELO_STATE_STRIDE;
+#pragma unroll
+        for (int k = 0; k < VELO_STATE_STRIDE; ++k) so[k] = st[k];
+        const uint32_t slot = atomicAdd(&S.hit_fill, n);
+        W.trk_pick[tb + t] = slot;
+        for (uint32_t j = 0; j < n; ++j) hit_stage[slot + j] = ids[j];
+      }
     }
   }
   __syncthreads();
@@ -580,7 +595,23 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   const uint32_t nt = W.ev_ntracks_all[e];
   const uint64_t to = L.out.track_offsets[e];
   const uint64_t hb = W.ev_hitbase[e];
-  for (uint32_t t = tid; t < nt; t += NT) {
+  if (!L.out.track_features) {  // states and hit ids as k_fit staged them
+    for (uint32_t t = tid; t < nt; t += NT) {
+      const uint32_t r = W.trk_rank[tb + t];
+      if (r == kNone) continue;
+      const uint32_t n = W.trk_meta[tb + t] & 255u, slot = W.trk_pick[tb + t];
+      const uint64_t dst = to + r;
+      const uint64_t h0 = hb + W.trk_hoff[tb + t];
+      L.out.track_hit_offsets[dst] = h0;
+      for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = W.sa[p0 + slot + j];
+      const float* si = W.trk_state + (tb + t) * VELO_STATE_STRIDE;
+      float* o = L.out.track_states + dst * VELO_STATE_STRIDE;
+#pragma unroll
+      for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = si[k];
+    }
+    return;
+  }
+  for (uint32_t t = tid; t < nt; t += NT) {  // with the features: gathered and fitted again
     const uint32_t r = W.trk_rank[tb + t];
     if (r == kNone) continue;
     float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
