@@ -21,6 +21,8 @@
 //      then the rare runs of equal fixed-point keys by insertion.
 // Events larger than the shared-memory tier run the same code on their
 // slice of the global workspace (generic pointers).
+#include <type_traits>
+
 #include "velo_device.cuh"
 #include "velo_internal.cuh"
 
@@ -314,16 +316,19 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   const bool narrow = n <= kNarrowPixels;
   const unsigned long long* acc = W.acc + 3 * p0;
   const uint32_t* acc32 = reinterpret_cast<const uint32_t*>(acc);
-  // the pixel arrays are dead from here on: the hit sort reuses the region
-  // (sort keys, values, their ping-pong copies, the cluster x, y and
-  // pseudo-angle key: 7 words per cluster)
+  // the pixel arrays are dead from here on.  In shared memory (HS) the hit
+  // sort keeps its keys (32-bit) and cluster ids (16-bit: fewer than 2^16
+  // clusters here) with their ping-pong copies, 12 bytes per cluster; the
+  // cluster x, y and pseudo-angle key, read once at the end, go to global
+  // scratch (cl_x, cl_y, and sc, unused by the shared tier).
+  using V = typename std::conditional<HS, uint16_t, uint32_t>::type;
   uint32_t* KA = HS ? region : W.sa + p0;
   uint32_t* KB = HS ? region + n_clusters : W.sb + p0;
-  uint32_t* VA = HS ? region + 2 * n_clusters : W.sc + p0;
-  uint32_t* VB = HS ? region + 3 * n_clusters : W.sd + p0;
-  float* cx = HS ? reinterpret_cast<float*>(region + 4 * n_clusters) : W.cl_x + p0;
-  float* cy = HS ? reinterpret_cast<float*>(region + 5 * n_clusters) : W.cl_y + p0;
-  float* ck = HS ? reinterpret_cast<float*>(region + 6 * n_clusters) : W.h_key + p0;
+  V* VA = HS ? reinterpret_cast<V*>(region + 2 * n_clusters) : reinterpret_cast<V*>(W.sc + p0);
+  V* VB = HS ? reinterpret_cast<V*>(region + 2 * n_clusters) + n_clusters : reinterpret_cast<V*>(W.sd + p0);
+  float* cx = W.cl_x + p0;
+  float* cy = W.cl_y + p0;
+  float* ck = HS ? reinterpret_cast<float*>(W.sc + p0) : W.h_key + p0;
   const Geo& g = L.geo;
   const uint32_t* mo = S.mod_off;
   for (uint32_t id = tid; id < n_clusters; id += NT) {
@@ -348,7 +353,7 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
     cy[id] = y;
     ck[id] = key;
     KA[id] = module_of(mo, M, id) << 19 | hit_key_fixed(key);
-    VA[id] = id;
+    VA[id] = (V)id;
   }
   __syncthreads();
 
@@ -373,9 +378,9 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
       for (; b > pos; --b) {
         const uint32_t o = VB[b - 1];
         if (((unsigned long long)__float_as_uint(ck[o]) << 32 | o) <= kv) break;
-        VB[b] = o;
+        VB[b] = (V)o;
       }
-      VB[b] = id;
+      VB[b] = (V)id;
     }
   }
   __syncthreads();
@@ -435,7 +440,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n)
                                         : pixel_phases<NT, false>(L, e, S, region, tier, p0, n);
   if (n_clusters == kNone) return;
-  if (7u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters);
+  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters);
   else hit_phases<NT, false>(L, e, S, region, p0, n, n_clusters);
 }
 

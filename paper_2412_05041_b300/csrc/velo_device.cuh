@@ -72,14 +72,14 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
 // scatters its chunk in index order: among the lanes of one step with equal
 // digits the lowest lane reads and advances the digit's slot and broadcasts
 // it, and each lane adds its rank among those lanes, so equal digits keep
-// their relative order.  a/b (and va/vb) may live in shared or global
-// memory.  cnt: radix_counters(NT) words.
+// their relative order.  a/b (and va/vb, of any unsigned type) may live in
+// shared or global memory.  cnt: radix_counters(NT) words.
 constexpr uint32_t kRadixRow = 257;  // 256 digit counters + 1 pad word per warp
 __host__ __device__ constexpr uint32_t radix_counters(int nt) { return kRadixRow * (uint32_t)(nt / 32); }
 
-template <int NT, bool HAS_VAL, class K, class DigitF>
-__device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, uint32_t n, DigitF digit,
-                           uint32_t* cnt, uint32_t* tmp) {
+template <int NT, bool HAS_VAL, class K, class V, class DigitF>
+__device__ void radix_pass(const K* a, K* b, const V* va, V* vb, uint32_t n, DigitF digit, uint32_t* cnt,
+                           uint32_t* tmp) {
   constexpr int NW = NT / 32;
   constexpr uint32_t NB = 256;
   const uint32_t lane = lane_id(), w = warp_id();
@@ -88,7 +88,7 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
   __syncthreads();
   const uint32_t chunk = (n + NW - 1) / NW;
   const uint32_t s = min(n, w * chunk), e = min(n, s + chunk);
-  for (uint32_t i = s + lane; i < e; i += 32) atomicAdd(row + digit(a[i], HAS_VAL ? va[i] : 0u), 1u);
+  for (uint32_t i = s + lane; i < e; i += 32) atomicAdd(row + digit(a[i], HAS_VAL ? (uint32_t)va[i] : 0u), 1u);
   __syncthreads();
   // exclusive scan of the 256*NW counters in (digit, warp) order; thread t
   // owns the 8 consecutive entries j = 8t .. 8t+7 (digit j / NW, warp j % NW)
@@ -114,11 +114,12 @@ __device__ void radix_pass(const K* a, K* b, const uint32_t* va, uint32_t* vb, u
     const uint32_t i = base + lane;
     const bool valid = i < e;
     K k = K(0);
-    uint32_t v = 0, d = NB;
+    V v = V(0);
+    uint32_t d = NB;
     if (valid) {
       k = a[i];
       if (HAS_VAL) v = va[i];
-      d = digit(k, v);
+      d = digit(k, (uint32_t)v);
     }
     // full steps (warp-uniform) have no idle lane, whose digit NB needs a ninth bit
     const uint32_t peers = base + 32u <= e ? warp_peers<8>(d) : warp_peers<9>(d);
