@@ -147,6 +147,16 @@ def test_equal_keys_order_by_id():
     assert_labels(g["pixel_cluster"].cpu().numpy(), r["pixel_cluster"], offsets, offsets)
 
 
+def test_uneven_module_spacing():
+    """Generated events on modules with uneven z spacing (every seed and
+    extension lever arm differs): identical to the oracle."""
+    zs = (-300.0, -280.0, -250.0, -180.0, -90.0, -40.0, 0.0, 20.0, 60.0, 130.0, 200.0, 230.0, 300.0, 390.0, 450.0,
+          520.0, 600.0, 700.0)
+    geo = velogen.Geometry(n_modules=len(zs), module_z=zs)
+    b = velogen.generate(velogen.C2, n_events=60, first_event=500, geometry=geo)
+    check_batch(b, 5e-4)
+
+
 def test_bad_offsets_fail_every_event():
     b = velogen.generate(velogen.C2, n_events=4)
     off = b.offsets.copy()

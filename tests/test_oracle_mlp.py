@@ -46,8 +46,11 @@ def test_bf16_rounding_is_round_to_nearest_even():
     v = np.concatenate([rng.normal(0, 10, 2000), rng.normal(0, 1e-3, 500), [0.0, -0.0, 1.0, 1.00390625, 1.01171875]])
     v = v.astype(np.float32)
     ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+    # exact ties (the lower 16 bits 0x8000) go to the even neighbour: 1 + 2^-8 rounds
+    # down to 1, 1 + 3 * 2^-8 up to 1 + 2^-6
+    assert ref[-2] == 1.0 and ref[-1] == 1.015625
     # a network whose only path is one input -> one hidden unit -> logit exposes bf16(x)
-    for x, r in zip(v[:300], ref[:300]):
+    for x, r in zip(np.concatenate([v[:300], v[-5:]]), np.concatenate([ref[:300], ref[-5:]])):
         blob = np.zeros(mlp.N_FLOATS, np.float32)
         p = mlp.unpack(blob)
         p["inv_std"][0] = 1.0

@@ -1,0 +1,104 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each case plants one mistake in a copy of the oracle's C++ source -- a dropped
+term, a wrong sign, index or comparison, a swapped operand -- builds that copy
+in a scratch directory and runs the oracle's pin tests against it; at least
+one pin must fail.  The mistakes are planted in the oracle only, on the CPU;
+the product library is not involved.  Each case names the step of the method
+it breaks (centroid, connectivity, pseudo-angle window, straight-line and
+Kalman fits, chi2/ndf and the 3-hit rule, extension, seeding and its
+conflicts, termination, learned-rejection features and bfloat16 rounding).
+"""
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PIN_TESTS = ("test_oracle_cluster.py", "test_oracle_fit.py", "test_oracle_track.py", "test_oracle_mlp.py")
+
+# (name, exact source text, replacement): each text occurs once in velo_oracle.cpp
+MUTATIONS = [
+    ("centroid without the half-pixel offset",
+     "snx[id] += q * (int64_t)(2 * w_col(w) + 1);", "snx[id] += q * (int64_t)(2 * w_col(w));"),
+    ("4-connectivity instead of 8",
+     "int rr = r + dr, cc = c + dc;", "if (dr != 0 && dc != 0) continue;\n        int rr = r + dr, cc = c + dc;"),
+    ("pseudo-angle: wrong sign in the second quadrant",
+     "k = 1.0f + (-x) / (y - x);", "k = 1.0f + x / (y - x);"),
+    ("window distance without the wrap at 4",
+     "if (d > 2.0f) d = 4.0f - d;", "if (d > 4.0f) d = 4.0f - d;"),
+    ("straight-line fit: Szz sums dz instead of dz^2",
+     "Szz = Szz + dz * dz;", "Szz = Szz + dz;"),
+    ("straight-line fit: intercept with the wrong sign",
+     "R x = (Sx - tx * Sz) / S0;", "R x = (Sx + tx * Sz) / S0;"),
+    ("Kalman start without the process noise",
+     "R C11 = (s2 + s2) / (dz0 * dz0) + q;", "R C11 = (s2 + s2) / (dz0 * dz0);"),
+    ("Kalman prediction with the wrong sign",
+     "X = X + T * dz;", "X = X - T * dz;"),
+    ("state ndf = 2n - 3",
+     "st[18] = (R)(2 * n - 4);", "st[18] = (R)(2 * n - 3);"),
+    ("cut ndf = 2n - 3",
+     "float ndf = (float)(2 * n - 4);", "float ndf = (float)(2 * n - 3);"),
+    ("3-hit rule inverted",
+     "if (n == 3 && !(r <= p->chi2ndf_max_3hit)) continue;", "if (n == 3 && (r <= p->chi2ndf_max_3hit)) continue;"),
+    ("extension extrapolates from the older hit",
+     "float xp = H.x[a] + tx * (Z[m] - H.z[a]);", "float xp = H.x[b] + tx * (Z[m] - H.z[a]);"),
+    ("extension takes used hits",
+     "        if (used0[h]) continue;\n", ""),
+    ("extension contention: largest key wins",
+     "claim[bh] = std::min(claim[bh], k);", "claim[bh] = claim[bh] == ~0ull ? k : std::max(claim[bh], k);"),
+    ("termination one module late",
+     "if (l - m - 1 > (int)p->max_skipped)", "if (l - m - 2 > (int)p->max_skipped)"),
+    ("seeding lever arm from the wrong module",
+     "float dz12 = H.z[h1] - H.z[h2];", "float dz12 = H.z[h0] - H.z[h1];"),
+    ("seeding slope with the wrong denominator",
+     "float tx = (H.x[h0] - H.x[h2]) / dz02;", "float tx = (H.x[h0] - H.x[h2]) / (H.z[h0] - H.z[h1]);"),
+    ("seeding tie goes to the larger h0",
+     "(s == best.s && (h0 < best.h0 ||", "(s == best.s && (h0 > best.h0 ||"),
+    ("seeding uses used h0",
+     "        if (used[h0]) continue;\n", ""),
+    ("seed survives without its h2 claim",
+     "if (sclaim[s.h0] != k || sclaim[s.h2] != k) continue;", "if (sclaim[s.h0] != k) continue;"),
+    ("bfloat16 rounding half away from zero",
+     "u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0x8000u;"),
+    ("feature RMS without the square root",
+     "f[8] = std::sqrt(sxx / fn);", "f[8] = sxx / fn;"),
+]
+
+
+def _run_case(case, scratch):
+    name, old, new = case
+    work = os.path.join(scratch, "case%02d" % MUTATIONS.index(case))
+    os.makedirs(os.path.join(work, "tests"))
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(work, "oracle"),
+                    ignore=shutil.ignore_patterns("__pycache__", "liboracle.so*"))
+    shutil.copytree(os.path.join(ROOT, "velogen"), os.path.join(work, "velogen"),
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    for f in ("conftest.py", "_compare.py") + PIN_TESTS:
+        shutil.copy2(os.path.join(ROOT, "tests", f), os.path.join(work, "tests", f))
+    shutil.copy2(os.path.join(ROOT, "pytest.ini"), os.path.join(work, "pytest.ini"))
+    src = os.path.join(work, "oracle", "velo_oracle.cpp")
+    text = open(src).read()
+    assert text.count(old) == 1, f"{name}: the source text is not unique"
+    open(src, "w").write(text.replace(old, new))
+    env = dict(os.environ, PYTHONPATH=work, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
+                       + [os.path.join("tests", f) for f in PIN_TESTS], cwd=work, env=env,
+                       capture_output=True, text=True, timeout=600)
+    failed = [ln.split(" ")[1] for ln in r.stdout.splitlines() if ln.startswith("FAILED ")]
+    return name, r.returncode, failed, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as scratch:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+            results = list(ex.map(lambda c: _run_case(c, scratch), MUTATIONS))
+    survivors = [(name, out) for name, rc, failed, out in results if rc == 0]
+    for name, rc, failed, out in results:
+        print(f"{name}: {'caught by ' + ', '.join(failed) if rc != 0 else 'NOT CAUGHT'}")
+    assert not survivors, "mistakes no pin catches: " + "; ".join(n for n, _ in survivors)

@@ -83,6 +83,34 @@ def test_seed_conflict_tie_goes_to_smaller_middle_id():
     assert len(tracks) == 1 and win in tracks[0] and ids["h0"] in tracks[0]
 
 
+def test_seed_tie_between_two_h0_goes_to_smaller_id():
+    """Two h0 candidates mirrored about a line in y = 0 (y0 = +d and -d, the same
+    x): the seed's scatter is exactly equal for both (negation is exact and the
+    square drops the sign), so the tie rule decides: the smaller h0 id wins."""
+    d = 0.0625
+    pts = {"h2": (2, 20.0, 0.0), "h1": (3, 21.0, 0.0), "h0a": (4, 22.0, d), "h0b": (4, 22.0, -d)}
+    tracks, _, ids = run(pts)
+    assert len(tracks) == 1
+    win = min(ids["h0a"], ids["h0b"])
+    assert sorted(tracks[0]) == sorted([ids["h2"], ids["h1"], win])
+
+
+def test_seed_lever_arms_with_uneven_module_spacing():
+    """Modules 20, 30, 70 and 90 mm apart: a noise-free straight track is found
+    only if the seed extrapolates with the lever arms of its own three modules
+    (equal spacing would hide a swapped lever arm)."""
+    zs = np.array([-300.0, -280.0, -250.0, -180.0, -90.0, 0.0, 20.0, 60.0, 130.0, 200.0, 230.0, 300.0])
+    geo = velogen.Geometry(n_modules=len(zs), module_z=tuple(zs.tolist()))
+    tx, ty = 0.06, 0.03
+    pts = {f"h{m}": (m, np.float32(5.0 + tx * (zs[m] - zs[0])), np.float32(3.0 + ty * (zs[m] - zs[0])))
+           for m in range(len(zs))}
+    module, x, y, ids = make_hits(pts)
+    tracks, states = oracle.track_event(module, x, y, geo, P0)
+    assert [sorted(map(int, t)) for t in tracks] == [sorted(ids.values())]
+    np.testing.assert_allclose(states[0][2], tx, atol=1e-6)
+    np.testing.assert_allclose(states[0][3], ty, atol=1e-6)
+
+
 def test_extension_contention_and_skip():
     """Tracks A and B pass within 0.05 mm of one hit on module 7; A exactly through it.
     A takes it, B counts module 7 as skipped and continues on module 6."""
