@@ -299,22 +299,33 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const float alpha = dz12 / dz02, one_m_alpha = 1.0f - alpha;
     const bool seed_narrow = one_m_alpha > 0.05f && one_m_alpha < 0.95f;
     const float seed_reach = seed_narrow ? sqrtf(P.max_scatter_seed) / one_m_alpha * 1.01f + 1e-3f : 0.0f;
-    // Division-free pre-test of the scatter cut.  With the slope
-    // tx' = (x0 - x2) * rcp(dz02) instead of the exact quotient, every binary32
-    // step of the exact chain (quotient, product with dz12, two sums) moves by at
-    // most a few units of roundoff u = 2^-24 of its operands, so for a triplet
-    // that passes the exact cuts |dx' - dx|, |dy' - dy| <= 8u (S |dz12| + 2 X +
-    // 2 r + 1) =: err, with S the slope cut, X the largest |coordinate| of a hit
-    // on the sensor and r = sqrt(scatter cut); its dx'^2 + dy'^2 is then below
-    // (r + 1.5 err)^2 (with margin for the roundoff of the test itself).  A
-    // candidate is dropped early only when it exceeds that bound, i.e. when the
-    // exact arithmetic (still run for every other candidate) rejects it too, so
-    // the result is unchanged.
+    // Division-free pre-test of the scatter cut.  The seed's residual at z1 is
+    // D = (1 - a) x2 + a x0 - x1 with a = dz12 / dz02; the pre-test uses
+    // a' = rcp(dz02) dz12 and dx' = (1 - a') x2 + (a' x0 - x1), the first term
+    // computed once per hit of module m - 1 and the second once per (h1, h0).
+    // With u = 2^-24, S the slope cut, X the largest |coordinate| of a hit on
+    // the sensor and r = sqrt(scatter cut): |a' - a| <= 2u a, so for a triplet
+    // that passes the exact slope cut the a' error moves D by at most
+    // 2u S dz12, and the roundings of the pre-test by at most 5u X + u r;
+    // the exact chain (quotient, product with dz12, two sums) stays within
+    // 5u S dz12 + 2u (X + r) + 2u r of D.  So for a triplet that passes the
+    // exact cuts |dx' - dx|, |dy' - dy| <= 8u (S |dz12| + 2 X + 2 r + 1) =: err
+    // and dx'^2 + dy'^2 is below (r + 1.5 err)^2 (with margin for the roundoff
+    // of the test itself).  A candidate is dropped early only when it exceeds
+    // that bound, i.e. when the exact arithmetic (still run, with the window
+    // test, for every other candidate) rejects it too: the result is unchanged.
     const float rcp_dz02 = __frcp_rn(dz02);
     const float pre_err =
         8.0f * 5.9604645e-8f * (P.max_slope * fabsf(dz12) + 2.0f * coord_max + 2.0f * sqrtf(P.max_scatter_seed) + 1.0f);
     const float pre_r = sqrtf(P.max_scatter_seed) * (1.0f + 1e-6f) + 1.5f * pre_err;
     const float pre_sc = pre_r * pre_r * (1.0f + 1e-5f);
+    const float ap = fm(rcp_dz02, dz12), oma = fs(1.0f, ap);
+    float* ux = W.cl_x + p0;  // (1 - a') x2, (1 - a') y2 of the hits of module m - 1 (the
+    float* uy = W.cl_y + p0;  // clustering's centroid scratch, free during tracking)
+    for (uint32_t q = lo2 + tid; q < hi2; q += NT) {
+      ux[q] = fm(oma, hx[q]);
+      uy[q] = fm(oma, hy[q]);
+    }
     constexpr uint32_t kChunk = seed_chunk<NT>();
     for (uint32_t cbase = mlo; cbase < mhi; cbase += kChunk) {
       const uint32_t cn = min(kChunk, mhi - cbase);
@@ -364,18 +375,16 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
           R2 = narrowed_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2, (x1 - alpha * x0) / one_m_alpha,
                                (y1 - alpha * y0) / one_m_alpha, seed_reach);
+        const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
         unsigned long long best = ~0ull;
         for (int part2 = 0; part2 < 2; ++part2) {
           const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
           for (uint32_t q2 = s2; q2 < e2; ++q2) {
+            const float ex = fa(ux[q2], c0x), ey = fa(uy[q2], c0y);
+            if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) continue;
             if (dmod4(hk[q2], k1) > P.win_seed) continue;
             const float x2 = hx[q2], y2 = hy[q2];
             const float dx02 = fs(x0, x2), dy02 = fs(y0, y2);
-            {
-              const float ex = fs(fa(x2, fm(fm(dx02, rcp_dz02), dz12)), x1);
-              const float ey = fs(fa(y2, fm(fm(dy02, rcp_dz02), dz12)), y1);
-              if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) continue;
-            }
             const float tx = fd(dx02, dz02), ty = fd(dy02, dz02);
             if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
             const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
