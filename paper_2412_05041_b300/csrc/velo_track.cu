@@ -247,12 +247,12 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           unsigned long long best = ~0ull;
           for (int part = 0; part < 2; ++part) {
             const uint32_t s = part ? R.b0 : R.a0, en = part ? R.b1 : R.a1;
-            for (uint32_t pos = s; pos < en; ++pos) {
-              if (used[pos]) continue;
-              if (dmod4(hk[pos], ka) > P.win_fwd) continue;
+            for (uint32_t pos = s; pos < en; ++pos) {  // the cut first: few candidates pass it
               const float dx = fs(xp, hx[pos]), dy = fs(yp, hy[pos]);
               const float d2 = fa(fm(dx, dx), fm(dy, dy));
               if (d2 > P.max_scatter_fwd) continue;
+              if (used[pos]) continue;
+              if (dmod4(hk[pos], ka) > P.win_fwd) continue;
               const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | hid[pos];
               if (cand < best) {
                 best = cand;
