@@ -5,8 +5,8 @@
 // clustering.  One CTA per event at a time (1024 threads and one CTA per SM,
 // or 512 threads and two; persistent, events from a work queue):
 //   1. load and validate the event's words (coalesced, 4 B per thread);
-//   2. stable block radix sort by the 27-bit (module, row, col) key
-//      (4 passes of 8 bits) in shared memory;
+//   2. stable sort by the 27-bit (module, row, col) key in shared memory:
+//      2 radix passes by (module, row), then each row by insertion;
 //   3. union-find over 8-connected neighbours found in the sorted array
 //      (they sit just before a word): every word links to its smallest
 //      earlier neighbour, and the few whose earlier neighbours are not
@@ -42,6 +42,7 @@ struct ClusterSmem {
 };
 
 constexpr uint32_t kRootFlag = 0x80000000u;
+constexpr uint32_t kRowSortMax = 32;  // longest row sorted by insertion (else the full radix sort)
 
 __device__ __forceinline__ uint32_t vload(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 
@@ -121,15 +122,46 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   uint32_t* A = PS ? region : W.sa + p0;
   uint32_t* B = PS ? region + tier : W.sb + p0;
 
-  // 2. sort by (module, row, col); 4 passes A->B->A->B->A
+  // 2. stable sort by (module, row, col).  Two LSD passes sort by (module,
+  // row) (A->B->A); the words of one row -- a few in a pile-up event -- then
+  // go in column order by a stable insertion sort, run by the thread that owns
+  // the row's first word.  Both steps are stable, so the array ends exactly as
+  // a stable sort by the full key leaves it.  If a row has more than
+  // kRowSortMax words, the whole array is sorted again by the full key (4
+  // passes; stable, from an order that still keeps equal keys in input order).
   radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
-                        [](uint32_t k, uint32_t) { return (k & kKeyMask) & 255u; }, S.cnt, S.tmp);
+                        [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 11) & 255u; }, S.cnt, S.tmp);
   radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
-                        [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 8) & 255u; }, S.cnt, S.tmp);
-  radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
-                        [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 16) & 255u; }, S.cnt, S.tmp);
-  radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
-                        [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 24; }, S.cnt, S.tmp);
+                        [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 19; }, S.cnt, S.tmp);
+  bool long_row = false;
+  for (uint32_t pos = tid; pos < n; pos += NT) {
+    // rows only permute inside themselves, so another thread's sort never
+    // changes the (module, row) read here
+    const uint32_t mr = (A[pos] & kKeyMask) >> 11;
+    if (pos > 0 && ((A[pos - 1] & kKeyMask) >> 11) == mr) continue;  // not the row's first word
+    uint32_t end = pos + 1;
+    while (end < n && end - pos <= kRowSortMax && ((A[end] & kKeyMask) >> 11) == mr) ++end;
+    if (end - pos > kRowSortMax) {
+      long_row = true;
+      continue;
+    }
+    for (uint32_t a = pos + 1; a < end; ++a) {
+      const uint32_t w = A[a], k = w & kKeyMask;
+      uint32_t b = a;
+      for (; b > pos && (A[b - 1] & kKeyMask) > k; --b) A[b] = A[b - 1];
+      A[b] = w;
+    }
+  }
+  if (__syncthreads_or(long_row)) {
+    radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                          [](uint32_t k, uint32_t) { return (k & kKeyMask) & 255u; }, S.cnt, S.tmp);
+    radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                          [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 8) & 255u; }, S.cnt, S.tmp);
+    radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                          [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 16) & 255u; }, S.cnt, S.tmp);
+    radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                          [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 24; }, S.cnt, S.tmp);
+  }
 
   // 3. union-find over 8-connected neighbours.  Every earlier neighbour of
   // word i has a key in [lo_all, k]: duplicates (k), the left neighbour
