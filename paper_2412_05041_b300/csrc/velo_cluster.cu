@@ -111,16 +111,17 @@ __device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offse
 // Phases 2-5 on the event's n pixel words in A (B: the second buffer), in
 // shared memory when PS (so that the sorts, the union-find and its atomics
 // compile to shared-memory instructions), else in the event's global slice.
-// Returns the cluster count, or kNone after failing the event.
+// Returns the cluster count, or kNone after failing the event; *sums gets
+// the 32-bit charge sums (3 per cluster) when they were kept in 32 bits.
 template <int NT, bool PS>
 __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S,
                                                  uint32_t* region, const uint32_t tier, const uint64_t p0,
-                                                 const uint32_t n) {
+                                                 const uint32_t n, uint32_t** sums) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
   uint32_t* A = PS ? region : W.sa + p0;
-  uint32_t* B = PS ? region + tier : W.sb + p0;
+  uint32_t* B = PS ? region + n : W.sb + p0;
 
   // 2. stable sort by (module, row, col).  Two LSD passes sort by (module,
   // row) (A->B->A); the words of one row -- a few in a pile-up event -- then
@@ -309,9 +310,14 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   // 5. integer charge sums per cluster, then the binary32 centroid.  With at
   // most kNarrowPixels words, sum q(2c+1) <= 15 * 4095 * 23552 < 2^32, so
   // 32-bit sums (and a 32-bit division) are exact; larger events use 64 bits.
+  // The 32-bit sums go to shared memory after the two pixel arrays when they
+  // fit there and clear of the hit sort's keys and first ids ([0, 2.5 n_c)
+  // words), which the centroid pass writes while it reads the sums.
   const bool narrow = n <= kNarrowPixels;
   unsigned long long* acc = W.acc + 3 * p0;
-  uint32_t* acc32 = reinterpret_cast<uint32_t*>(acc);  // inside this event's own 64-bit slice
+  const bool sums_smem = PS && narrow && 2u * n + 3u * n_clusters <= 2u * tier && 5u * n_clusters <= 4u * n;
+  uint32_t* acc32 = sums_smem ? region + 2 * n : reinterpret_cast<uint32_t*>(acc);  // global: in this event's slice
+  *sums = acc32;
   if (narrow) {
     for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc32[i] = 0u;
   } else {
@@ -338,16 +344,17 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
 }
 
 // Centroids, pseudo-angle keys and the hit sort of the event's n_clusters
-// clusters (charge sums in the workspace), through shared memory when HS.
+// clusters (charge sums: acc32 when 32-bit, else the 64-bit workspace
+// sums), through shared memory when HS.
 template <int NT, bool HS>
 __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
-                                           const uint64_t p0, const uint32_t n, const uint32_t n_clusters) {
+                                           const uint64_t p0, const uint32_t n, const uint32_t n_clusters,
+                                           const uint32_t* acc32) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
   const bool narrow = n <= kNarrowPixels;
   const unsigned long long* acc = W.acc + 3 * p0;
-  const uint32_t* acc32 = reinterpret_cast<const uint32_t*>(acc);
   // the pixel arrays are dead from here on.  In shared memory (HS) the hit
   // sort keeps its keys (32-bit) and cluster ids (16-bit: fewer than 2^16
   // clusters here) with their ping-pong copies, 12 bytes per cluster; the
@@ -469,11 +476,12 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
     fail_event(L, e, VELO_EVT_BADWORD, offsets_ok, p0, n);
     return;
   }
-  const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n)
-                                        : pixel_phases<NT, false>(L, e, S, region, tier, p0, n);
+  uint32_t* sums = nullptr;
+  const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n, &sums)
+                                        : pixel_phases<NT, false>(L, e, S, region, tier, p0, n, &sums);
   if (n_clusters == kNone) return;
-  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters);
-  else hit_phases<NT, false>(L, e, S, region, p0, n, n_clusters);
+  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters, sums);
+  else hit_phases<NT, false>(L, e, S, region, p0, n, n_clusters, sums);
 }
 
 // Persistent: every CTA takes events from the work queue until it is empty,
