@@ -273,11 +273,21 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   for (uint32_t i = lo; i < hi; ++i) nroot += (B[i] == i);
   uint32_t n_clusters;
   uint32_t rank = block_exclusive_scan<NT, uint32_t>(nroot, &n_clusters, S.tmp);
+  // roots per module: a chunk is sorted, so count per run of one module and
+  // add once per run (not once per root onto 26 shared counters)
+  uint32_t run_mod = 0, run_cnt = 0;
   for (uint32_t i = lo; i < hi; ++i)
     if (B[i] == i) {
       B[i] = rank++ | kRootFlag;
-      atomicAdd(&S.mod_count[(A[i] >> 22) & 31u], 1u);
+      const uint32_t m = (A[i] >> 22) & 31u;
+      if (m != run_mod && run_cnt) {
+        atomicAdd(&S.mod_count[run_mod], run_cnt);
+        run_cnt = 0;
+      }
+      run_mod = m;
+      ++run_cnt;
     }
+  if (run_cnt) atomicAdd(&S.mod_count[run_mod], run_cnt);
   __syncthreads();
   for (uint32_t i = lo; i < hi; ++i) {
     const uint32_t v = B[i];
@@ -465,11 +475,14 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   const bool smem_tier = n <= tier;
   uint32_t* A = smem_tier ? region : W.sa + p0;
   if (offsets_ok) {
+    bool bad = false;
+#pragma unroll 4
     for (uint32_t i = tid; i < n; i += NT) {
       const uint32_t w = __ldg(L.pix + p0 + i);
-      if (!word_valid(w, L.geo)) S.flag = 1u;
+      bad |= !word_valid(w, L.geo);
       A[i] = w;
     }
+    if (bad) S.flag = 1u;
   }
   __syncthreads();
   if (S.flag) {
