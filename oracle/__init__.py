@@ -68,6 +68,34 @@ class _Par(ctypes.Structure):
                 ("use_mlp", ctypes.c_uint32), ("mlp_logit_min", ctypes.c_float), ("mlp", ctypes.c_void_p)]
 
 
+@dataclass(frozen=True)
+class FwdParams:
+    """Forward tracking (pixel-tracker tracks to the downstream layers)."""
+    p_min: float = 3.0
+    win_y: float = 40.0
+    tol_x: float = 8.0
+    tol_y: float = 40.0
+    tol_x_far: float = 3.0
+    sigma_x: float = 0.08
+    tol_match: float = 25.0
+    chi2ndf_max: float = 4.0
+    min_hits: int = 9
+
+
+FWD_LAYERS = 12
+FWD_STATE = 6
+
+
+class _Down(ctypes.Structure):
+    _fields_ = [("z_mag", ctypes.c_float), ("z_layers", ctypes.c_float * FWD_LAYERS), ("kappa", ctypes.c_float)]
+
+
+class _FwdPar(ctypes.Structure):
+    _fields_ = [("p_min", ctypes.c_float), ("win_y", ctypes.c_float), ("tol_x", ctypes.c_float),
+                ("tol_y", ctypes.c_float), ("tol_x_far", ctypes.c_float), ("sigma_x", ctypes.c_float),
+                ("tol_match", ctypes.c_float), ("chi2ndf_max", ctypes.c_float), ("min_hits", ctypes.c_uint32)]
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so in place: g++ -O2 -ffp-contract=off (no FMA contraction, no fast-math)."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
@@ -105,6 +133,8 @@ def _load():
         lib.vo_mlp_logit.restype = ctypes.c_float
         lib.vo_mlp_logit.argtypes = [_P, _P]
         lib.vo_batch_free.argtypes = [ctypes.c_void_p]
+        lib.vo_forward_event.argtypes = [ctypes.c_uint64, _P, _P, _P, ctypes.c_uint64, _P, _P, _P, _P, _P,
+                                         ctypes.POINTER(_Down), ctypes.POINTER(_FwdPar), _P, _P, _P]
         _lib = lib
     return _lib
 
@@ -240,3 +270,48 @@ def mlp_logit(mlp: np.ndarray, f: np.ndarray) -> float:
     mlp = np.ascontiguousarray(mlp, np.float32)
     f = np.ascontiguousarray(f, np.float32)
     return float(lib.vo_mlp_logit(_ptr(mlp), _ptr(f)))
+
+
+def downstream_struct(down) -> _Down:
+    d = _Down()
+    d.z_mag = float(down.z_mag)
+    for i, z in enumerate(down.z_layers):
+        d.z_layers[i] = float(z)
+    d.kappa = float(down.kappa)
+    return d
+
+
+def forward(scifi_offsets, layer, x, y, result, down, params: FwdParams = FwdParams()):
+    """Forward tracking of a batch: downstream hits in CSR (per event, ids =
+    index within the event) and a reconstruction result (numpy dict with
+    cluster_offsets, cluster_x/y/z, track_offsets, track_hit_offsets,
+    track_hits).  Returns n_found [T], hits [T, 12] (event-local hit ids,
+    0xFFFFFFFF = none), state [T, 6] = (q/p, chi2/ndf, b, a, d_x, d_y)."""
+    lib = _load()
+    so = np.asarray(scifi_offsets, np.int64)
+    to = np.asarray(result["track_offsets"], np.int64)
+    co = np.asarray(result["cluster_offsets"], np.int64)
+    hoff = np.asarray(result["track_hit_offsets"], np.uint64)
+    th = np.ascontiguousarray(result["track_hits"], np.uint32)
+    cx = np.ascontiguousarray(result["cluster_x"], np.float32)
+    cy = np.ascontiguousarray(result["cluster_y"], np.float32)
+    cz = np.ascontiguousarray(result["cluster_z"], np.float32)
+    layer = np.ascontiguousarray(layer, np.uint32)
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    T = int(to[-1])
+    n_found = np.zeros(max(T, 1), np.uint32)
+    hits = np.full((max(T, 1), FWD_LAYERS), 0xFFFFFFFF, np.uint32)
+    state = np.zeros((max(T, 1), FWD_STATE), np.float32)
+    d = downstream_struct(down)
+    p = _FwdPar(**asdict(params))
+    for e in range(len(to) - 1):
+        h0, h1, t0, t1, c0 = int(so[e]), int(so[e + 1]), int(to[e]), int(to[e + 1]), int(co[e])
+        if t1 == t0:
+            continue
+        ho = np.ascontiguousarray(hoff[t0:t1 + 1] - hoff[t0])
+        tk = np.ascontiguousarray(th[int(hoff[t0]):int(hoff[t1])])
+        lib.vo_forward_event(h1 - h0, _ptr(layer[h0:h1]), _ptr(x[h0:h1]), _ptr(y[h0:h1]), t1 - t0, _ptr(ho), _ptr(tk),
+                             _ptr(cx[c0:]), _ptr(cy[c0:]), _ptr(cz[c0:]), ctypes.byref(d), ctypes.byref(p),
+                             _ptr(n_found[t0:t1]), _ptr(hits[t0:t1]), _ptr(state[t0:t1]))
+    return n_found[:T], hits[:T], state[:T]

@@ -662,4 +662,140 @@ void vo_features(uint32_t n, const float* x, const float* y, const float* z, con
 
 float vo_mlp_logit(const float* mlp, const float* f) { return mlp_logit(mlp, f); }
 
+// Forward tracking of one event, the steps in the order the header states.
+void vo_forward_event(uint64_t n_hits, const uint32_t* layer, const float* x, const float* y, uint64_t n_tracks,
+                      const uint64_t* track_hit_offsets, const uint32_t* track_hits, const float* cluster_x,
+                      const float* cluster_y, const float* cluster_z, const vo_downstream_t* geo,
+                      const vo_fwd_params_t* p, uint32_t* n_found, uint32_t* hits, float* state) {
+  const int NL = VO_FWD_LAYERS;
+  for (uint64_t t = 0; t < n_tracks; ++t) {
+    // 0. the line through the two most downstream hits (ids ascend with z)
+    const uint32_t ha = track_hits[track_hit_offsets[t + 1] - 1], hb = track_hits[track_hit_offsets[t + 1] - 2];
+    const float x0 = cluster_x[ha], y0 = cluster_y[ha], z0 = cluster_z[ha];
+    const float dzab = z0 - cluster_z[hb];
+    const float tx = (x0 - cluster_x[hb]) / dzab, ty = (y0 - cluster_y[hb]) / dzab;
+    // 1. the straight line at the kick plane
+    const float dzm = geo->z_mag - z0;
+    const float xm = x0 + tx * dzm, ym = y0 + ty * dzm;
+    bool have = false;
+    uint32_t b_n = 0, b_c = 0;
+    float b_r = 0.0f, b_b = 0.0f, b_a = 0.0f, b_d = 0.0f, b_dy = 0.0f, b_ad = 0.0f;
+    uint32_t b_hits[VO_FWD_LAYERS];
+    for (int r = 0; r < 2; ++r) {
+      // 2. candidates in the first two layers
+      const float dzr = geo->z_layers[r] - geo->z_mag;
+      const float xr = xm + tx * dzr, yr = ym + ty * dzr;
+      const float wx = (geo->kappa / p->p_min) * dzr + p->tol_x;
+      for (uint64_t c = 0; c < n_hits; ++c) {
+        if (layer[c] != (uint32_t)r) continue;
+        if (std::fabs(x[c] - xr) > wx || std::fabs(y[c] - yr) > p->win_y) continue;
+        // 3. the slope behind the magnet; the first station from it, the
+        // others from the line through the first station's hits
+        const float tk = (x[c] - xm) / dzr;
+        uint32_t hl[VO_FWD_LAYERS];
+        auto nearest = [&](int L, float xp, float yp, float tol) -> uint32_t {
+          bool f = false;
+          float bd = 0.0f;
+          uint32_t bh = 0xFFFFFFFFu;
+          for (uint64_t h = 0; h < n_hits; ++h) {
+            if (layer[h] != (uint32_t)L) continue;
+            const float d = std::fabs(x[h] - xp);
+            if (d > tol || std::fabs(y[h] - yp) > p->tol_y) continue;
+            if (!f || d < bd || (d == bd && h < bh)) { f = true; bd = d; bh = (uint32_t)h; }
+          }
+          return bh;
+        };
+        // least-squares line x = a + b (z - z_0) through the found hits of layers [l0, l1)
+        auto line = [&](int l0, int l1, float* a_out, float* b_out) -> uint32_t {
+          float S0 = 0.0f, Sz = 0.0f, Szz = 0.0f, Sx = 0.0f, Sxz = 0.0f;
+          uint32_t k = 0;
+          for (int L = l0; L < l1; ++L) {
+            if (hl[L] == 0xFFFFFFFFu) continue;
+            const float dz = geo->z_layers[L] - geo->z_layers[0];
+            S0 = S0 + 1.0f;
+            Sz = Sz + dz;
+            Szz = Szz + dz * dz;
+            Sx = Sx + x[hl[L]];
+            Sxz = Sxz + x[hl[L]] * dz;
+            ++k;
+          }
+          const float det = S0 * Szz - Sz * Sz;
+          const float bb = (S0 * Sxz - Sz * Sx) / det;
+          *b_out = bb;
+          *a_out = (Sx - bb * Sz) / S0;
+          return k;
+        };
+        uint32_t n1 = 0;
+        for (int L = 0; L < 4; ++L) {
+          const float dzl = geo->z_layers[L] - geo->z_mag;
+          hl[L] = nearest(L, xm + tk * dzl, ym + ty * dzl, p->tol_x);
+          n1 += hl[L] != 0xFFFFFFFFu ? 1u : 0u;
+        }
+        if (n1 < 2) continue;
+        float a1, b1;
+        line(0, 4, &a1, &b1);
+        uint32_t n = n1;
+        for (int L = 4; L < NL; ++L) {
+          const float dzl = geo->z_layers[L] - geo->z_mag;
+          hl[L] = nearest(L, a1 + b1 * (geo->z_layers[L] - geo->z_layers[0]), ym + ty * dzl, p->tol_x_far);
+          n += hl[L] != 0xFFFFFFFFu ? 1u : 0u;
+        }
+        if (n < p->min_hits) continue;
+        // 4. straight line through all of them and its chi2
+        float a, b;
+        line(0, NL, &a, &b);
+        float chi2 = 0.0f;
+        for (int L = 0; L < NL; ++L) {
+          if (hl[L] == 0xFFFFFFFFu) continue;
+          const float dz = geo->z_layers[L] - geo->z_layers[0];
+          const float res = ((x[hl[L]] - a) - b * dz) / p->sigma_x;
+          chi2 = chi2 + res * res;
+        }
+        const float rchi = chi2 / (float)(n - 2);
+        if (!(rchi <= p->chi2ndf_max)) continue;
+        // 4-5. the y line and the match at the kick plane, in x and in y (y is not bent)
+        const float d = (a + b * (geo->z_mag - geo->z_layers[0])) - xm;
+        float Y0 = 0.0f, Yz = 0.0f, Yzz = 0.0f, Yy = 0.0f, Yyz = 0.0f;
+        for (int L = 0; L < NL; ++L) {
+          if (hl[L] == 0xFFFFFFFFu) continue;
+          const float dz = geo->z_layers[L] - geo->z_layers[0];
+          Y0 = Y0 + 1.0f;
+          Yz = Yz + dz;
+          Yzz = Yzz + dz * dz;
+          Yy = Yy + y[hl[L]];
+          Yyz = Yyz + y[hl[L]] * dz;
+        }
+        const float ydet = Y0 * Yzz - Yz * Yz;
+        const float yb = (Y0 * Yyz - Yz * Yy) / ydet;
+        const float ya = (Yy - yb * Yz) / Y0;
+        const float dy = (ya + yb * (geo->z_mag - geo->z_layers[0])) - ym;
+        const float ad = d * d + dy * dy;
+        if (!(ad <= p->tol_match * p->tol_match)) continue;
+        // 6. most hits, then the smallest distance, then the smallest candidate id
+        const bool better = !have || n > b_n || (n == b_n && (ad < b_ad || (ad == b_ad && c < b_c)));
+        if (!better) continue;
+        have = true;
+        b_n = n;
+        b_c = (uint32_t)c;
+        b_r = rchi;
+        b_b = b;
+        b_a = a;
+        b_d = d;
+        b_dy = dy;
+        b_ad = ad;
+        for (int L = 0; L < NL; ++L) b_hits[L] = hl[L];
+      }
+    }
+    n_found[t] = have ? b_n : 0u;
+    for (int L = 0; L < NL; ++L) hits[t * NL + L] = have ? b_hits[L] : 0xFFFFFFFFu;
+    float* so = state + t * VO_FWD_STATE;
+    so[0] = have ? (b_b - tx) / geo->kappa : 0.0f;
+    so[1] = have ? b_r : 0.0f;
+    so[2] = have ? b_b : 0.0f;
+    so[3] = have ? b_a : 0.0f;
+    so[4] = have ? b_d : 0.0f;
+    so[5] = have ? b_dy : 0.0f;
+  }
+}
+
 }  // extern "C"

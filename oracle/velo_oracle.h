@@ -116,6 +116,69 @@ void vo_batch_copy(void* h, int32_t* status, uint64_t* cluster_offsets, float* c
                    uint32_t* track_hits, float* track_states, float* track_features);
 void vo_batch_free(void* h);
 
+/* ---- Forward tracking (pixel-tracker tracks traced to a downstream tracker)
+ *
+ * The paper traces pixel-tracker tracks forwards: straight to the middle of
+ * the magnet, where the field acts as one change of angle, then straight to
+ * the fibre tracker, keeping a track when enough hits with a low enough chi2
+ * are found (Sec. "HLT1 details and results").  It gives no geometry and no
+ * algorithm; this is the project's reading, on an invented downstream
+ * geometry (12 layers measuring (x, y), a kick plane at z_mag, a kick
+ * kappa q / p to tx only), every step in binary32 in the written order.
+ * Per pixel-tracker track:
+ *   0. the line through its two most downstream hits a (last) and b:
+ *      tx = (x_a - x_b) / (z_a - z_b), ty likewise, from (x_a, y_a, z_a);
+ *   1. xm = x_a + tx (z_mag - z_a), ym = y_a + ty (z_mag - z_a);
+ *   2. candidates: every hit c of the two first layers r (r = 0, 1) with
+ *      |x_c - (xm + tx dz_r)| <= (kappa / p_min) dz_r + tol_x and
+ *      |y_c - (ym + ty dz_r)| <= win_y, dz_r = z_r - z_mag;
+ *   3. a candidate gives the slope behind the magnet t = (x_c - xm) / dz_r;
+ *      in each layer L of the first station (0-3) it takes the hit nearest
+ *      to xm + t dz_L in x (ties: the smaller id) with
+ *      |x - (xm + t dz_L)| <= tol_x and |y - (ym + ty dz_L)| <= tol_y; with
+ *      fewer than 2 such hits the candidate is dropped; the straight line
+ *      through them (least squares as in 4.) then predicts the layers of the
+ *      other stations, where the nearest hit within tol_x_far (and tol_y) is
+ *      taken;
+ *   4. a candidate with n >= min_hits hits is fitted by the straight lines
+ *      x = a + b (z - z_0) and y = ay + by (z - z_0) (least squares, sums in
+ *      layer order S0, Sz, Szz, Sx, Sxz, dz = z_L - z_0) with
+ *      chi2 = sum (((x - a) - b dz) / sigma_x)^2 over n - 2;
+ *   5. behind a single kick the lines meet the pixel-tracker line at the
+ *      kick plane: d_x = (a + b (z_mag - z_0)) - xm, d_y likewise with ym,
+ *      D = d_x^2 + d_y^2;
+ *   6. among candidates with chi2/ndf <= chi2ndf_max and D <= tol_match^2
+ *      the one with the most hits, then the smallest D, then the smallest
+ *      candidate id wins; its q/p = (b - tx) / kappa.
+ * Outputs per track: n (0 = none), hit ids per layer (0xFFFFFFFF = none),
+ * state[VO_FWD_STATE] = q/p, chi2/ndf, b, a, d_x, d_y. */
+#define VO_FWD_LAYERS 12
+#define VO_FWD_STATE 6
+typedef struct vo_downstream {
+  float z_mag;
+  float z_layers[VO_FWD_LAYERS];
+  float kappa;
+} vo_downstream_t;
+typedef struct vo_fwd_params {
+  float p_min;        /* GeV/c: smallest momentum whose kick is searched */
+  float win_y;        /* mm, candidate window in y */
+  float tol_x, tol_y; /* mm, hit collection windows around a candidate's prediction */
+  float tol_x_far;    /* mm, in x in the stations after the first */
+  float sigma_x;      /* mm, for the chi2 */
+  float tol_match;    /* mm, distance of the lines at the kick plane */
+  float chi2ndf_max;
+  uint32_t min_hits;
+} vo_fwd_params_t;
+/* One event: downstream hits (layer, x, y) in any order, ids = their
+ * indices; pixel-tracker tracks as hit lists (track_hit_offsets[n_tracks+1]
+ * into track_hits: event-local cluster ids ascending, >= 2 per track) over
+ * the event's clusters (x, y, z by id).  Writes n_found[t],
+ * hits[t * 12 + L], state[t * VO_FWD_STATE + k]. */
+void vo_forward_event(uint64_t n_hits, const uint32_t* layer, const float* x, const float* y, uint64_t n_tracks,
+                      const uint64_t* track_hit_offsets, const uint32_t* track_hits, const float* cluster_x,
+                      const float* cluster_y, const float* cluster_z, const vo_downstream_t* geo,
+                      const vo_fwd_params_t* p, uint32_t* n_found, uint32_t* hits, float* state);
+
 #ifdef __cplusplus
 }
 #endif

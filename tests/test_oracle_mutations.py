@@ -7,7 +7,8 @@ one pin must fail.  The mistakes are planted in the oracle only, on the CPU;
 the product library is not involved.  Each case names the step of the method
 it breaks (centroid, connectivity, pseudo-angle window, straight-line and
 Kalman fits, chi2/ndf and the 3-hit rule, extension, seeding and its
-conflicts, termination, learned-rejection features and bfloat16 rounding).
+conflicts, termination, learned-rejection features and bfloat16 rounding,
+forward tracking).
 """
 import concurrent.futures
 import os
@@ -19,7 +20,8 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PIN_TESTS = ("test_oracle_cluster.py", "test_oracle_fit.py", "test_oracle_track.py", "test_oracle_mlp.py")
+PIN_TESTS = ("test_oracle_cluster.py", "test_oracle_fit.py", "test_oracle_track.py", "test_oracle_mlp.py",
+             "test_oracle_forward.py")
 
 # (name, exact source text, replacement): each text occurs once in velo_oracle.cpp
 MUTATIONS = [
@@ -32,7 +34,7 @@ MUTATIONS = [
     ("window distance without the wrap at 4",
      "if (d > 2.0f) d = 4.0f - d;", "if (d > 4.0f) d = 4.0f - d;"),
     ("straight-line fit: Szz sums dz instead of dz^2",
-     "Szz = Szz + dz * dz;", "Szz = Szz + dz;"),
+     "    Sz = Sz + dz;\n    Szz = Szz + dz * dz;", "    Sz = Sz + dz;\n    Szz = Szz + dz;"),
     ("straight-line fit: intercept with the wrong sign",
      "R x = (Sx - tx * Sz) / S0;", "R x = (Sx + tx * Sz) / S0;"),
     ("Kalman start without the process noise",
@@ -67,6 +69,23 @@ MUTATIONS = [
      "u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0x8000u;"),
     ("feature RMS without the square root",
      "f[8] = std::sqrt(sxx / fn);", "f[8] = sxx / fn;"),
+    ("forward: q/p with the wrong sign",
+     "so[0] = have ? (b_b - tx) / geo->kappa : 0.0f;", "so[0] = have ? (tx - b_b) / geo->kappa : 0.0f;"),
+    ("forward: chi2 over n - 1",
+     "const float rchi = chi2 / (float)(n - 2);", "const float rchi = chi2 / (float)(n - 1);"),
+    ("forward: match distance without y",
+     "const float ad = d * d + dy * dy;", "const float ad = d * d;"),
+    ("forward: far stations from the kick line",
+     "hl[L] = nearest(L, a1 + b1 * (geo->z_layers[L] - geo->z_layers[0]), ym + ty * dzl, p->tol_x_far);",
+     "hl[L] = nearest(L, xm + tk * dzl, ym + ty * dzl, p->tol_x_far);"),
+    ("forward: fewer hits preferred",
+     "const bool better = !have || n > b_n ||", "const bool better = !have || n < b_n ||"),
+    ("forward: nearest-hit tie to the larger id",
+     "if (!f || d < bd || (d == bd && h < bh)) { f = true; bd = d; bh = (uint32_t)h; }\n          }\n          return bh;",
+     "if (!f || d < bd || (d == bd && h > bh)) { f = true; bd = d; bh = (uint32_t)h; }\n          }\n          return bh;"),
+    ("forward: line from the two most upstream hits",
+     "const uint32_t ha = track_hits[track_hit_offsets[t + 1] - 1], hb = track_hits[track_hit_offsets[t + 1] - 2];",
+     "const uint32_t ha = track_hits[track_hit_offsets[t] + 1], hb = track_hits[track_hit_offsets[t]];"),
 ]
 
 

@@ -28,7 +28,9 @@ _SRC = os.path.join(_HERE, "velogen.cpp")
 _LIB = os.path.join(_HERE, "libvelogen.so")
 
 N_MODULES = 26
-PARTICLE_FIELDS = 10  # pv, x0, y0, z0, tx, ty, eta, phi, n_modules_with_pixels, heavy_ion
+# pv, x0, y0, z0, tx, ty, eta, phi, n_modules_with_pixels, heavy_ion, then the line the
+# particle leaves the pixel tracker on: x, y, z, tx, ty (after the last kink)
+PARTICLE_FIELDS = 15
 
 
 def module_z() -> np.ndarray:
@@ -167,8 +169,10 @@ class Batch:
     pixels: np.ndarray             # uint32 [n_pixels]
     pixel_truth: np.ndarray | None = None       # int32 [n_pixels], -1 = noise
     particle_offsets: np.ndarray | None = None  # uint64 [n_events + 1]
-    particles: np.ndarray | None = None         # float64 [n_particles, 10]
+    particles: np.ndarray | None = None         # float64 [n_particles, PARTICLE_FIELDS]
     geometry: Geometry = field(default_factory=Geometry)
+    first_event: int = 0                        # index of the batch's first event in its stream
+    seed: int = 0                               # the configuration's seed
 
     @property
     def n_events(self) -> int:
@@ -219,7 +223,7 @@ def generate(cfg: Config, n_events: int | None = None, first_event: int = 0, tru
             raise RuntimeError(f"velogen_copy failed ({rc})")
     finally:
         lib.velogen_free(h)
-    return Batch(offsets, pixels, ptruth, poff, parts, geometry)
+    return Batch(offsets, pixels, ptruth, poff, parts, geometry, int(first_event), int(cfg.seed))
 
 
 def with_events(cfg: Config, n_events: int) -> Config:

@@ -66,9 +66,11 @@ typedef struct velogen_geometry {
   double r_min, r_max;    // sensitive annulus, judged at the pixel centre [mm]
 } velogen_geometry_t;
 
-// Per particle record (float64 x 10):
-//   pv, x0, y0, z0, tx, ty, eta, phi, n_modules_with_pixels, heavy_ion_event
-enum { VELOGEN_PARTICLE_FIELDS = 10 };
+// Per particle record (float64 x 15):
+//   pv, x0, y0, z0, tx, ty, eta, phi, n_modules_with_pixels, heavy_ion_event,
+//   and the line it leaves the pixel tracker on (after the last kink):
+//   x, y, z, tx, ty there (the vertex and first direction if it crossed no module)
+enum { VELOGEN_PARTICLE_FIELDS = 15 };
 
 }  // extern "C"
 
@@ -210,7 +212,7 @@ struct Gen {
         }
         if (want_truth) {
           double rec[VELOGEN_PARTICLE_FIELDS] = {(double)v, vx, vy, vz, tx0, ty0, eta, phi,
-                                                 (double)n_mod_dep, hi ? 1.0 : 0.0};
+                                                 (double)n_mod_dep, hi ? 1.0 : 0.0, x, y, z, tx, ty};
           parts.insert(parts.end(), rec, rec + VELOGEN_PARTICLE_FIELDS);
         }
       }
@@ -322,7 +324,7 @@ int velogen_sizes(void* hv, uint64_t* n_events, uint64_t* n_pixels, uint64_t* n_
 
 // Copies the generated batch out. Any output pointer may be NULL.
 //   offsets[n_events+1], pixels[n_pixels], pixel_truth[n_pixels],
-//   particle_offsets[n_events+1], particles[n_particles * 10]
+//   particle_offsets[n_events+1], particles[n_particles * VELOGEN_PARTICLE_FIELDS]
 int velogen_copy(void* hv, uint64_t* offsets, uint32_t* pixels, int32_t* pixel_truth,
                  uint64_t* particle_offsets, double* particles) {
   Handle* h = (Handle*)hv;
