@@ -290,6 +290,97 @@ int velo_mlp_adam_step(float* w, const float* grad, float* m, float* v, uint32_t
                        float beta2, float eps, uint32_t step, void* stream);
 
 /* Name of a VELO_* return code. */
+/* ---- Forward tracking: pixel-tracker tracks traced to a downstream tracker
+ *
+ * The first stage traces pixel-tracker tracks forwards: straight to the
+ * middle of the magnet, where the field is taken as one change of angle, then
+ * straight to the fibre tracker, keeping a track when enough hits with a low
+ * enough chi2 are found (Sec. "HLT1 details and results").  The paper gives
+ * neither the geometry nor the algorithm; this library reads it on a
+ * downstream tracker of VELO_FWD_LAYERS planar layers measuring (x, y) and a
+ * kick plane at z_mag (kick kappa q / p to tx, none to ty), every step in
+ * binary32 in a fixed order (the CPU oracle defines the same steps):
+ *   0. the track's line through its two most downstream clusters a, b:
+ *      tx = (x_a - x_b) / (z_a - z_b), ty likewise;
+ *   1. xm = x_a + tx (z_mag - z_a), ym likewise: the line at the kick plane;
+ *   2. candidates: hits c of layers 0 and 1 with
+ *      |x_c - (xm + tx dz)| <= (kappa / p_min) dz + tol_x, |y_c - (ym + ty dz)|
+ *      <= win_y, dz = z_layer - z_mag;
+ *   3. slope t = (x_c - xm) / dz; in layers 0-3 the nearest hit in x to
+ *      xm + t dz_L (ties: smaller id) within tol_x (and tol_y in y); at least
+ *      2 of them, whose least-squares line predicts layers 4-11 (nearest hit
+ *      within tol_x_far);
+ *   4. n >= min_hits: least-squares lines x = a + b (z - z_layer0),
+ *      y = ay + by (z - z_layer0), chi2 = sum (((x - a) - b dz) / sigma_x)^2;
+ *   5. match at the kick plane d_x = a + b (z_mag - z_layer0) - xm, d_y
+ *      likewise, D = d_x^2 + d_y^2;
+ *   6. among candidates with chi2 / (n - 2) <= chi2ndf_max and
+ *      D <= tol_match^2: most hits, then smallest D, then smallest candidate
+ *      id; q/p = (b - tx) / kappa.
+ * Tracks are searched independently (a hit may serve several tracks). */
+#define VELO_FWD_LAYERS 12u
+#define VELO_FWD_STATE 6u /* q/p, chi2/ndf, b (slope behind the magnet), a (x at layer 0), d_x, d_y */
+
+typedef struct velo_downstream {
+  float z_mag;                    /* mm */
+  float z_layers[VELO_FWD_LAYERS];/* mm, ascending; layers 0-3 form the first station */
+  float kappa;                    /* GeV/c * rad: kick = kappa * q / p */
+} velo_downstream_t;
+
+typedef struct velo_forward_params {
+  float p_min;        /* GeV/c: smallest momentum whose kick is searched */
+  float win_y;        /* mm: candidate window in y */
+  float tol_x, tol_y; /* mm: hit windows around a candidate's prediction */
+  float tol_x_far;    /* mm: in x in layers 4-11 */
+  float sigma_x;      /* mm: for the chi2 */
+  float tol_match;    /* mm: distance of the lines at the kick plane */
+  float chi2ndf_max;
+  uint32_t min_hits;
+} velo_forward_params_t;
+
+/* Downstream hits in CSR form, DEVICE pointers: hits of event e at
+ * [event_offsets[e], event_offsets[e+1]) in any order; a hit's id is its
+ * index inside its event.  Hits with layer >= VELO_FWD_LAYERS, or an x
+ * or y that is not finite, are never taken (a window test holds only for a
+ * distance that is a number within the tolerance). */
+typedef struct velo_downstream_hits {
+  uint64_t n_events;
+  uint64_t n_hits;
+  const uint64_t* event_offsets; /* [n_events + 1] */
+  const uint32_t* layer;         /* [n_hits] */
+  const float* x;                /* [n_hits] mm */
+  const float* y;                /* [n_hits] mm */
+} velo_downstream_hits_t;
+
+/* Per pixel-tracker track (the batch-global track index of the result),
+ * DEVICE pointers, capacity cap_tracks (tracks beyond it are not written). */
+typedef struct velo_forward_output {
+  uint32_t* n_found;  /* [cap_tracks] hits found, 0 = no downstream track */
+  uint32_t* hits;     /* [cap_tracks * VELO_FWD_LAYERS] event-local hit ids, 0xFFFFFFFF = none */
+  float* state;       /* [cap_tracks * VELO_FWD_STATE] */
+  uint64_t cap_tracks;
+} velo_forward_output_t;
+
+int velo_forward_params_default(velo_forward_params_t* params);
+/* Device scratch velo_forward needs for a batch of n_events / n_hits. */
+int velo_forward_workspace_size(uint64_t n_events, uint64_t n_hits, uint64_t* bytes);
+/* Forward tracking of the tracks of a reconstruction result `tracks` (the
+ * device outputs of velo_reconstruct_into on the same events, in order;
+ * cluster_offsets, cluster_x/y/z, track_offsets, track_hit_offsets,
+ * track_hits and totals are read), on `stream`, asynchronously.  Workspace:
+ * 256-byte aligned, >= velo_forward_workspace_size.  VELO_EINVAL for a NULL
+ * or inconsistent argument (a parameter or z that is not finite, z_layers not
+ * ascending behind z_mag, min_hits outside [3, 12], a non-positive p_min,
+ * sigma_x or kappa), VELO_ECAPACITY for a small workspace.  Event offsets
+ * that do not start at 0, decrease, end past n_hits or give an event 2^31
+ * hits leave every track without a downstream track (n 0, no hits, state
+ * 0); a track of fewer than two hits never has one; a result whose totals
+ * exceed its capacities (no track lists written) makes velo_forward write
+ * nothing. */
+int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks, const velo_downstream_t* geometry,
+                 const velo_forward_params_t* params, const velo_forward_output_t* out, void* workspace,
+                 uint64_t workspace_bytes, void* stream);
+
 /* Measurement helper, not part of the method: the FP32 multiply-add rate of
  * the current device (flops/s, 2 per FMA), from a kernel of independent FMA
  * chains on every SM timed with CUDA events on `stream` (best of three

@@ -14,6 +14,7 @@ module docstring of ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import ctypes
 import os
 import subprocess
@@ -281,12 +282,14 @@ def downstream_struct(down) -> _Down:
     return d
 
 
-def forward(scifi_offsets, layer, x, y, result, down, params: FwdParams = FwdParams()):
+def forward(scifi_offsets, layer, x, y, result, down, params: FwdParams = FwdParams(), threads: int = 0):
     """Forward tracking of a batch: downstream hits in CSR (per event, ids =
     index within the event) and a reconstruction result (numpy dict with
     cluster_offsets, cluster_x/y/z, track_offsets, track_hit_offsets,
     track_hits).  Returns n_found [T], hits [T, 12] (event-local hit ids,
-    0xFFFFFFFF = none), state [T, 6] = (q/p, chi2/ndf, b, a, d_x, d_y)."""
+    0xFFFFFFFF = none), state [T, 6] = (q/p, chi2/ndf, b, a, d_x, d_y).
+    Events are independent; `threads` (0 = every core) run them side by side
+    (each event is one call of the C function, which releases the GIL)."""
     lib = _load()
     so = np.asarray(scifi_offsets, np.int64)
     to = np.asarray(result["track_offsets"], np.int64)
@@ -305,13 +308,21 @@ def forward(scifi_offsets, layer, x, y, result, down, params: FwdParams = FwdPar
     state = np.zeros((max(T, 1), FWD_STATE), np.float32)
     d = downstream_struct(down)
     p = _FwdPar(**asdict(params))
-    for e in range(len(to) - 1):
+    def one(e):
         h0, h1, t0, t1, c0 = int(so[e]), int(so[e + 1]), int(to[e]), int(to[e + 1]), int(co[e])
         if t1 == t0:
-            continue
+            return
         ho = np.ascontiguousarray(hoff[t0:t1 + 1] - hoff[t0])
         tk = np.ascontiguousarray(th[int(hoff[t0]):int(hoff[t1])])
         lib.vo_forward_event(h1 - h0, _ptr(layer[h0:h1]), _ptr(x[h0:h1]), _ptr(y[h0:h1]), t1 - t0, _ptr(ho), _ptr(tk),
                              _ptr(cx[c0:]), _ptr(cy[c0:]), _ptr(cz[c0:]), ctypes.byref(d), ctypes.byref(p),
                              _ptr(n_found[t0:t1]), _ptr(hits[t0:t1]), _ptr(state[t0:t1]))
+
+    n_thr = threads if threads > 0 else (os.cpu_count() or 1)
+    if n_thr == 1 or len(to) <= 2:
+        for e in range(len(to) - 1):
+            one(e)
+    else:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=n_thr) as ex:
+            list(ex.map(one, range(len(to) - 1)))
     return n_found[:T], hits[:T], state[:T]

@@ -669,6 +669,10 @@ void vo_forward_event(uint64_t n_hits, const uint32_t* layer, const float* x, co
                       const vo_fwd_params_t* p, uint32_t* n_found, uint32_t* hits, float* state) {
   const int NL = VO_FWD_LAYERS;
   for (uint64_t t = 0; t < n_tracks; ++t) {
+    n_found[t] = 0u;
+    for (int L = 0; L < NL; ++L) hits[t * NL + L] = 0xFFFFFFFFu;
+    for (int k = 0; k < VO_FWD_STATE; ++k) state[t * VO_FWD_STATE + k] = 0.0f;
+    if (track_hit_offsets[t + 1] < track_hit_offsets[t] + 2) continue;  // no line through fewer than two hits
     // 0. the line through the two most downstream hits (ids ascend with z)
     const uint32_t ha = track_hits[track_hit_offsets[t + 1] - 1], hb = track_hits[track_hit_offsets[t + 1] - 2];
     const float x0 = cluster_x[ha], y0 = cluster_y[ha], z0 = cluster_z[ha];
@@ -688,7 +692,8 @@ void vo_forward_event(uint64_t n_hits, const uint32_t* layer, const float* x, co
       const float wx = (geo->kappa / p->p_min) * dzr + p->tol_x;
       for (uint64_t c = 0; c < n_hits; ++c) {
         if (layer[c] != (uint32_t)r) continue;
-        if (std::fabs(x[c] - xr) > wx || std::fabs(y[c] - yr) > p->win_y) continue;
+        // a distance that is not a number never lies within a window
+        if (!(std::fabs(x[c] - xr) <= wx) || !(std::fabs(y[c] - yr) <= p->win_y)) continue;
         // 3. the slope behind the magnet; the first station from it, the
         // others from the line through the first station's hits
         const float tk = (x[c] - xm) / dzr;
@@ -700,7 +705,7 @@ void vo_forward_event(uint64_t n_hits, const uint32_t* layer, const float* x, co
           for (uint64_t h = 0; h < n_hits; ++h) {
             if (layer[h] != (uint32_t)L) continue;
             const float d = std::fabs(x[h] - xp);
-            if (d > tol || std::fabs(y[h] - yp) > p->tol_y) continue;
+            if (!(d <= tol) || !(std::fabs(y[h] - yp) <= p->tol_y)) continue;
             if (!f || d < bd || (d == bd && h < bh)) { f = true; bd = d; bh = (uint32_t)h; }
           }
           return bh;

@@ -171,9 +171,11 @@ typedef struct vo_fwd_params {
 } vo_fwd_params_t;
 /* One event: downstream hits (layer, x, y) in any order, ids = their
  * indices; pixel-tracker tracks as hit lists (track_hit_offsets[n_tracks+1]
- * into track_hits: event-local cluster ids ascending, >= 2 per track) over
- * the event's clusters (x, y, z by id).  Writes n_found[t],
- * hits[t * 12 + L], state[t * VO_FWD_STATE + k]. */
+ * into track_hits: event-local cluster ids ascending; a track of fewer than
+ * two gets no downstream track) over the event's clusters (x, y, z by id).
+ * A window test holds only for a distance that is a number within its
+ * tolerance, so hits with a coordinate that is not finite are never taken.
+ * Writes n_found[t], hits[t * 12 + L], state[t * VO_FWD_STATE + k]. */
 void vo_forward_event(uint64_t n_hits, const uint32_t* layer, const float* x, const float* y, uint64_t n_tracks,
                       const uint64_t* track_hit_offsets, const uint32_t* track_hits, const float* cluster_x,
                       const float* cluster_y, const float* cluster_z, const vo_downstream_t* geo,

@@ -76,6 +76,30 @@ class ResultView(ctypes.Structure):
                 ("cap_tracks", ctypes.c_uint64), ("cap_track_hits", ctypes.c_uint64), ("out", Output)]
 
 
+FWD_LAYERS = 12
+FWD_STATE = 6
+FWD_STATE_FIELDS = ("qop", "chi2ndf", "b", "a", "d_x", "d_y")
+
+
+class Downstream(ctypes.Structure):
+    _fields_ = [("z_mag", ctypes.c_float), ("z_layers", ctypes.c_float * FWD_LAYERS), ("kappa", ctypes.c_float)]
+
+
+class ForwardParams(ctypes.Structure):
+    _fields_ = [("p_min", ctypes.c_float), ("win_y", ctypes.c_float), ("tol_x", ctypes.c_float),
+                ("tol_y", ctypes.c_float), ("tol_x_far", ctypes.c_float), ("sigma_x", ctypes.c_float),
+                ("tol_match", ctypes.c_float), ("chi2ndf_max", ctypes.c_float), ("min_hits", ctypes.c_uint32)]
+
+
+class DownstreamHits(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint64), ("n_hits", ctypes.c_uint64), ("event_offsets", _P), ("layer", _P),
+                ("x", _P), ("y", _P)]
+
+
+class ForwardOutput(ctypes.Structure):
+    _fields_ = [("n_found", _P), ("hits", _P), ("state", _P), ("cap_tracks", ctypes.c_uint64)]
+
+
 class VeloError(RuntimeError):
     pass
 
@@ -87,7 +111,8 @@ EXPORTS = ("velo_params_default", "velo_query_sizes", "velo_reconstruct_into", "
            "velo_tuning_default", "velo_reconstruct_into_tuned", "velo_reconstruct",
            "velo_result_view", "velo_result_free", "velo_context_create", "velo_context_destroy",
            "velo_context_set_pipeline", "velo_reconstruct_host", "velo_reconstruct_static", "velo_mlp_infer", "velo_mlp_workspace_size",
-           "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_measure_fp32_peak", "velo_strerror", "velo_version")
+           "velo_mlp_loss_grad", "velo_mlp_adam_step", "velo_forward_params_default", "velo_forward_workspace_size",
+           "velo_forward", "velo_measure_fp32_peak", "velo_strerror", "velo_version")
 
 
 def lib():
@@ -122,6 +147,11 @@ def lib():
         L.velo_mlp_loss_grad.argtypes = [_P, _P, ctypes.c_uint64, _P, _P, _P, _P, ctypes.c_uint64, _P]
         L.velo_mlp_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, ctypes.c_float, ctypes.c_uint32, _P]
+        L.velo_forward_params_default.argtypes = [ctypes.POINTER(ForwardParams)]
+        L.velo_forward_workspace_size.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+        L.velo_forward.argtypes = [ctypes.POINTER(DownstreamHits), ctypes.POINTER(Output), ctypes.POINTER(Downstream),
+                                   ctypes.POINTER(ForwardParams), ctypes.POINTER(ForwardOutput), _P, ctypes.c_uint64,
+                                   _P]
         L.velo_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _P]
         L.velo_strerror.restype = ctypes.c_char_p
         L.velo_strerror.argtypes = [ctypes.c_int]
@@ -171,4 +201,23 @@ def query_sizes(n_events: int, n_pixels: int) -> Sizes:
     return s
 
 
+def default_forward_params(**overrides) -> ForwardParams:
+    p = ForwardParams()
+    check(lib().velo_forward_params_default(ctypes.byref(p)), "velo_forward_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def downstream_struct(g) -> Downstream:
+    """From any object with z_mag, z_layers (12), kappa."""
+    d = Downstream()
+    d.z_mag = float(g.z_mag)
+    for i, z in enumerate(g.z_layers):
+        d.z_layers[i] = float(z)
+    d.kappa = float(g.kappa)
+    return d
+
+
 from .api import GraphReconstructor, HostReconstructor, Reconstructor, reconstruct  # noqa: E402,F401
+from .forward import ForwardTracker  # noqa: E402,F401

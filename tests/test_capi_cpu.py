@@ -70,6 +70,46 @@ def test_argument_validation_before_any_device_call(L, geometry):
     assert call(ctypes.byref(ev), ctypes.byref(g.s), ctypes.byref(p), ctypes.byref(nul), ws, 1 << 40) == velo.EINVAL
 
 
+def test_forward_argument_validation_before_any_device_call(L):
+    from velogen import scifi
+    d = velo.downstream_struct(scifi.Downstream())
+    p = velo.default_forward_params()
+    assert (p.p_min, p.tol_x_far, p.sigma_x, p.min_hits) == (3.0, 3.0, pytest.approx(0.08), 9)
+    trk = velo.Output(*([ctypes.c_void_p(256)] * 11))
+    h = velo.DownstreamHits(1, 10, *([ctypes.c_void_p(256)] * 4))
+    o = velo.ForwardOutput(ctypes.c_void_p(256), ctypes.c_void_p(256), ctypes.c_void_p(256), 10)
+    ws = ctypes.c_void_p(1 << 20)
+    need = ctypes.c_uint64()
+    assert L.velo_forward_workspace_size(1, 10, ctypes.byref(need)) == velo.OK
+    assert need.value % 256 == 0 and need.value >= 10 * 24
+    big = ctypes.c_uint64()
+    L.velo_forward_workspace_size(1, 1000, ctypes.byref(big))
+    assert big.value > need.value
+
+    def call(hh=h, pp=p, dd=d, w=ws, nbytes=1 << 40, oo=o, tt=trk):
+        return L.velo_forward(ctypes.byref(hh) if hh is not None else None, ctypes.byref(tt), ctypes.byref(dd),
+                              ctypes.byref(pp), ctypes.byref(oo), w, nbytes, None)
+
+    assert call(hh=None) == velo.EINVAL
+    for k, v in (("min_hits", 2), ("min_hits", 13), ("p_min", 0.0), ("sigma_x", -1.0), ("tol_x", float("nan")),
+                 ("tol_match", float("inf")), ("p_min", 1e-44)):
+        assert call(pp=velo.default_forward_params(**{k: v})) == velo.EINVAL, (k, v)
+    dz = velo.downstream_struct(scifi.Downstream())
+    dz.z_layers[5] = dz.z_layers[4]  # not strictly ascending
+    assert call(dd=dz) == velo.EINVAL
+    dz = velo.downstream_struct(scifi.Downstream())
+    dz.z_mag = dz.z_layers[0] + 1.0  # a layer in front of the kick plane
+    assert call(dd=dz) == velo.EINVAL
+    dz = velo.downstream_struct(scifi.Downstream())
+    dz.kappa = 0.0
+    assert call(dd=dz) == velo.EINVAL
+    assert call(w=ctypes.c_void_p((1 << 20) + 16)) == velo.EINVAL  # misaligned workspace
+    assert call(nbytes=need.value - 1) == velo.ECAPACITY
+    no_totals = velo.Output(*([ctypes.c_void_p(256)] * 10 + [None]))
+    assert call(tt=no_totals) == velo.EINVAL
+    assert call(oo=velo.ForwardOutput(None, ctypes.c_void_p(256), ctypes.c_void_p(256), 10)) == velo.EINVAL
+
+
 def test_no_cpu_fallback(monkeypatch, tmp_path):
     """Without the built library every call raises instead of computing elsewhere."""
     import importlib

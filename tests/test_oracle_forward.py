@@ -178,3 +178,36 @@ def test_generated_events_invariants():
             res.append(abs(st[t][0] - qop) / abs(qop))
     assert own >= 0.85 * len(found)
     assert np.median(res) <= 0.02
+
+
+def test_non_finite_hits_never_taken():
+    """A window test holds only for a distance that is a number: hits on the
+    track's x with a NaN y, and hits with a NaN or infinite x, are never
+    taken, even with the smaller ids (as distances they would tie or beat
+    the real hits under a plain `>` rejection)."""
+    exact = track_hits(LINE, 0.1)
+    nan = float("nan")
+    bad = [(L, x, nan) for (L, x, y) in exact] + [(L, nan, y) for (L, x, y) in exact[:6]] + \
+          [(L, float("inf"), y) for (L, x, y) in exact[6:]]
+    n, h, st = run([LINE], bad + exact)
+    assert n[0] == 12 and list(h[0]) == list(range(24, 36))
+    n0, _, st0 = run([LINE], exact)
+    assert np.array_equal(st[0], st0[0])
+
+
+def test_track_of_one_hit_has_no_line():
+    """A pixel-tracker track of fewer than two hits gets no downstream track;
+    the others are unaffected."""
+    res = velo_result([LINE])
+    res["cluster_x"] = np.append(res["cluster_x"], np.float32(3.0))
+    res["cluster_y"] = np.append(res["cluster_y"], np.float32(3.0))
+    res["cluster_z"] = np.append(res["cluster_z"], np.float32(700.0))
+    res["cluster_offsets"] = np.array([0, 3], np.uint64)
+    res["track_offsets"] = np.array([0, 2], np.uint64)
+    res["track_hit_offsets"] = np.array([0, 2, 3], np.uint64)
+    res["track_hits"] = np.array([0, 1, 2], np.uint32)
+    hits = track_hits(LINE, 0.1)
+    off = np.array([0, len(hits)], np.uint64)
+    n, h, st = oracle.forward(off, np.array([q[0] for q in hits], np.uint32), np.array([q[1] for q in hits], np.float32),
+                              np.array([q[2] for q in hits], np.float32), res, DOWN)
+    assert list(n) == [12, 0] and np.all(h[1] == NONE) and np.all(st[1] == 0)

@@ -83,6 +83,9 @@ MUTATIONS = [
     ("forward: nearest-hit tie to the larger id",
      "if (!f || d < bd || (d == bd && h < bh)) { f = true; bd = d; bh = (uint32_t)h; }\n          }\n          return bh;",
      "if (!f || d < bd || (d == bd && h > bh)) { f = true; bd = d; bh = (uint32_t)h; }\n          }\n          return bh;"),
+    ("forward: a NaN distance passes the hit window",
+     "if (!(d <= tol) || !(std::fabs(y[h] - yp) <= p->tol_y)) continue;",
+     "if (d > tol || std::fabs(y[h] - yp) > p->tol_y) continue;"),
     ("forward: line from the two most upstream hits",
      "const uint32_t ha = track_hits[track_hit_offsets[t + 1] - 1], hb = track_hits[track_hit_offsets[t + 1] - 2];",
      "const uint32_t ha = track_hits[track_hit_offsets[t] + 1], hb = track_hits[track_hit_offsets[t]];"),
