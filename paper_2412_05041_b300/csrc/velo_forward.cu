@@ -6,12 +6,17 @@
 // tracker (Sec. "HLT1 details and results").  One CTA per event:
 //   1. the event's downstream hits are sorted by (layer, x) -- four stable
 //      radix passes over the order-preserving bits of x, one over the layer
-//      -- and gathered into sorted x, y arrays with per-layer offsets;
-//   2. every thread takes tracks of the event: the line through the track's
-//      two most downstream clusters, the candidates of layers 0 and 1, the
-//      hits each candidate collects (bisection of a layer's sorted x for a
-//      superset of the window, then the exact binary32 tests), the fits and
-//      the choice of the best candidate.
+//      -- and gathered into sorted x, y arrays (shared memory when the event
+//      fits, else its slice of the workspace), with per-layer offsets and a
+//      bucket index per layer (first position of each of kFwdNB x buckets);
+//   2. the tracks of the event, up to kFwdThreads at a time: one thread per
+//      track finds its line and the position ranges of its candidate windows
+//      in layers 0 and 1; a scan flattens the (track, candidate) pairs and
+//      the threads share them out evenly -- each runs the exact window test
+//      and, for a candidate inside it, the hit collection, fits and cuts, and
+//      offers the candidate's rank key (hits, distance, id) to its track by a
+//      64-bit atomicMin;
+//   3. one thread per track recomputes its winning candidate and writes it.
 // All arithmetic is binary32 in the order the oracle uses (-fmad=false and
 // the __f*_rn intrinsics); every choice is a minimum under a strict total
 // order, so the search order does not matter.
@@ -31,7 +36,7 @@ namespace {
 constexpr int kFwdThreads = 256;
 constexpr uint32_t kFwdL = VELO_FWD_LAYERS;
 
-// x range [xp - tol - m, xp + tol + m] bisected in a layer's sorted x: m =
+// x range [xp - tol - m, xp + tol + m] searched in a layer's sorted x: m =
 // 0.05 mm + 10^-6 (|xp| + tol) is more than ten times the rounding of the
 // bounds and of the exact test |x - xp| <= tol, so the range holds every hit
 // the exact test (which decides) accepts
@@ -46,6 +51,8 @@ struct FwdWork {
   uint32_t *ka, *kb;         // sort keys (ordered x bits) and their ping-pong copy
   uint32_t *va, *vb;         // hit ids
   float *sx, *sy;            // x, y in sorted order
+  uint32_t *yka, *ykb;       // layers 0 and 1 by y: keys (ordered y bits)
+  uint32_t *yva, *yvb;       // and (layer, x)-sorted positions
 };
 
 struct Fwd {
@@ -73,6 +80,10 @@ uint64_t fwd_carve(uint8_t* base, uint64_t n_hits, FwdWork* w) {
   w->vb = reinterpret_cast<uint32_t*>(take(4 * H));
   w->sx = reinterpret_cast<float*>(take(4 * H));
   w->sy = reinterpret_cast<float*>(take(4 * H));
+  w->yka = reinterpret_cast<uint32_t*>(take(4 * H));
+  w->ykb = reinterpret_cast<uint32_t*>(take(4 * H));
+  w->yva = reinterpret_cast<uint32_t*>(take(4 * H));
+  w->yvb = reinterpret_cast<uint32_t*>(take(4 * H));
   return (off + 255ull) & ~255ull;
 }
 
@@ -81,19 +92,24 @@ __device__ __forceinline__ uint32_t ordered_bits(float v) {  // monotone in v
   return u ^ ((u >> 31) ? 0xFFFFFFFFu : 0x80000000u);
 }
 
+
 // flag bits: the hit offsets are invalid / the pixel-tracker result did not
 // fit its buffers (its track lists were not written)
 constexpr uint32_t kFwdBadOffsets = 1u, kFwdNoTracks = 2u;
+constexpr uint32_t kFwdIdBits = 29;  // hit ids in a rank key: events hold fewer than 2^29 hits
+constexpr uint32_t kFwdNB = 128;     // x buckets per layer
+constexpr uint32_t kFwdSmemHits = 4608;  // events up to this size keep x, y in shared memory
+constexpr int kFwdCtasPerSm = 4;
 
 // One CTA: the event offsets start at 0, never decrease, end at n_hits and
-// give no event 2^31 hits or more; the pixel-tracker totals fit its capacities.
+// give no event 2^29 hits or more; the pixel-tracker totals fit its capacities.
 __global__ void __launch_bounds__(1024) k_fwd_validate(Fwd F) {
   const uint64_t E = F.h.n_events;
   int bad = 0;
   if (threadIdx.x == 0) bad |= (F.h.event_offsets[0] != 0ull) | (F.h.event_offsets[E] != F.h.n_hits);
   for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) {
     const uint64_t a = F.h.event_offsets[e], b = F.h.event_offsets[e + 1];
-    bad |= (b < a) | (b - a >= (1ull << 31));
+    bad |= (b < a) | (b - a >= (1ull << kFwdIdBits));
   }
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
@@ -106,40 +122,80 @@ __global__ void __launch_bounds__(1024) k_fwd_validate(Fwd F) {
 
 // sort bucket of a hit: its layer, or kFwdL (never searched) for a layer
 // number >= kFwdL or an x that is not finite
-__device__ __forceinline__ uint32_t fwd_bucket(const uint32_t* lay, const float* x, uint32_t id) {
+__device__ __forceinline__ uint32_t fwd_layer_of(const uint32_t* lay, const float* x, uint32_t id) {
   return isfinite(x[id]) ? min(lay[id], kFwdL) : kFwdL;
 }
 
 struct FwdSmem {
-  uint32_t cnt[radix_counters(kFwdThreads)];
-  uint32_t tmp[64];
-  uint32_t loff[kFwdL + 1];  // first sorted position of each layer; [kFwdL] = end of the valid layers
+  union {
+    uint32_t cnt[radix_counters(kFwdThreads)];  // radix counters of the (layer, x) sort
+    float xy[2 * kFwdSmemHits];                 // then x, y in sorted order (events that fit)
+  } u;
+  union {
+    uint32_t cnt[radix_counters(kFwdThreads)];  // radix counters of the y sort
+    struct {                                    // then the tracks of the current chunk
+      float4 trk[kFwdThreads];                  // xm, ym, tx, ty
+      uint32_t rlo[kFwdThreads][2];             // first entries of the candidate ranges in the y order
+      uint32_t rn0[kFwdThreads];                // length of the layer-0 range
+      uint32_t poff[kFwdThreads + 1];           // first pair of each track
+      unsigned long long best[kFwdThreads];
+    } c;
+  } u2;
+  uint32_t tab[kFwdL][kFwdNB + 1];  // first position of each bucket of each layer (+ its end)
+  uint32_t loff[kFwdL + 1];         // first position of each layer; [kFwdL] = end of the searched layers
+  float xmin[kFwdL], inv[kFwdL];    // bucket of x in layer L: (x - xmin) * inv, clamped
+  // layers 0 and 1 by y (candidate search): ypos holds (layer, x)-sorted
+  // positions in (layer, finite y, y) order; yoff[2 r] .. yoff[2 r + 1] are
+  // layer r's hits with a finite y
+  uint32_t yoff[5];
+  uint32_t ytab[2][kFwdNB + 1];
+  float ymin[2], yinv[2];
   float zl[kFwdL];
+  float wx[2];                      // candidate half-widths in x, layers 0 and 1
+  uint32_t tmp[64];
 };
 
-// The hits of one layer sorted by x: positions [lo, hi) of sx.
-struct LayerView {
-  const float* sx;
+__device__ __forceinline__ uint32_t fwd_bucket(float x, float xmin, float inv) {
+  const float t = fm(fs(x, xmin), inv);  // monotone in x; NaN goes to bucket 0
+  if (!(t >= 0.0f)) return 0u;
+  if (t >= (float)kFwdNB) return kFwdNB - 1u;
+  return (uint32_t)t;
+}
+
+// bucket of a sorted range's values: span and scale
+__device__ __forceinline__ void fwd_bucket_scale(float vmin, float vmax, float* lo, float* inv) {
+  const float span = fs(vmax, vmin);
+  float iv = span > 0.0f ? fd((float)kFwdNB, span) : 0.0f;
+  *lo = vmin;
+  *inv = isfinite(iv) ? iv : 0.0f;
+}
+
+// the sorted hits of one event and their indexes
+struct FwdEvent {
+  const float* sx;      // x in sorted order (shared or global memory)
   const float* sy;
-  const uint32_t* id;
-  uint32_t lo, hi;
+  const uint32_t* sid;  // hit id of each sorted position (global)
+  const FwdSmem* S;
+  __device__ __forceinline__ uint32_t start(int L, float x) const {
+    return S->tab[L][fwd_bucket(x, S->xmin[L], S->inv[L])];
+  }
 };
 
 // nearest hit in x to xp (ties: the smaller id) with |x - xp| <= tol and
-// |y - yp| <= tol_y; returns its sorted position or kNone
-__device__ __forceinline__ uint32_t fwd_nearest(const LayerView& V, float xp, float yp, float tol, float tol_y) {
+// |y - yp| <= tol_y in layer L; returns its sorted position or kNone
+__device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent& V, int L, float xp, float yp, float tol, float tol_y) {
   float lo_x, hi_x;
   fwd_range(xp, tol, &lo_x, &hi_x);
-  uint32_t pos = lower_bound_by(V.lo, V.hi, [&](uint32_t i) { return V.sx[i] < lo_x; });
-  uint32_t best = kNone, best_id = 0;
+  const uint32_t end = V.S->loff[L + 1];
+  uint32_t pos = V.start(L, lo_x);  // every hit with x >= lo_x lies at or after it
+  while (pos < end && V.sx[pos] < lo_x) ++pos;
+  uint32_t best = kNone;
   float bd = 0.0f;
-  for (; pos < V.hi && V.sx[pos] <= hi_x; ++pos) {
+  for (; pos < end && V.sx[pos] <= hi_x; ++pos) {
     const float d = fabsf(fs(V.sx[pos], xp));
     if (!(d <= tol) || !(fabsf(fs(V.sy[pos], yp)) <= tol_y)) continue;
-    const uint32_t id = V.id[pos];
-    if (best == kNone || d < bd || (d == bd && id < best_id)) {
+    if (best == kNone || d < bd || (d == bd && V.sid[pos] < V.sid[best])) {
       best = pos;
-      best_id = id;
       bd = d;
     }
   }
@@ -150,6 +206,7 @@ __device__ __forceinline__ uint32_t fwd_nearest(const LayerView& V, float xp, fl
 __device__ __forceinline__ void fwd_line(const uint32_t* hl, const float* v, const float* zl, int l0, int l1, float* a,
                                          float* b) {
   float S0 = 0.0f, Sz = 0.0f, Szz = 0.0f, Sx = 0.0f, Sxz = 0.0f;
+#pragma unroll
   for (int L = l0; L < l1; ++L) {
     if (hl[L] == kNone) continue;
     const float dz = fs(zl[L], zl[0]);
@@ -166,114 +223,81 @@ __device__ __forceinline__ void fwd_line(const uint32_t* hl, const float* v, con
   *a = fd(fs(Sx, fm(bb, Sz)), S0);
 }
 
-__device__ void fwd_track(const Fwd& F, const FwdSmem& S, uint64_t e, uint64_t tg, uint64_t h0) {
-  const velo_forward_params_t& P = F.p;
-  const float zmag = F.g.z_mag, kappa = F.g.kappa;
-  const float* zl = S.zl;
-  // 0. the line through the two most downstream clusters (ids ascend with z)
-  const uint64_t c0 = F.t.cluster_offsets[e];
-  const uint64_t he = F.t.track_hit_offsets[tg + 1];
-  if (he < F.t.track_hit_offsets[tg] + 2) {  // fewer than two hits: no line, no downstream track
-    F.o.n_found[tg] = 0u;
-    for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[tg * kFwdL + L] = kNone;
-    for (int k = 0; k < (int)VELO_FWD_STATE; ++k) F.o.state[tg * VELO_FWD_STATE + k] = 0.0f;
-    return;
-  }
-  const uint64_t ha = c0 + F.t.track_hits[he - 1], hb = c0 + F.t.track_hits[he - 2];
-  const float x0 = F.t.cluster_x[ha], y0 = F.t.cluster_y[ha], z0 = F.t.cluster_z[ha];
-  const float dzab = fs(z0, F.t.cluster_z[hb]);
-  const float tx = fd(fs(x0, F.t.cluster_x[hb]), dzab), ty = fd(fs(y0, F.t.cluster_y[hb]), dzab);
-  // 1. the line at the kick plane
-  const float dzm = fs(zmag, z0);
-  const float xm = fa(x0, fm(tx, dzm)), ym = fa(y0, fm(ty, dzm));
-  const float tm2 = fm(P.tol_match, P.tol_match);
-  const float* sx = F.w.sx + h0;
-  const float* sy = F.w.sy + h0;
-  const uint32_t* sid = F.w.vb + h0;
-  auto layer = [&](int L) { return LayerView{sx, sy, sid, S.loff[L], S.loff[L + 1]}; };
+struct FwdCand {
+  uint32_t n;
+  float rchi, a, b, d, dy, ad;
+  uint32_t hl[kFwdL];  // sorted positions, kNone = no hit
+};
 
-  bool have = false;
-  uint32_t b_n = 0, b_c = 0;
-  float b_r = 0.0f, b_b = 0.0f, b_a = 0.0f, b_d = 0.0f, b_dy = 0.0f, b_ad = 0.0f;
-  uint32_t b_hits[kFwdL];
-  for (int r = 0; r < 2; ++r) {
-    // 2. candidates in layers 0 and 1
-    const float dzr = fs(zl[r], zmag);
-    const float xr = fa(xm, fm(tx, dzr)), yr = fa(ym, fm(ty, dzr));
-    const float wx = fa(fm(fd(kappa, P.p_min), dzr), P.tol_x);
-    const LayerView R = layer(r);
-    float lo_x, hi_x;
-    fwd_range(xr, wx, &lo_x, &hi_x);
-    for (uint32_t pc = lower_bound_by(R.lo, R.hi, [&](uint32_t i) { return sx[i] < lo_x; }); pc < R.hi && sx[pc] <= hi_x;
-         ++pc) {
-      const float xc = sx[pc];
-      if (!(fabsf(fs(xc, xr)) <= wx) || !(fabsf(fs(sy[pc], yr)) <= P.win_y)) continue;
-      const uint32_t c = sid[pc];
-      // 3. the first station from the kick line, the others from the line through it
-      const float tk = fd(fs(xc, xm), dzr);
-      uint32_t hl[kFwdL];
-      uint32_t n1 = 0;
-      for (int L = 0; L < 4; ++L) {
-        const float dzl = fs(zl[L], zmag);
-        hl[L] = fwd_nearest(layer(L), fa(xm, fm(tk, dzl)), fa(ym, fm(ty, dzl)), P.tol_x, P.tol_y);
-        n1 += hl[L] != kNone ? 1u : 0u;
-      }
-      if (n1 < 2) continue;
-      float a1, b1;
-      fwd_line(hl, sx, zl, 0, 4, &a1, &b1);
-      uint32_t n = n1;
-      for (int L = 4; L < (int)kFwdL; ++L) {
-        const float dzl = fs(zl[L], zmag);
-        hl[L] = fwd_nearest(layer(L), fa(a1, fm(b1, fs(zl[L], zl[0]))), fa(ym, fm(ty, dzl)), P.tol_x_far, P.tol_y);
-        n += hl[L] != kNone ? 1u : 0u;
-      }
-      if (n < P.min_hits) continue;
-      // 4. the lines through all of them and the chi2 in x
-      float a, b;
-      fwd_line(hl, sx, zl, 0, kFwdL, &a, &b);
-      float chi2 = 0.0f;
-      for (int L = 0; L < (int)kFwdL; ++L) {
-        if (hl[L] == kNone) continue;
-        const float res = fd(fs(fs(sx[hl[L]], a), fm(b, fs(zl[L], zl[0]))), P.sigma_x);
-        chi2 = fa(chi2, fm(res, res));
-      }
-      const float rchi = fd(chi2, (float)(n - 2));
-      if (!(rchi <= P.chi2ndf_max)) continue;
-      // 5. the match at the kick plane
-      const float d = fs(fa(a, fm(b, fs(zmag, zl[0]))), xm);
-      float ya, yb;
-      fwd_line(hl, sy, zl, 0, kFwdL, &ya, &yb);
-      const float dy = fs(fa(ya, fm(yb, fs(zmag, zl[0]))), ym);
-      const float ad = fa(fm(d, d), fm(dy, dy));
-      if (!(ad <= tm2)) continue;
-      // 6. most hits, then the smallest distance, then the smallest candidate id
-      const bool better = !have || n > b_n || (n == b_n && (ad < b_ad || (ad == b_ad && c < b_c)));
-      if (!better) continue;
-      have = true;
-      b_n = n;
-      b_c = c;
-      b_r = rchi;
-      b_b = b;
-      b_a = a;
-      b_d = d;
-      b_dy = dy;
-      b_ad = ad;
-      for (int L = 0; L < (int)kFwdL; ++L) b_hits[L] = hl[L] != kNone ? sid[hl[L]] : kNone;
-    }
+// steps 3-5 for the candidate at sorted position pc of layer r of a track
+// whose line reaches the kick plane at (xm, ym) with slope ty: false when a
+// cut drops it
+__device__ __forceinline__ bool fwd_candidate(const FwdEvent& V, const Fwd& F, float xm, float ym, float ty, int r,
+                                              uint32_t pc, FwdCand& C) {
+  const velo_forward_params_t& P = F.p;
+  const float zmag = F.g.z_mag;
+  const float* zl = V.S->zl;
+  const float tk = fd(fs(V.sx[pc], xm), fs(zl[r], zmag));
+  uint32_t n1 = 0;
+#pragma unroll
+  for (int L = 0; L < 4; ++L) {
+    const float dzl = fs(zl[L], zmag);
+    C.hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, dzl)), fa(ym, fm(ty, dzl)), P.tol_x, P.tol_y);
+    n1 += C.hl[L] != kNone ? 1u : 0u;
   }
-  F.o.n_found[tg] = have ? b_n : 0u;
-  for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[tg * kFwdL + L] = have ? b_hits[L] : kNone;
-  float* so = F.o.state + tg * VELO_FWD_STATE;
-  so[0] = have ? fd(fs(b_b, tx), kappa) : 0.0f;
-  so[1] = have ? b_r : 0.0f;
-  so[2] = have ? b_b : 0.0f;
-  so[3] = have ? b_a : 0.0f;
-  so[4] = have ? b_d : 0.0f;
-  so[5] = have ? b_dy : 0.0f;
+  if (n1 < 2) return false;
+  float a1, b1;
+  fwd_line(C.hl, V.sx, zl, 0, 4, &a1, &b1);
+  uint32_t n = n1;
+#pragma unroll
+  for (int L = 4; L < (int)kFwdL; ++L) {
+    const float dzl = fs(zl[L], zmag);
+    C.hl[L] = fwd_nearest(V, L, fa(a1, fm(b1, fs(zl[L], zl[0]))), fa(ym, fm(ty, dzl)), P.tol_x_far, P.tol_y);
+    n += C.hl[L] != kNone ? 1u : 0u;
+  }
+  if (n < P.min_hits) return false;
+  float a, b;
+  fwd_line(C.hl, V.sx, zl, 0, kFwdL, &a, &b);
+  float chi2 = 0.0f;
+#pragma unroll
+  for (int L = 0; L < (int)kFwdL; ++L) {
+    if (C.hl[L] == kNone) continue;
+    const float res = fd(fs(fs(V.sx[C.hl[L]], a), fm(b, fs(zl[L], zl[0]))), P.sigma_x);
+    chi2 = fa(chi2, fm(res, res));
+  }
+  const float rchi = fd(chi2, (float)(n - 2));
+  if (!(rchi <= P.chi2ndf_max)) return false;
+  const float d = fs(fa(a, fm(b, fs(zmag, zl[0]))), xm);
+  float ya, yb;
+  fwd_line(C.hl, V.sy, zl, 0, kFwdL, &ya, &yb);
+  const float dy = fs(fa(ya, fm(yb, fs(zmag, zl[0]))), ym);
+  const float ad = fa(fm(d, d), fm(dy, dy));
+  if (!(ad <= fm(P.tol_match, P.tol_match))) return false;
+  C.n = n;
+  C.rchi = rchi;
+  C.a = a;
+  C.b = b;
+  C.d = d;
+  C.dy = dy;
+  C.ad = ad;
+  return true;
 }
 
-__global__ void __launch_bounds__(kFwdThreads) k_forward(Fwd F) {
-  __shared__ FwdSmem S;
+// rank key: more hits, then the smaller distance (non-negative binary32
+// orders as its bits), then the smaller candidate id -- the smallest key wins
+__device__ __forceinline__ unsigned long long fwd_key(uint32_t n, float ad, uint32_t c) {
+  return ((unsigned long long)(kFwdL - n) << 60) | ((unsigned long long)__float_as_uint(ad) << kFwdIdBits) | c;
+}
+
+__device__ __forceinline__ void fwd_write_none(const Fwd& F, uint64_t t) {
+  F.o.n_found[t] = 0u;
+  for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[t * kFwdL + L] = kNone;
+  for (int k = 0; k < (int)VELO_FWD_STATE; ++k) F.o.state[t * VELO_FWD_STATE + k] = 0.0f;
+}
+
+__global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
+  extern __shared__ __align__(16) uint8_t fwd_smem_raw[];
+  FwdSmem& S = *reinterpret_cast<FwdSmem*>(fwd_smem_raw);
   const uint64_t e = blockIdx.x;
   const uint32_t tid = threadIdx.x;
   const uint64_t t0 = F.t.track_offsets[e], t1 = F.t.track_offsets[e + 1];
@@ -281,11 +305,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(Fwd F) {
   const uint32_t flag = *(const volatile uint32_t*)F.w.flag;
   if (flag & kFwdNoTracks) return;  // no track lists to read: nothing is written
   if (flag & kFwdBadOffsets) {      // hits rejected: no track has a downstream track
-    for (uint64_t t = t0 + tid; t < t1 && t < cap; t += kFwdThreads) {
-      F.o.n_found[t] = 0u;
-      for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[t * kFwdL + L] = kNone;
-      for (int k = 0; k < (int)VELO_FWD_STATE; ++k) F.o.state[t * VELO_FWD_STATE + k] = 0.0f;
-    }
+    for (uint64_t t = t0 + tid; t < t1 && t < cap; t += kFwdThreads) fwd_write_none(F, t);
     return;
   }
   const uint64_t h0 = F.h.event_offsets[e];
@@ -299,32 +319,183 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(Fwd F) {
   }
   __syncthreads();
   const uint32_t* lay = F.h.layer + h0;
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [](uint32_t k, uint32_t) { return k & 255u; }, S.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                                [](uint32_t k, uint32_t) { return k >> 24; }, S.cnt, S.tmp);
   const float* xin = F.h.x + h0;
+  const float* yin = F.h.y + h0;
   radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [lay, xin](uint32_t, uint32_t id) { return fwd_bucket(lay, xin, id); }, S.cnt, S.tmp);
-  // sorted x, y, and the first position of every layer (a layer's slots from
-  // its predecessor's layer (exclusive) to its own get the position)
+                                [](uint32_t k, uint32_t) { return k & 255u; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
+                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
+                                [](uint32_t k, uint32_t) { return k >> 24; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                                [lay, xin](uint32_t, uint32_t id) { return fwd_layer_of(lay, xin, id); }, S.u.cnt,
+                                S.tmp);
+  // sorted x, y (shared memory when the event fits), the sorted position of
+  // every id (into va, free after the sort), the first position of every
+  // layer (a layer's slots after its predecessor's layer get the position)
+  const bool big = n > kFwdSmemHits;
+  float* sx = big ? W.sx + h0 : S.u.xy;
+  float* sy = big ? W.sy + h0 : S.u.xy + kFwdSmemHits;
+  const uint32_t* sid = W.vb + h0;
+  uint32_t* pos_of = W.va + h0;
   for (uint32_t q = tid; q <= kFwdL; q += kFwdThreads) S.loff[q] = n;
   __syncthreads();
   for (uint32_t pos = tid; pos < n; pos += kFwdThreads) {
-    const uint32_t id = W.vb[h0 + pos];
-    W.sx[h0 + pos] = F.h.x[h0 + id];
-    W.sy[h0 + pos] = F.h.y[h0 + id];
-    const uint32_t L = fwd_bucket(lay, xin, id), Lp = pos ? fwd_bucket(lay, xin, W.vb[h0 + pos - 1]) + 1u : 0u;
+    const uint32_t id = sid[pos];
+    sx[pos] = xin[id];
+    sy[pos] = yin[id];
+    pos_of[id] = pos;
+    const uint32_t L = fwd_layer_of(lay, xin, id), Lp = pos ? fwd_layer_of(lay, xin, sid[pos - 1]) + 1u : 0u;
     for (uint32_t q = Lp; q <= L; ++q) S.loff[q] = pos;
   }
   __syncthreads();
-  // 2. the tracks of the event
-  for (uint64_t t = t0 + tid; t < t1; t += kFwdThreads)
-    if (t < cap) fwd_track(F, S, e, t, h0);
+  // layers 0 and 1 sorted by y: four passes over the ordered bits of y, one
+  // over (layer, y not finite)
+  const uint32_t n01 = S.loff[2];
+  for (uint32_t pos = tid; pos < n01; pos += kFwdThreads) {
+    W.yka[h0 + pos] = ordered_bits(sy[pos]);
+    W.yva[h0 + pos] = pos;
+  }
+  __syncthreads();
+  const uint32_t l1 = S.loff[1];
+  auto ydig = [sy, l1](uint32_t, uint32_t pos) { return (pos >= l1 ? 2u : 0u) + (isfinite(sy[pos]) ? 0u : 1u); };
+  radix_pass<kFwdThreads, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
+                                [](uint32_t k, uint32_t) { return k & 255u; }, S.u2.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
+                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.u2.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
+                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.u2.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
+                                [](uint32_t k, uint32_t) { return k >> 24; }, S.u2.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01, ydig, S.u2.cnt, S.tmp);
+  const uint32_t* ypos = W.yvb + h0;
+  for (uint32_t q = tid; q < 5; q += kFwdThreads) S.yoff[q] = n01;
+  __syncthreads();
+  for (uint32_t i = tid; i < n01; i += kFwdThreads) {
+    const uint32_t g = ydig(0u, ypos[i]), gp = i ? ydig(0u, ypos[i - 1]) + 1u : 0u;
+    for (uint32_t q = gp; q <= g; ++q) S.yoff[q] = i;
+  }
+  __syncthreads();
+  // bucket index of every layer over its x span, of layers 0 and 1 over their y span
+  if (tid < kFwdL) {
+    const uint32_t lo = S.loff[tid], hi = S.loff[tid + 1];
+    fwd_bucket_scale(hi > lo ? sx[lo] : 0.0f, hi > lo ? sx[hi - 1] : 0.0f, &S.xmin[tid], &S.inv[tid]);
+  } else if (tid >= 32 && tid < 34) {
+    const uint32_t r = tid - 32, lo = S.yoff[2 * r], hi = S.yoff[2 * r + 1];
+    fwd_bucket_scale(hi > lo ? sy[ypos[lo]] : 0.0f, hi > lo ? sy[ypos[hi - 1]] : 0.0f, &S.ymin[r], &S.yinv[r]);
+  }
+  for (uint32_t i = tid; i < 2 * (kFwdNB + 1); i += kFwdThreads) {
+    const uint32_t r = i / (kFwdNB + 1);
+    S.ytab[r][i % (kFwdNB + 1)] = S.yoff[2 * r + 1];
+  }
+  if (tid < 2) S.wx[tid] = fa(fm(fd(F.g.kappa, F.p.p_min), fs(S.zl[tid], F.g.z_mag)), F.p.tol_x);
+  for (uint32_t i = tid; i < kFwdL * (kFwdNB + 1); i += kFwdThreads) {
+    const uint32_t L = i / (kFwdNB + 1);
+    S.tab[L][i % (kFwdNB + 1)] = S.loff[L + 1];  // buckets past the layer's last hit: its end
+  }
+  __syncthreads();
+  for (uint32_t pos = tid; pos < S.loff[kFwdL]; pos += kFwdThreads) {
+    uint32_t L = 0;
+    while (S.loff[L + 1] <= pos) ++L;
+    const uint32_t b = fwd_bucket(sx[pos], S.xmin[L], S.inv[L]);
+    const uint32_t bp = pos > S.loff[L] ? fwd_bucket(sx[pos - 1], S.xmin[L], S.inv[L]) + 1u : 0u;
+    for (uint32_t q = bp; q <= b; ++q) S.tab[L][q] = pos;
+  }
+  for (uint32_t r = 0; r < 2; ++r)
+    for (uint32_t i = S.yoff[2 * r] + tid; i < S.yoff[2 * r + 1]; i += kFwdThreads) {
+      const uint32_t b = fwd_bucket(sy[ypos[i]], S.ymin[r], S.yinv[r]);
+      const uint32_t bp = i > S.yoff[2 * r] ? fwd_bucket(sy[ypos[i - 1]], S.ymin[r], S.yinv[r]) + 1u : 0u;
+      for (uint32_t q = bp; q <= b; ++q) S.ytab[r][q] = i;
+    }
+  __syncthreads();
+  const FwdEvent V{sx, sy, sid, &S};
+  const float zmag = F.g.z_mag;
+  // 2.-3. the tracks, kFwdThreads at a time
+  for (uint64_t tc = t0; tc < t1; tc += kFwdThreads) {
+    const uint64_t t = tc + tid;
+    uint32_t cnt = 0;
+    bool live = false;
+    if (t < t1 && t < cap) {
+      const uint64_t hs = F.t.track_hit_offsets[t], he = F.t.track_hit_offsets[t + 1];
+      if (he >= hs + 2) {
+        // 0.-1. the line through the two most downstream clusters, at the kick plane
+        const uint64_t c0 = F.t.cluster_offsets[e];
+        const uint64_t ha = c0 + F.t.track_hits[he - 1], hb = c0 + F.t.track_hits[he - 2];
+        const float x0 = F.t.cluster_x[ha], y0 = F.t.cluster_y[ha], z0 = F.t.cluster_z[ha];
+        const float dzab = fs(z0, F.t.cluster_z[hb]);
+        const float tx = fd(fs(x0, F.t.cluster_x[hb]), dzab), ty = fd(fs(y0, F.t.cluster_y[hb]), dzab);
+        const float dzm = fs(zmag, z0);
+        const float xm = fa(x0, fm(tx, dzm)), ym = fa(y0, fm(ty, dzm));
+        S.u2.c.trk[tid] = make_float4(xm, ym, tx, ty);
+        live = true;
+        // 2. ranges of the y order holding the candidate windows of layers 0 and 1
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          float lo_y, hi_y;
+          fwd_range(fa(ym, fm(ty, fs(S.zl[r], zmag))), F.p.win_y, &lo_y, &hi_y);
+          const uint32_t lo = S.ytab[r][fwd_bucket(lo_y, S.ymin[r], S.yinv[r])];
+          const uint32_t hi = S.ytab[r][fwd_bucket(hi_y, S.ymin[r], S.yinv[r]) + 1u];
+          S.u2.c.rlo[tid][r] = lo;
+          const uint32_t len = hi > lo ? hi - lo : 0u;
+          if (r == 0) S.u2.c.rn0[tid] = len;
+          cnt += len;
+        }
+      } else {
+        fwd_write_none(F, t);
+      }
+    }
+    S.u2.c.best[tid] = ~0ull;
+    uint32_t total;
+    const uint32_t first = block_exclusive_scan<kFwdThreads, uint32_t>(cnt, &total, S.tmp);
+    S.u2.c.poff[tid] = first;
+    if (tid == 0) S.u2.c.poff[kFwdThreads] = total;
+    __syncthreads();
+    // the (track, candidate) pairs, shared out evenly
+    for (uint32_t q = tid; q < total; q += kFwdThreads) {
+      uint32_t lo = 0, hi = kFwdThreads;  // the track j with poff[j] <= q < poff[j + 1]
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (S.u2.c.poff[mid] <= q) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t j = lo, k = q - S.u2.c.poff[j];
+      const int r = k < S.u2.c.rn0[j] ? 0 : 1;
+      const uint32_t pc = ypos[S.u2.c.rlo[j][r] + (r ? k - S.u2.c.rn0[j] : k)];
+      const float4 tr = S.u2.c.trk[j];
+      const float dzr = fs(S.zl[r], zmag);
+      if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, dzr)))) <= S.wx[r]) ||
+          !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, dzr)))) <= F.p.win_y))
+        continue;
+      FwdCand C;
+      if (fwd_candidate(V, F, tr.x, tr.y, tr.w, r, pc, C)) atomicMin(&S.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
+    }
+    __syncthreads();
+    // 3. the winner of every track, recomputed and written
+    if (live) {
+      const unsigned long long key = S.u2.c.best[tid];
+      if (key == ~0ull) {
+        fwd_write_none(F, t);
+      } else {
+        const uint32_t pc = pos_of[(uint32_t)(key & ((1ull << kFwdIdBits) - 1ull))];
+        const float4 tr = S.u2.c.trk[tid];
+        FwdCand C;
+        fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C);
+        F.o.n_found[t] = C.n;
+#pragma unroll
+        for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[t * kFwdL + L] = C.hl[L] != kNone ? sid[C.hl[L]] : kNone;
+        float* so = F.o.state + t * VELO_FWD_STATE;
+        so[0] = fd(fs(C.b, tr.z), F.g.kappa);
+        so[1] = C.rchi;
+        so[2] = C.b;
+        so[3] = C.a;
+        so[4] = C.d;
+        so[5] = C.dy;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -389,8 +560,9 @@ int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks
   F.o = *out;
   if (fwd_carve(static_cast<uint8_t*>(workspace), hits->n_hits, &F.w) > workspace_bytes) return VELO_ECAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!set_max_smem_once(reinterpret_cast<const void*>(k_forward), 2)) return VELO_ECUDA;
   k_fwd_validate<<<1, 1024, 0, s>>>(F);
-  if (hits->n_events) k_forward<<<(uint32_t)hits->n_events, kFwdThreads, 0, s>>>(F);
+  if (hits->n_events) k_forward<<<(uint32_t)hits->n_events, kFwdThreads, sizeof(FwdSmem), s>>>(F);
   return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;
 }
 
