@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default block shapes instead of autotuned ones")
     ap.add_argument("--no-batched", action="store_true", help="skip the 100k-event uneven graph-launch measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the streaming (continuous batching) measurement")
+    ap.add_argument("--no-forward", action="store_true", help="skip the forward-tracking measurement")
+    ap.add_argument("--forward-only", action="store_true",
+                    help="only the forward-tracking measurement (one JSON line of its own; for profiling)")
     return ap.parse_args()
 
 
@@ -162,11 +165,23 @@ def measured_peaks():
 HOST_ONLY_SOURCES = ("velo_host.cu", "velo_static.cu", "velo_peak.cu")
 
 
-def kernel_source_hash():
+# the forward-tracking kernel's own source and the device headers it includes;
+# the pixel-tracker kernels' summaries cover every other kernel source
+FORWARD_SOURCES = ("velo_forward.cu", "velo_device.cuh", "velo_fit.cuh", "velo_internal.cuh")
+
+
+def kernel_source_hash(kernel: str = ""):
+    """First 16 hex digits of the SHA-256 over the sources a kernel's ncu
+    summary depends on (a summary of other sources is stale)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2412_05041_b300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name in HOST_ONLY_SOURCES:
+            continue
+        if kernel == "k_forward":
+            if name not in FORWARD_SOURCES:
+                continue
+        elif name == "velo_forward.cu":
             continue
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
@@ -183,7 +198,7 @@ def profiled_traffic(kernel: str):
     txt = open(path).read()
     m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
     m_b = re.search(r"dram_bytes_per_event:\s*([0-9.eE+]+)", txt)
-    if not m_src or not m_b or m_src.group(1) != kernel_source_hash():
+    if not m_src or not m_b or m_src.group(1) != kernel_source_hash(kernel):
         return None
     return float(m_b.group(1))
 
@@ -196,7 +211,7 @@ def profiled_metric(kernel: str, name: str):
     txt = open(path).read()
     m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
     m = re.search(r"\|\s*" + re.escape(name) + r"\s*\|\s*([0-9.eE+,-]+)\s*\|", txt)
-    if not m_src or not m or m_src.group(1) != kernel_source_hash():
+    if not m_src or not m or m_src.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1).replace(",", ""))
 
@@ -342,6 +357,66 @@ def run_serving(args, dev, vp, tuning):
             "p50_latency_ms": poi["p50_latency_ms"], "p99_latency_ms": poi["p99_latency_ms"]}
 
 
+def run_forward(args, dev, vp, n_ev):
+    """Forward tracking of the pixel-tracker tracks of n_ev pile-up-5.5 events
+    to twelve downstream layers (invented geometry, 20 noise hits per layer):
+    the pixel-tracker path runs once, then K timed launches of velo_forward
+    alone and K of both stages back to back (inputs resident in HBM)."""
+    import torch
+
+    import paper_2412_05041_b300 as velo
+    import velogen
+    from velogen import scifi
+    b = velogen.generate(velogen.C2, n_events=n_ev, truth=True)
+    s = scifi.generate(b)
+    stream = torch.cuda.current_stream(dev)
+    off = torch.from_numpy(b.offsets.view(np.int64)).to(dev)
+    pix = torch.from_numpy(b.pixels.view(np.int32)).to(dev)
+    R = velo.Reconstructor(b.geometry, vp, max_events=n_ev, max_pixels=pix.numel(), device=dev)
+    F = velo.ForwardTracker(s.geometry, max_events=n_ev, max_hits=len(s.x), cap_tracks=R.sizes.cap_tracks, device=dev)
+    so = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    la = torch.from_numpy(s.layer.view(np.int32)).to(dev)
+    x = torch.from_numpy(s.x).to(dev)
+    y = torch.from_numpy(s.y).to(dev)
+    R.run(off, pix, stream)
+    for _ in range(max(args.warmup, 3)):
+        F.run(R, so, la, x, y, stream)
+    torch.cuda.synchronize(dev)
+    K = max(3, args.steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    for _ in range(K):
+        F.run(R, so, la, x, y, stream)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(K):
+        R.run(off, pix, stream)
+        F.run(R, so, la, x, y, stream)
+    ev[3].record(stream)
+    torch.cuda.synchronize(dev)
+    ms_f = ev[0].elapsed_time(ev[1]) / K
+    ms_both = ev[2].elapsed_time(ev[3]) / K
+    r = F.result(stream)
+    n = r["n_found"].cpu().numpy()
+    T, H = len(n), len(s.x)
+    # algorithmic bytes of one launch: the hits (layer, x, y) and offsets, per
+    # track its last two clusters (x, y, z), two hit ids, its offsets, and
+    # the outputs (count, 12 hit ids, 6-float state)
+    alg = 12 * H + 8 * (n_ev + 1) + T * (24 + 8 + 16 + 4 + 48 + 24) + 8 * (n_ev + 1)
+    peaks, peak_kind = measured_peaks()
+    achieved = alg / (ms_f / 1000.0) / 1e9
+    traffic = profiled_traffic("k_forward")
+    return {"workload": f"C2 ({n_ev} events) pixel-tracker tracks + 12 downstream layers (20 noise hits/layer)",
+            "value": n_ev / (ms_f / 1000.0), "unit": UNIT, "ms_per_launch": ms_f, "launches": K,
+            "with_pixel_tracking": {"value": n_ev / (ms_both / 1000.0), "unit": UNIT, "ms_per_step": ms_both},
+            "downstream_hits": H, "tracks_in": T, "found_fraction": float((n > 0).mean()) if T else 0.0,
+            "roofline": {"kernel": "k_forward", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "algorithmic_bytes": alg,
+                         "traffic": None if traffic is None else traffic * n_ev,
+                         "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+            "gpu_launches_per_call": 2}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -359,6 +434,13 @@ def run_ours(args):
     cfg = velogen.C2
     n_ev = args.events
     first, n_ev = shard(rank, world, n_ev)
+    if args.forward_only:
+        out = run_forward(args, dev, velo.default_params(**params_values(cfg.ms_theta)), n_ev)
+        if rank == 0:
+            print(json.dumps({"forward": out}))
+        if world > 1:
+            dist.destroy_process_group()
+        return
     b = velogen.generate(cfg, n_events=n_ev, first_event=first)
     vp = velo.default_params(**params_values(cfg.ms_theta))
     off_h = torch.from_numpy(b.offsets.view(np.int64)).pin_memory()
@@ -483,6 +565,14 @@ def run_ours(args):
         except Exception as exc:
             serving = {"error": repr(exc)[:300]}
 
+    forward = None
+    if world == 1 and not args.no_forward:
+        try:
+            forward = run_forward(args, dev, vp, n_ev)
+        except Exception as exc:
+            forward = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
+
     batched = None
     if world == 1 and not args.no_batched:
         R = RL = Rb = None
@@ -540,6 +630,7 @@ def run_ours(args):
         "tuning_table_ms": tuning_table,
         "batched": batched,
         "serving": serving,
+        "forward": forward,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfg)

@@ -22,8 +22,10 @@
 // order, so the search order does not matter.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "velo_device.cuh"
 #include "velo_fit.cuh"
@@ -62,6 +64,7 @@ struct Fwd {
   velo_forward_params_t p;
   velo_forward_output_t o;
   FwdWork w;
+  float lam;  // largest sum |w_i| of the final x fit's weights at the kick plane (any admissible hit set)
 };
 
 uint64_t fwd_carve(uint8_t* base, uint64_t n_hits, FwdWork* w) {
@@ -98,7 +101,8 @@ __device__ __forceinline__ uint32_t ordered_bits(float v) {  // monotone in v
 constexpr uint32_t kFwdBadOffsets = 1u, kFwdNoTracks = 2u;
 constexpr uint32_t kFwdIdBits = 29;  // hit ids in a rank key: events hold fewer than 2^29 hits
 constexpr uint32_t kFwdNB = 128;     // x buckets per layer
-constexpr uint32_t kFwdSmemHits = 4608;  // events up to this size keep x, y in shared memory
+constexpr uint32_t kFwdSmemHits = 4096;  // events up to this size keep x, y in shared memory
+constexpr uint32_t kFwdSurv = 1280;      // pairs per round (each leaves at most one survivor)
 constexpr int kFwdCtasPerSm = 4;
 
 // One CTA: the event offsets start at 0, never decrease, end at n_hits and
@@ -153,7 +157,13 @@ struct FwdSmem {
   float zl[kFwdL];
   float wx[2];                      // candidate half-widths in x, layers 0 and 1
   uint32_t tmp[64];
+  uint32_t nsv;                     // survivors of the current round
+  uint32_t sv_pc[kFwdSurv];         // their sorted positions
+  uint8_t sv_j[kFwdSurv];           // and tracks in the chunk
 };
+
+// four CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+static_assert(sizeof(FwdSmem) + 1024 <= 228 * 1024 / kFwdCtasPerSm, "shared memory for four CTAs per SM");
 
 __device__ __forceinline__ uint32_t fwd_bucket(float x, float xmin, float inv) {
   const float t = fm(fs(x, xmin), inv);  // monotone in x; NaN goes to bucket 0
@@ -281,6 +291,45 @@ __device__ __forceinline__ bool fwd_candidate(const FwdEvent& V, const Fwd& F, f
   C.dy = dy;
   C.ad = ad;
   return true;
+}
+
+// Step 3's first station for the candidate at sorted position pc of layer r,
+// and a necessary condition for passing the match cut: false when the
+// candidate certainly fails a cut.  The final x line is the least-squares
+// line of the first-station hits and the far hits; written as the
+// first-station line L1 (a1, b1) plus the least-squares line of the hits'
+// offsets e_i from L1, its distance at the kick plane is d1 + sum w_i e_i,
+// with d1 that of L1, w_i the fit's weights at the kick plane and |e_i| at
+// most E = max(first-station residuals, tol_x_far).  So |d| <= tol_match
+// needs |d1| <= tol_match + lam E, lam the largest sum |w_i| over the hit
+// sets a candidate can end with (host arithmetic); the allowance
+// 1 mm + 2e-3 M (M the size of the coordinates involved) covers the binary32
+// rounding of both lines, its worst case being some 1e-4 M.
+__device__ __forceinline__ bool fwd_first_station(const FwdEvent& V, const Fwd& F, float xm, float ym, float ty, int r,
+                                                  uint32_t pc) {
+  const velo_forward_params_t& P = F.p;
+  const float zmag = F.g.z_mag;
+  const float* zl = V.S->zl;
+  const float tk = fd(fs(V.sx[pc], xm), fs(zl[r], zmag));
+  uint32_t hl[4];
+  uint32_t n1 = 0;
+#pragma unroll
+  for (int L = 0; L < 4; ++L) {
+    const float dzl = fs(zl[L], zmag);
+    hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, dzl)), fa(ym, fm(ty, dzl)), P.tol_x, P.tol_y);
+    n1 += hl[L] != kNone ? 1u : 0u;
+  }
+  if (n1 < 2) return false;
+  float a1, b1;
+  fwd_line(hl, V.sx, zl, 0, 4, &a1, &b1);
+  float E = P.tol_x_far;
+#pragma unroll
+  for (int L = 0; L < 4; ++L)
+    if (hl[L] != kNone) E = fmaxf(E, fabsf(fs(V.sx[hl[L]], fa(a1, fm(b1, fs(zl[L], zl[0]))))));
+  const float reach = fmaxf(fabsf(fs(zmag, zl[0])), fs(zl[kFwdL - 1], zl[0]));
+  const float M = fa(fa(fa(fabsf(a1), fm(fabsf(b1), reach)), fabsf(xm)), E);
+  const float d1 = fs(fa(a1, fm(b1, fs(zmag, zl[0]))), xm);
+  return fabsf(d1) <= fa(fa(P.tol_match, fm(F.lam, E)), fa(1.0f, fm(2e-3f, M)));
 }
 
 // rank key: more hits, then the smaller distance (non-negative binary32
@@ -452,26 +501,43 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
     S.u2.c.poff[tid] = first;
     if (tid == 0) S.u2.c.poff[kFwdThreads] = total;
     __syncthreads();
-    // the (track, candidate) pairs, shared out evenly
-    for (uint32_t q = tid; q < total; q += kFwdThreads) {
-      uint32_t lo = 0, hi = kFwdThreads;  // the track j with poff[j] <= q < poff[j + 1]
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (S.u2.c.poff[mid] <= q) lo = mid;
-        else hi = mid;
+    // the (track, candidate) pairs, shared out evenly, kFwdSurv at a time:
+    // the window test, the first station and the bound, the survivors listed;
+    // then the survivors' far stations, fits and cuts
+    for (uint32_t q0 = 0; q0 < total; q0 += kFwdSurv) {
+      if (tid == 0) S.nsv = 0;
+      __syncthreads();
+      for (uint32_t q = q0 + tid; q < min(total, q0 + kFwdSurv); q += kFwdThreads) {
+        uint32_t lo = 0, hi = kFwdThreads;  // the track j with poff[j] <= q < poff[j + 1]
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (S.u2.c.poff[mid] <= q) lo = mid;
+          else hi = mid;
+        }
+        const uint32_t j = lo, k = q - S.u2.c.poff[j];
+        const int r = k < S.u2.c.rn0[j] ? 0 : 1;
+        const uint32_t pc = ypos[S.u2.c.rlo[j][r] + (r ? k - S.u2.c.rn0[j] : k)];
+        const float4 tr = S.u2.c.trk[j];
+        const float dzr = fs(S.zl[r], zmag);
+        if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, dzr)))) <= S.wx[r]) ||
+            !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, dzr)))) <= F.p.win_y))
+          continue;
+        if (!fwd_first_station(V, F, tr.x, tr.y, tr.w, r, pc)) continue;
+        const uint32_t slot = atomicAdd(&S.nsv, 1u);
+        S.sv_pc[slot] = pc;
+        S.sv_j[slot] = (uint8_t)j;
       }
-      const uint32_t j = lo, k = q - S.u2.c.poff[j];
-      const int r = k < S.u2.c.rn0[j] ? 0 : 1;
-      const uint32_t pc = ypos[S.u2.c.rlo[j][r] + (r ? k - S.u2.c.rn0[j] : k)];
-      const float4 tr = S.u2.c.trk[j];
-      const float dzr = fs(S.zl[r], zmag);
-      if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, dzr)))) <= S.wx[r]) ||
-          !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, dzr)))) <= F.p.win_y))
-        continue;
-      FwdCand C;
-      if (fwd_candidate(V, F, tr.x, tr.y, tr.w, r, pc, C)) atomicMin(&S.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
+      __syncthreads();
+      const uint32_t nsv = S.nsv;
+      for (uint32_t i = tid; i < nsv; i += kFwdThreads) {
+        const uint32_t pc = S.sv_pc[i], j = S.sv_j[i];
+        const float4 tr = S.u2.c.trk[j];
+        FwdCand C;
+        if (fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C))
+          atomicMin(&S.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // 3. the winner of every track, recomputed and written
     if (live) {
       const unsigned long long key = S.u2.c.best[tid];
@@ -503,6 +569,49 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
 }  // namespace velo
 
 using namespace velo;
+
+namespace {
+
+// Largest sum over the hits of |w_i|, w_i the weights of the least-squares
+// line's value at the kick plane, over every set of layers a candidate can
+// end with (at least min_hits layers, two or more of them in the first
+// station); in double, rounded up.  The last answer is kept.
+float fwd_lambda(const velo_downstream_t& g, uint32_t min_hits) {
+  static std::mutex mu;
+  static velo_downstream_t last_g;
+  static uint32_t last_min = 0;
+  static float last = -1.0f;
+  std::lock_guard<std::mutex> lk(mu);
+  if (last >= 0.0f && last_min == min_hits && std::memcmp(&last_g, &g, sizeof(g)) == 0) return last;
+  double best = 0.0;
+  for (uint32_t m = 0; m < (1u << VELO_FWD_LAYERS); ++m) {
+    if ((uint32_t)__builtin_popcount(m) < min_hits || __builtin_popcount(m & 15u) < 2) continue;
+    double n = 0.0, zb = 0.0;
+    for (uint32_t L = 0; L < VELO_FWD_LAYERS; ++L)
+      if (m >> L & 1u) {
+        n += 1.0;
+        zb += (double)g.z_layers[L] - g.z_layers[0];
+      }
+    zb /= n;
+    double sxx = 0.0;
+    for (uint32_t L = 0; L < VELO_FWD_LAYERS; ++L)
+      if (m >> L & 1u) {
+        const double dz = (double)g.z_layers[L] - g.z_layers[0] - zb;
+        sxx += dz * dz;
+      }
+    const double zq = (double)g.z_mag - g.z_layers[0] - zb;
+    double sum = 0.0;
+    for (uint32_t L = 0; L < VELO_FWD_LAYERS; ++L)
+      if (m >> L & 1u) sum += std::fabs(1.0 / n + zq * ((double)g.z_layers[L] - g.z_layers[0] - zb) / sxx);
+    best = std::max(best, sum);
+  }
+  last = std::nextafter((float)(best * (1.0 + 1e-6)), INFINITY);
+  last_g = g;
+  last_min = min_hits;
+  return last;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -553,6 +662,7 @@ int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks
       return VELO_EINVAL;
   Fwd F;
   std::memset(&F, 0, sizeof(F));
+  F.lam = fwd_lambda(*geometry, p.min_hits);
   F.h = *hits;
   F.t = *tracks;
   F.g = *geometry;

@@ -199,11 +199,14 @@ def test_constructed_cases_match_oracle():
         ([LINE], [(L + 12, x, y) for (L, x, y) in ex] + [(0xFFFFFFFF, x, y) for (L, x, y) in ex[:3]] + ex),
         ([LINE, L2], []),
         ([], ex),
+        ([LINE], line_hits(LINE, 0.1, shift=24.9)), ([LINE], line_hits(LINE, 0.1, shift=-25.1)),
+        ([LINE], line_hits(LINE, 0.1, range(4)) + line_hits(LINE, 0.1, range(4, 12), shift=2.9)),
     ]
     res = lines_result([c[0] for c in cases])
     g, r = run_both(res, *csr([c[1] for c in cases]))
     assert_forward_same(g, r)
     assert list(r[0][:6]) == [12, 12, 12, 11, 0, 12] and r[0][6] == 0  # the cases do what they say
+    assert list(r[0][-3:-1]) == [12, 0]  # the match distance at 24.9 and 25.1 mm
 
 
 def test_dense_layers_and_ragged_events():
