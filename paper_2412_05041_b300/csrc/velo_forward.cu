@@ -8,7 +8,8 @@
 //      radix passes over the order-preserving bits of x, one over the layer
 //      -- and gathered into sorted x, y arrays (shared memory when the event
 //      fits, else its slice of the workspace), with per-layer offsets and a
-//      bucket index per layer (first position of each of kFwdNB x buckets);
+//      bucket index per layer (first position of each of its x buckets),
+//      layers 0 and 1 also in y order with a bucket index over y;
 //   2. the tracks of the event, up to kFwdThreads at a time: one thread per
 //      track finds its line and the position ranges of its candidate windows
 //      in layers 0 and 1; a scan flattens the (track, candidate) pairs and
@@ -99,11 +100,15 @@ __device__ __forceinline__ uint32_t ordered_bits(float v) {  // monotone in v
 // flag bits: the hit offsets are invalid / the pixel-tracker result did not
 // fit its buffers (its track lists were not written)
 constexpr uint32_t kFwdBadOffsets = 1u, kFwdNoTracks = 2u;
-constexpr uint32_t kFwdIdBits = 29;  // hit ids in a rank key: events hold fewer than 2^29 hits
-constexpr uint32_t kFwdNB = 128;     // x buckets per layer
+constexpr uint32_t kFwdIdBits = 29;      // hit ids in a rank key: events hold fewer than 2^29 hits
 constexpr uint32_t kFwdSmemHits = 4096;  // events up to this size keep x, y in shared memory
 constexpr uint32_t kFwdSurv = 1280;      // pairs per round (each leaves at most one survivor)
 constexpr int kFwdCtasPerSm = 4;
+constexpr uint32_t kFwdRows = kFwdL + 2;  // bucket tables: x of every layer, y of layers 0 and 1
+
+// buckets per table: 256 of 16-bit positions for events in shared memory
+// (positions < kFwdSmemHits), 128 of 32-bit positions otherwise
+__host__ __device__ constexpr uint32_t fwd_nb(bool sm) { return sm ? 256u : 128u; }
 
 // One CTA: the event offsets start at 0, never decrease, end at n_hits and
 // give no event 2^29 hits or more; the pixel-tracker totals fit its capacities.
@@ -145,59 +150,91 @@ struct FwdSmem {
       unsigned long long best[kFwdThreads];
     } c;
   } u2;
-  uint32_t tab[kFwdL][kFwdNB + 1];  // first position of each bucket of each layer (+ its end)
-  uint32_t loff[kFwdL + 1];         // first position of each layer; [kFwdL] = end of the searched layers
-  float xmin[kFwdL], inv[kFwdL];    // bucket of x in layer L: (x - xmin) * inv, clamped
+  // row q < kFwdL: first position of each x bucket of layer q (+ the layer's
+  // end); rows kFwdL + r: first entry of each y bucket of layer r in the y order
+  union {
+    uint16_t s[kFwdRows][fwd_nb(true) + 1];
+    uint32_t g[kFwdRows][fwd_nb(false) + 1];
+  } tab;
+  float vmin[kFwdRows], vinv[kFwdRows];  // bucket of v in row q: (v - vmin) * vinv, clamped
+  uint32_t loff[kFwdL + 1];  // first position of each layer; [kFwdL] = end of the searched layers
   // layers 0 and 1 by y (candidate search): ypos holds (layer, x)-sorted
   // positions in (layer, finite y, y) order; yoff[2 r] .. yoff[2 r + 1] are
   // layer r's hits with a finite y
   uint32_t yoff[5];
-  uint32_t ytab[2][kFwdNB + 1];
-  float ymin[2], yinv[2];
-  float zl[kFwdL];
-  float wx[2];                      // candidate half-widths in x, layers 0 and 1
+  float dzm[kFwdL], dz0[kFwdL];  // z_L - z_mag, z_L - z_0
+  float zm0, reach;              // z_mag - z_0; max(|z_mag - z_0|, z_11 - z_0)
+  float wx[2];                   // candidate half-widths in x, layers 0 and 1
   uint32_t tmp[64];
-  uint32_t nsv;                     // survivors of the current round
-  uint32_t sv_pc[kFwdSurv];         // their sorted positions
-  uint8_t sv_j[kFwdSurv];           // and tracks in the chunk
+  uint32_t nsv;                  // survivors of the current round
+  uint32_t sv_pc[kFwdSurv];      // their sorted positions
+  uint8_t sv_j[kFwdSurv];        // and tracks in the chunk
 };
 
 // four CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
 static_assert(sizeof(FwdSmem) + 1024 <= 228 * 1024 / kFwdCtasPerSm, "shared memory for four CTAs per SM");
+static_assert(kFwdSmemHits <= 65535u, "16-bit bucket tables");
 
-__device__ __forceinline__ uint32_t fwd_bucket(float x, float xmin, float inv) {
-  const float t = fm(fs(x, xmin), inv);  // monotone in x; NaN goes to bucket 0
+template <bool SM>
+__device__ __forceinline__ uint32_t fwd_bucket(float v, float vmin, float inv) {
+  constexpr uint32_t NB = fwd_nb(SM);
+  const float t = fm(fs(v, vmin), inv);  // monotone in v; NaN goes to bucket 0
   if (!(t >= 0.0f)) return 0u;
-  if (t >= (float)kFwdNB) return kFwdNB - 1u;
+  if (t >= (float)NB) return NB - 1u;
   return (uint32_t)t;
 }
 
-// bucket of a sorted range's values: span and scale
-__device__ __forceinline__ void fwd_bucket_scale(float vmin, float vmax, float* lo, float* inv) {
-  const float span = fs(vmax, vmin);
-  float iv = span > 0.0f ? fd((float)kFwdNB, span) : 0.0f;
-  *lo = vmin;
-  *inv = isfinite(iv) ? iv : 0.0f;
+template <bool SM>
+__device__ __forceinline__ uint32_t tab_get(const FwdSmem& S, uint32_t row, uint32_t b) {
+  if constexpr (SM) return S.tab.s[row][b];
+  else return S.tab.g[row][b];
 }
 
-// the sorted hits of one event and their indexes
+template <bool SM>
+__device__ __forceinline__ void tab_set(FwdSmem& S, uint32_t row, uint32_t b, uint32_t v) {
+  if constexpr (SM) S.tab.s[row][b] = (uint16_t)v;
+  else S.tab.g[row][b] = v;
+}
+
+// first entry of row q at or after which every value >= v lies
+template <bool SM>
+__device__ __forceinline__ uint32_t tab_first(const FwdSmem& S, uint32_t row, float v) {
+  return tab_get<SM>(S, row, fwd_bucket<SM>(v, S.vmin[row], S.vinv[row]));
+}
+
+// first entry of row q before which every value <= v lies
+template <bool SM>
+__device__ __forceinline__ uint32_t tab_past(const FwdSmem& S, uint32_t row, float v) {
+  return tab_get<SM>(S, row, fwd_bucket<SM>(v, S.vmin[row], S.vinv[row]) + 1u);
+}
+
+// scale of row q's buckets over a sorted range [vmin, vmax]
+template <bool SM>
+__device__ __forceinline__ void fwd_bucket_scale(FwdSmem& S, uint32_t row, bool any, float vmin, float vmax) {
+  const float span = fs(vmax, vmin);
+  const float iv = any && span > 0.0f ? fd((float)fwd_nb(SM), span) : 0.0f;
+  S.vmin[row] = any ? vmin : 0.0f;
+  S.vinv[row] = isfinite(iv) ? iv : 0.0f;
+}
+
+// the sorted hits of one event
+template <bool SM>
 struct FwdEvent {
-  const float* sx;      // x in sorted order (shared or global memory)
+  const float* sx;      // x in sorted order (shared memory when SM, else global)
   const float* sy;
   const uint32_t* sid;  // hit id of each sorted position (global)
   const FwdSmem* S;
-  __device__ __forceinline__ uint32_t start(int L, float x) const {
-    return S->tab[L][fwd_bucket(x, S->xmin[L], S->inv[L])];
-  }
 };
 
 // nearest hit in x to xp (ties: the smaller id) with |x - xp| <= tol and
 // |y - yp| <= tol_y in layer L; returns its sorted position or kNone
-__device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent& V, int L, float xp, float yp, float tol, float tol_y) {
+template <bool SM>
+__device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent<SM>& V, int L, float xp, float yp, float tol,
+                                                float tol_y) {
   float lo_x, hi_x;
   fwd_range(xp, tol, &lo_x, &hi_x);
   const uint32_t end = V.S->loff[L + 1];
-  uint32_t pos = V.start(L, lo_x);  // every hit with x >= lo_x lies at or after it
+  uint32_t pos = tab_first<SM>(*V.S, L, lo_x);
   while (pos < end && V.sx[pos] < lo_x) ++pos;
   uint32_t best = kNone;
   float bd = 0.0f;
@@ -213,13 +250,13 @@ __device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent& V, int L, float 
 }
 
 // least-squares line v = a + b (z - z_0) through the found hits of layers [l0, l1)
-__device__ __forceinline__ void fwd_line(const uint32_t* hl, const float* v, const float* zl, int l0, int l1, float* a,
-                                         float* b) {
+__device__ __forceinline__ void fwd_line(const uint32_t* hl, const float* v, const float* dz0, int l0, int l1,
+                                         float* a, float* b) {
   float S0 = 0.0f, Sz = 0.0f, Szz = 0.0f, Sx = 0.0f, Sxz = 0.0f;
 #pragma unroll
   for (int L = l0; L < l1; ++L) {
     if (hl[L] == kNone) continue;
-    const float dz = fs(zl[L], zl[0]);
+    const float dz = dz0[L];
     const float xv = v[hl[L]];
     S0 = fa(S0, 1.0f);
     Sz = fa(Sz, dz);
@@ -242,45 +279,43 @@ struct FwdCand {
 // steps 3-5 for the candidate at sorted position pc of layer r of a track
 // whose line reaches the kick plane at (xm, ym) with slope ty: false when a
 // cut drops it
-__device__ __forceinline__ bool fwd_candidate(const FwdEvent& V, const Fwd& F, float xm, float ym, float ty, int r,
-                                              uint32_t pc, FwdCand& C) {
+template <bool SM>
+__device__ __forceinline__ bool fwd_candidate(const FwdEvent<SM>& V, const Fwd& F, float xm, float ym, float ty,
+                                              int r, uint32_t pc, FwdCand& C) {
   const velo_forward_params_t& P = F.p;
-  const float zmag = F.g.z_mag;
-  const float* zl = V.S->zl;
-  const float tk = fd(fs(V.sx[pc], xm), fs(zl[r], zmag));
+  const FwdSmem& S = *V.S;
+  const float tk = fd(fs(V.sx[pc], xm), S.dzm[r]);
   uint32_t n1 = 0;
 #pragma unroll
   for (int L = 0; L < 4; ++L) {
-    const float dzl = fs(zl[L], zmag);
-    C.hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, dzl)), fa(ym, fm(ty, dzl)), P.tol_x, P.tol_y);
+    C.hl[L] = fwd_nearest<SM>(V, L, fa(xm, fm(tk, S.dzm[L])), fa(ym, fm(ty, S.dzm[L])), P.tol_x, P.tol_y);
     n1 += C.hl[L] != kNone ? 1u : 0u;
   }
   if (n1 < 2) return false;
   float a1, b1;
-  fwd_line(C.hl, V.sx, zl, 0, 4, &a1, &b1);
+  fwd_line(C.hl, V.sx, S.dz0, 0, 4, &a1, &b1);
   uint32_t n = n1;
 #pragma unroll
   for (int L = 4; L < (int)kFwdL; ++L) {
-    const float dzl = fs(zl[L], zmag);
-    C.hl[L] = fwd_nearest(V, L, fa(a1, fm(b1, fs(zl[L], zl[0]))), fa(ym, fm(ty, dzl)), P.tol_x_far, P.tol_y);
+    C.hl[L] = fwd_nearest<SM>(V, L, fa(a1, fm(b1, S.dz0[L])), fa(ym, fm(ty, S.dzm[L])), P.tol_x_far, P.tol_y);
     n += C.hl[L] != kNone ? 1u : 0u;
   }
   if (n < P.min_hits) return false;
   float a, b;
-  fwd_line(C.hl, V.sx, zl, 0, kFwdL, &a, &b);
+  fwd_line(C.hl, V.sx, S.dz0, 0, kFwdL, &a, &b);
   float chi2 = 0.0f;
 #pragma unroll
   for (int L = 0; L < (int)kFwdL; ++L) {
     if (C.hl[L] == kNone) continue;
-    const float res = fd(fs(fs(V.sx[C.hl[L]], a), fm(b, fs(zl[L], zl[0]))), P.sigma_x);
+    const float res = fd(fs(fs(V.sx[C.hl[L]], a), fm(b, S.dz0[L])), P.sigma_x);
     chi2 = fa(chi2, fm(res, res));
   }
   const float rchi = fd(chi2, (float)(n - 2));
   if (!(rchi <= P.chi2ndf_max)) return false;
-  const float d = fs(fa(a, fm(b, fs(zmag, zl[0]))), xm);
+  const float d = fs(fa(a, fm(b, S.zm0)), xm);
   float ya, yb;
-  fwd_line(C.hl, V.sy, zl, 0, kFwdL, &ya, &yb);
-  const float dy = fs(fa(ya, fm(yb, fs(zmag, zl[0]))), ym);
+  fwd_line(C.hl, V.sy, S.dz0, 0, kFwdL, &ya, &yb);
+  const float dy = fs(fa(ya, fm(yb, S.zm0)), ym);
   const float ad = fa(fm(d, d), fm(dy, dy));
   if (!(ad <= fm(P.tol_match, P.tol_match))) return false;
   C.n = n;
@@ -305,30 +340,28 @@ __device__ __forceinline__ bool fwd_candidate(const FwdEvent& V, const Fwd& F, f
 // sets a candidate can end with (host arithmetic); the allowance
 // 1 mm + 2e-3 M (M the size of the coordinates involved) covers the binary32
 // rounding of both lines, its worst case being some 1e-4 M.
-__device__ __forceinline__ bool fwd_first_station(const FwdEvent& V, const Fwd& F, float xm, float ym, float ty, int r,
-                                                  uint32_t pc) {
+template <bool SM>
+__device__ __forceinline__ bool fwd_first_station(const FwdEvent<SM>& V, const Fwd& F, float xm, float ym, float ty,
+                                                  int r, uint32_t pc) {
   const velo_forward_params_t& P = F.p;
-  const float zmag = F.g.z_mag;
-  const float* zl = V.S->zl;
-  const float tk = fd(fs(V.sx[pc], xm), fs(zl[r], zmag));
+  const FwdSmem& S = *V.S;
+  const float tk = fd(fs(V.sx[pc], xm), S.dzm[r]);
   uint32_t hl[4];
   uint32_t n1 = 0;
 #pragma unroll
   for (int L = 0; L < 4; ++L) {
-    const float dzl = fs(zl[L], zmag);
-    hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, dzl)), fa(ym, fm(ty, dzl)), P.tol_x, P.tol_y);
+    hl[L] = fwd_nearest<SM>(V, L, fa(xm, fm(tk, S.dzm[L])), fa(ym, fm(ty, S.dzm[L])), P.tol_x, P.tol_y);
     n1 += hl[L] != kNone ? 1u : 0u;
   }
   if (n1 < 2) return false;
   float a1, b1;
-  fwd_line(hl, V.sx, zl, 0, 4, &a1, &b1);
+  fwd_line(hl, V.sx, S.dz0, 0, 4, &a1, &b1);
   float E = P.tol_x_far;
 #pragma unroll
   for (int L = 0; L < 4; ++L)
-    if (hl[L] != kNone) E = fmaxf(E, fabsf(fs(V.sx[hl[L]], fa(a1, fm(b1, fs(zl[L], zl[0]))))));
-  const float reach = fmaxf(fabsf(fs(zmag, zl[0])), fs(zl[kFwdL - 1], zl[0]));
-  const float M = fa(fa(fa(fabsf(a1), fm(fabsf(b1), reach)), fabsf(xm)), E);
-  const float d1 = fs(fa(a1, fm(b1, fs(zmag, zl[0]))), xm);
+    if (hl[L] != kNone) E = fmaxf(E, fabsf(fs(V.sx[hl[L]], fa(a1, fm(b1, S.dz0[L])))));
+  const float M = fa(fa(fa(fabsf(a1), fm(fabsf(b1), S.reach)), fabsf(xm)), E);
+  const float d1 = fs(fa(a1, fm(b1, S.zm0)), xm);
   return fabsf(d1) <= fa(fa(P.tol_match, fm(F.lam, E)), fa(1.0f, fm(2e-3f, M)));
 }
 
@@ -344,49 +377,21 @@ __device__ __forceinline__ void fwd_write_none(const Fwd& F, uint64_t t) {
   for (int k = 0; k < (int)VELO_FWD_STATE; ++k) F.o.state[t * VELO_FWD_STATE + k] = 0.0f;
 }
 
-__global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
-  extern __shared__ __align__(16) uint8_t fwd_smem_raw[];
-  FwdSmem& S = *reinterpret_cast<FwdSmem*>(fwd_smem_raw);
-  const uint64_t e = blockIdx.x;
+// Steps 1 (after the sort by (layer, x)) to 3 of one event.
+template <bool SM>
+__device__ __forceinline__ void fwd_event(const Fwd& F, FwdSmem& S, uint64_t e, uint64_t t0, uint64_t t1, uint64_t h0,
+                                          uint32_t n) {
   const uint32_t tid = threadIdx.x;
-  const uint64_t t0 = F.t.track_offsets[e], t1 = F.t.track_offsets[e + 1];
   const uint64_t cap = F.o.cap_tracks;
-  const uint32_t flag = *(const volatile uint32_t*)F.w.flag;
-  if (flag & kFwdNoTracks) return;  // no track lists to read: nothing is written
-  if (flag & kFwdBadOffsets) {      // hits rejected: no track has a downstream track
-    for (uint64_t t = t0 + tid; t < t1 && t < cap; t += kFwdThreads) fwd_write_none(F, t);
-    return;
-  }
-  const uint64_t h0 = F.h.event_offsets[e];
-  const uint32_t n = (uint32_t)(F.h.event_offsets[e + 1] - h0);
   const FwdWork& W = F.w;
-  if (tid < kFwdL) S.zl[tid] = F.g.z_layers[tid];
-  // 1. sort by (layer, x): four passes over the ordered bits of x, one over the layer
-  for (uint32_t i = tid; i < n; i += kFwdThreads) {
-    W.ka[h0 + i] = ordered_bits(F.h.x[h0 + i]);
-    W.va[h0 + i] = i;
-  }
-  __syncthreads();
   const uint32_t* lay = F.h.layer + h0;
   const float* xin = F.h.x + h0;
   const float* yin = F.h.y + h0;
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [](uint32_t k, uint32_t) { return k & 255u; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                                [](uint32_t k, uint32_t) { return k >> 24; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [lay, xin](uint32_t, uint32_t id) { return fwd_layer_of(lay, xin, id); }, S.u.cnt,
-                                S.tmp);
-  // sorted x, y (shared memory when the event fits), the sorted position of
-  // every id (into va, free after the sort), the first position of every
-  // layer (a layer's slots after its predecessor's layer get the position)
-  const bool big = n > kFwdSmemHits;
-  float* sx = big ? W.sx + h0 : S.u.xy;
-  float* sy = big ? W.sy + h0 : S.u.xy + kFwdSmemHits;
+  // sorted x, y, the sorted position of every id (into va, free after the
+  // sort), the first position of every layer (a layer's slots after its
+  // predecessor's layer get the position)
+  float* sx = SM ? S.u.xy : W.sx + h0;
+  float* sy = SM ? S.u.xy + kFwdSmemHits : W.sy + h0;
   const uint32_t* sid = W.vb + h0;
   uint32_t* pos_of = W.va + h0;
   for (uint32_t q = tid; q <= kFwdL; q += kFwdThreads) S.loff[q] = n;
@@ -427,40 +432,45 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
     for (uint32_t q = gp; q <= g; ++q) S.yoff[q] = i;
   }
   __syncthreads();
-  // bucket index of every layer over its x span, of layers 0 and 1 over their y span
+  // bucket tables: x of every layer over its span, y of layers 0 and 1 over theirs
+  constexpr uint32_t NB = fwd_nb(SM);
+  const float zmag = F.g.z_mag;
   if (tid < kFwdL) {
     const uint32_t lo = S.loff[tid], hi = S.loff[tid + 1];
-    fwd_bucket_scale(hi > lo ? sx[lo] : 0.0f, hi > lo ? sx[hi - 1] : 0.0f, &S.xmin[tid], &S.inv[tid]);
+    fwd_bucket_scale<SM>(S, tid, hi > lo, hi > lo ? sx[lo] : 0.0f, hi > lo ? sx[hi - 1] : 0.0f);
+    const float z = F.g.z_layers[tid];
+    S.dzm[tid] = fs(z, zmag);
+    S.dz0[tid] = fs(z, F.g.z_layers[0]);
   } else if (tid >= 32 && tid < 34) {
     const uint32_t r = tid - 32, lo = S.yoff[2 * r], hi = S.yoff[2 * r + 1];
-    fwd_bucket_scale(hi > lo ? sy[ypos[lo]] : 0.0f, hi > lo ? sy[ypos[hi - 1]] : 0.0f, &S.ymin[r], &S.yinv[r]);
+    fwd_bucket_scale<SM>(S, kFwdL + r, hi > lo, hi > lo ? sy[ypos[lo]] : 0.0f, hi > lo ? sy[ypos[hi - 1]] : 0.0f);
+  } else if (tid == 64) {
+    S.zm0 = fs(zmag, F.g.z_layers[0]);
+    S.reach = fmaxf(fabsf(S.zm0), fs(F.g.z_layers[kFwdL - 1], F.g.z_layers[0]));
+  } else if (tid >= 96 && tid < 98) {
+    S.wx[tid - 96] = fa(fm(fd(F.g.kappa, F.p.p_min), fs(F.g.z_layers[tid - 96], zmag)), F.p.tol_x);
   }
-  for (uint32_t i = tid; i < 2 * (kFwdNB + 1); i += kFwdThreads) {
-    const uint32_t r = i / (kFwdNB + 1);
-    S.ytab[r][i % (kFwdNB + 1)] = S.yoff[2 * r + 1];
-  }
-  if (tid < 2) S.wx[tid] = fa(fm(fd(F.g.kappa, F.p.p_min), fs(S.zl[tid], F.g.z_mag)), F.p.tol_x);
-  for (uint32_t i = tid; i < kFwdL * (kFwdNB + 1); i += kFwdThreads) {
-    const uint32_t L = i / (kFwdNB + 1);
-    S.tab[L][i % (kFwdNB + 1)] = S.loff[L + 1];  // buckets past the layer's last hit: its end
+  for (uint32_t i = tid; i < kFwdRows * (NB + 1); i += kFwdThreads) {
+    const uint32_t q = i / (NB + 1);  // entries past a row's last value: the row's end
+    tab_set<SM>(S, q, i % (NB + 1), q < kFwdL ? S.loff[q + 1] : S.yoff[2 * (q - kFwdL) + 1]);
   }
   __syncthreads();
   for (uint32_t pos = tid; pos < S.loff[kFwdL]; pos += kFwdThreads) {
     uint32_t L = 0;
     while (S.loff[L + 1] <= pos) ++L;
-    const uint32_t b = fwd_bucket(sx[pos], S.xmin[L], S.inv[L]);
-    const uint32_t bp = pos > S.loff[L] ? fwd_bucket(sx[pos - 1], S.xmin[L], S.inv[L]) + 1u : 0u;
-    for (uint32_t q = bp; q <= b; ++q) S.tab[L][q] = pos;
+    const uint32_t b = fwd_bucket<SM>(sx[pos], S.vmin[L], S.vinv[L]);
+    const uint32_t bp = pos > S.loff[L] ? fwd_bucket<SM>(sx[pos - 1], S.vmin[L], S.vinv[L]) + 1u : 0u;
+    for (uint32_t q = bp; q <= b; ++q) tab_set<SM>(S, L, q, pos);
   }
   for (uint32_t r = 0; r < 2; ++r)
     for (uint32_t i = S.yoff[2 * r] + tid; i < S.yoff[2 * r + 1]; i += kFwdThreads) {
-      const uint32_t b = fwd_bucket(sy[ypos[i]], S.ymin[r], S.yinv[r]);
-      const uint32_t bp = i > S.yoff[2 * r] ? fwd_bucket(sy[ypos[i - 1]], S.ymin[r], S.yinv[r]) + 1u : 0u;
-      for (uint32_t q = bp; q <= b; ++q) S.ytab[r][q] = i;
+      const uint32_t q = kFwdL + r;
+      const uint32_t b = fwd_bucket<SM>(sy[ypos[i]], S.vmin[q], S.vinv[q]);
+      const uint32_t bp = i > S.yoff[2 * r] ? fwd_bucket<SM>(sy[ypos[i - 1]], S.vmin[q], S.vinv[q]) + 1u : 0u;
+      for (uint32_t b2 = bp; b2 <= b; ++b2) tab_set<SM>(S, q, b2, i);
     }
   __syncthreads();
-  const FwdEvent V{sx, sy, sid, &S};
-  const float zmag = F.g.z_mag;
+  const FwdEvent<SM> V{sx, sy, sid, &S};
   // 2.-3. the tracks, kFwdThreads at a time
   for (uint64_t tc = t0; tc < t1; tc += kFwdThreads) {
     const uint64_t t = tc + tid;
@@ -483,9 +493,9 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           float lo_y, hi_y;
-          fwd_range(fa(ym, fm(ty, fs(S.zl[r], zmag))), F.p.win_y, &lo_y, &hi_y);
-          const uint32_t lo = S.ytab[r][fwd_bucket(lo_y, S.ymin[r], S.yinv[r])];
-          const uint32_t hi = S.ytab[r][fwd_bucket(hi_y, S.ymin[r], S.yinv[r]) + 1u];
+          fwd_range(fa(ym, fm(ty, S.dzm[r])), F.p.win_y, &lo_y, &hi_y);
+          const uint32_t lo = tab_first<SM>(S, kFwdL + r, lo_y);
+          const uint32_t hi = tab_past<SM>(S, kFwdL + r, hi_y);
           S.u2.c.rlo[tid][r] = lo;
           const uint32_t len = hi > lo ? hi - lo : 0u;
           if (r == 0) S.u2.c.rn0[tid] = len;
@@ -518,11 +528,10 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
         const int r = k < S.u2.c.rn0[j] ? 0 : 1;
         const uint32_t pc = ypos[S.u2.c.rlo[j][r] + (r ? k - S.u2.c.rn0[j] : k)];
         const float4 tr = S.u2.c.trk[j];
-        const float dzr = fs(S.zl[r], zmag);
-        if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, dzr)))) <= S.wx[r]) ||
-            !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, dzr)))) <= F.p.win_y))
+        if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, S.dzm[r])))) <= S.wx[r]) ||
+            !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, S.dzm[r])))) <= F.p.win_y))
           continue;
-        if (!fwd_first_station(V, F, tr.x, tr.y, tr.w, r, pc)) continue;
+        if (!fwd_first_station<SM>(V, F, tr.x, tr.y, tr.w, r, pc)) continue;
         const uint32_t slot = atomicAdd(&S.nsv, 1u);
         S.sv_pc[slot] = pc;
         S.sv_j[slot] = (uint8_t)j;
@@ -533,7 +542,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
         const uint32_t pc = S.sv_pc[i], j = S.sv_j[i];
         const float4 tr = S.u2.c.trk[j];
         FwdCand C;
-        if (fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C))
+        if (fwd_candidate<SM>(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C))
           atomicMin(&S.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
       }
       __syncthreads();
@@ -547,7 +556,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
         const uint32_t pc = pos_of[(uint32_t)(key & ((1ull << kFwdIdBits) - 1ull))];
         const float4 tr = S.u2.c.trk[tid];
         FwdCand C;
-        fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C);
+        fwd_candidate<SM>(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C);
         F.o.n_found[t] = C.n;
 #pragma unroll
         for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[t * kFwdL + L] = C.hl[L] != kNone ? sid[C.hl[L]] : kNone;
@@ -562,6 +571,49 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
     }
     __syncthreads();
   }
+}
+
+// One CTA per event; the instance with SM = true takes the events whose hits
+// fit in shared memory, the other the rest (a CTA of the wrong instance
+// returns at once).
+template <bool SM>
+__global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
+  extern __shared__ __align__(16) uint8_t fwd_smem_raw[];
+  FwdSmem& S = *reinterpret_cast<FwdSmem*>(fwd_smem_raw);
+  const uint64_t e = blockIdx.x;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t flag = *(const volatile uint32_t*)F.w.flag;
+  if (flag & kFwdNoTracks) return;  // no track lists to read: nothing is written
+  const uint64_t t0 = F.t.track_offsets[e], t1 = F.t.track_offsets[e + 1];
+  if (flag & kFwdBadOffsets) {      // hits rejected: no track has a downstream track
+    if (SM)
+      for (uint64_t t = t0 + tid; t < t1 && t < F.o.cap_tracks; t += kFwdThreads) fwd_write_none(F, t);
+    return;
+  }
+  const uint64_t h0 = F.h.event_offsets[e];
+  const uint32_t n = (uint32_t)(F.h.event_offsets[e + 1] - h0);
+  if ((n <= kFwdSmemHits) != SM) return;
+  const FwdWork& W = F.w;
+  // 1. sort by (layer, x): four passes over the ordered bits of x, one over the layer
+  for (uint32_t i = tid; i < n; i += kFwdThreads) {
+    W.ka[h0 + i] = ordered_bits(F.h.x[h0 + i]);
+    W.va[h0 + i] = i;
+  }
+  __syncthreads();
+  const uint32_t* lay = F.h.layer + h0;
+  const float* xin = F.h.x + h0;
+  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                                [](uint32_t k, uint32_t) { return k & 255u; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
+                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
+                                [](uint32_t k, uint32_t) { return k >> 24; }, S.u.cnt, S.tmp);
+  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                                [lay, xin](uint32_t, uint32_t id) { return fwd_layer_of(lay, xin, id); }, S.u.cnt,
+                                S.tmp);
+  fwd_event<SM>(F, S, e, t0, t1, h0, n);
 }
 
 }  // namespace
@@ -670,9 +722,14 @@ int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks
   F.o = *out;
   if (fwd_carve(static_cast<uint8_t*>(workspace), hits->n_hits, &F.w) > workspace_bytes) return VELO_ECAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!set_max_smem_once(reinterpret_cast<const void*>(k_forward), 2)) return VELO_ECUDA;
+  if (!set_max_smem_once(reinterpret_cast<const void*>(k_forward<true>), 2) ||
+      !set_max_smem_once(reinterpret_cast<const void*>(k_forward<false>), 3))
+    return VELO_ECUDA;
   k_fwd_validate<<<1, 1024, 0, s>>>(F);
-  if (hits->n_events) k_forward<<<(uint32_t)hits->n_events, kFwdThreads, sizeof(FwdSmem), s>>>(F);
+  if (hits->n_events) {
+    k_forward<true><<<(uint32_t)hits->n_events, kFwdThreads, sizeof(FwdSmem), s>>>(F);
+    k_forward<false><<<(uint32_t)hits->n_events, kFwdThreads, sizeof(FwdSmem), s>>>(F);
+  }
   return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;
 }
 
