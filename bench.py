@@ -414,7 +414,7 @@ def run_forward(args, dev, vp, n_ev):
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "algorithmic_bytes": alg,
                          "traffic": None if traffic is None else traffic * n_ev,
                          "peak_source": f"{peak_kind} hbm_gbs (copy)"},
-            "gpu_launches_per_call": 2}
+            "gpu_launches_per_call": 2 + (H > 4096) + (H > 16384)}  # validate, large events, huge events, the rest
 
 
 def run_ours(args):

@@ -10,14 +10,19 @@
 //      fits, else its slice of the workspace), with per-layer offsets and a
 //      bucket index per layer (first position of each of its x buckets),
 //      layers 0 and 1 also in y order with a bucket index over y;
-//   2. the tracks of the event, up to kFwdThreads at a time: one thread per
-//      track finds its line and the position ranges of its candidate windows
-//      in layers 0 and 1; a scan flattens the (track, candidate) pairs and
-//      the threads share them out evenly -- each runs the exact window test
-//      and, for a candidate inside it, the hit collection, fits and cuts, and
-//      offers the candidate's rank key (hits, distance, id) to its track by a
-//      64-bit atomicMin;
+//   2. the tracks of the event, up to one per thread at a time: one thread
+//      per track finds its line and the ranges of its candidate windows in
+//      layers 0 and 1; a scan flattens the (track, candidate) pairs and the
+//      threads share them out evenly -- the exact window test, the first
+//      station and a bound on the match distance; the survivors' far
+//      stations, fits and cuts, each offering its rank key (hits, distance,
+//      id) to its track by a 64-bit atomicMin;
 //   3. one thread per track recomputes its winning candidate and writes it.
+// The work of an event grows about as the square of its hit count, so events
+// of up to kFwdSmallHits hits run on 256-thread CTAs, four per SM, one event
+// each; larger events on 1024-thread CTAs, one per SM, looping over a list
+// of them that the validation kernel builds (shared memory up to
+// kFwdBigHits hits, the workspace beyond).
 // All arithmetic is binary32 in the order the oracle uses (-fmad=false and
 // the __f*_rn intrinsics); every choice is a minimum under a strict total
 // order, so the search order does not matter.
@@ -27,6 +32,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "velo_device.cuh"
 #include "velo_fit.cuh"
@@ -36,7 +42,6 @@ namespace velo {
 
 namespace {
 
-constexpr int kFwdThreads = 256;
 constexpr uint32_t kFwdL = VELO_FWD_LAYERS;
 
 // x range [xp - tol - m, xp + tol + m] searched in a layer's sorted x: m =
@@ -56,6 +61,8 @@ struct FwdWork {
   float *sx, *sy;            // x, y in sorted order
   uint32_t *yka, *ykb;       // layers 0 and 1 by y: keys (ordered y bits)
   uint32_t *yva, *yvb;       // and (layer, x)-sorted positions
+  uint32_t* nlist;           // [2]: events in list_big, list_huge
+  uint32_t *list_big, *list_huge;  // events of more than kFwdSmallHits / kFwdBigHits hits
 };
 
 struct Fwd {
@@ -68,7 +75,7 @@ struct Fwd {
   float lam;  // largest sum |w_i| of the final x fit's weights at the kick plane (any admissible hit set)
 };
 
-uint64_t fwd_carve(uint8_t* base, uint64_t n_hits, FwdWork* w) {
+uint64_t fwd_carve(uint8_t* base, uint64_t n_events, uint64_t n_hits, FwdWork* w) {
   uint64_t off = 0;
   auto take = [&](uint64_t bytes) -> uint8_t* {
     off = (off + 255ull) & ~255ull;
@@ -88,6 +95,10 @@ uint64_t fwd_carve(uint8_t* base, uint64_t n_hits, FwdWork* w) {
   w->ykb = reinterpret_cast<uint32_t*>(take(4 * H));
   w->yva = reinterpret_cast<uint32_t*>(take(4 * H));
   w->yvb = reinterpret_cast<uint32_t*>(take(4 * H));
+  const uint64_t E = n_events ? n_events : 1;
+  w->nlist = reinterpret_cast<uint32_t*>(take(8));
+  w->list_big = reinterpret_cast<uint32_t*>(take(4 * E));
+  w->list_huge = reinterpret_cast<uint32_t*>(take(4 * E));
   return (off + 255ull) & ~255ull;
 }
 
@@ -100,20 +111,19 @@ __device__ __forceinline__ uint32_t ordered_bits(float v) {  // monotone in v
 // flag bits: the hit offsets are invalid / the pixel-tracker result did not
 // fit its buffers (its track lists were not written)
 constexpr uint32_t kFwdBadOffsets = 1u, kFwdNoTracks = 2u;
-constexpr uint32_t kFwdIdBits = 29;      // hit ids in a rank key: events hold fewer than 2^29 hits
-constexpr uint32_t kFwdSmemHits = 4096;  // events up to this size keep x, y in shared memory
-constexpr uint32_t kFwdSurv = 1280;      // pairs per round (each leaves at most one survivor)
-constexpr int kFwdCtasPerSm = 4;
-constexpr uint32_t kFwdRows = kFwdL + 2;  // bucket tables: x of every layer, y of layers 0 and 1
-
-// buckets per table: 256 of 16-bit positions for events in shared memory
-// (positions < kFwdSmemHits), 128 of 32-bit positions otherwise
-__host__ __device__ constexpr uint32_t fwd_nb(bool sm) { return sm ? 256u : 128u; }
+constexpr uint32_t kFwdIdBits = 29;        // hit ids in a rank key: events hold fewer than 2^29 hits
+constexpr uint32_t kFwdSmallHits = 4096;   // events up to this size: 256-thread CTAs, hits in shared memory
+constexpr uint32_t kFwdBigHits = 16384;    // up to this size: 1024-thread CTAs, hits in shared memory
+constexpr uint32_t kFwdRows = kFwdL + 2;   // bucket tables: x of every layer, y of layers 0 and 1
 
 // One CTA: the event offsets start at 0, never decrease, end at n_hits and
-// give no event 2^29 hits or more; the pixel-tracker totals fit its capacities.
+// give no event 2^29 hits or more; the pixel-tracker totals fit its
+// capacities.  With valid offsets, the lists of events above kFwdSmallHits
+// and above kFwdBigHits hits (any order).
 __global__ void __launch_bounds__(1024) k_fwd_validate(Fwd F) {
+  __shared__ uint32_t nl[2];
   const uint64_t E = F.h.n_events;
+  if (threadIdx.x < 2) nl[threadIdx.x] = 0u;
   int bad = 0;
   if (threadIdx.x == 0) bad |= (F.h.event_offsets[0] != 0ull) | (F.h.event_offsets[E] != F.h.n_hits);
   for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) {
@@ -121,11 +131,20 @@ __global__ void __launch_bounds__(1024) k_fwd_validate(Fwd F) {
     bad |= (b < a) | (b - a >= (1ull << kFwdIdBits));
   }
   bad = __syncthreads_or(bad);
+  if (!bad)
+    for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) {
+      const uint64_t n = F.h.event_offsets[e + 1] - F.h.event_offsets[e];
+      if (n > kFwdBigHits) F.w.list_huge[atomicAdd(&nl[1], 1u)] = (uint32_t)e;
+      else if (n > kFwdSmallHits) F.w.list_big[atomicAdd(&nl[0], 1u)] = (uint32_t)e;
+    }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const velo_output_t& o = F.t;
     const bool fits = (!o.cap_clusters || o.totals[0] <= o.cap_clusters) && (!o.cap_tracks || o.totals[1] <= o.cap_tracks) &&
                       (!o.cap_track_hits || o.totals[2] <= o.cap_track_hits);
     *F.w.flag = (bad ? kFwdBadOffsets : 0u) | (fits ? 0u : kFwdNoTracks);
+    F.w.nlist[0] = nl[0];
+    F.w.nlist[1] = nl[1];
   }
 }
 
@@ -135,26 +154,33 @@ __device__ __forceinline__ uint32_t fwd_layer_of(const uint32_t* lay, const floa
   return isfinite(x[id]) ? min(lay[id], kFwdL) : kFwdL;
 }
 
+// Shared memory of a CTA of NT threads holding up to HC hits (HC = 0: the
+// hits stay in the workspace).
+template <int NT, uint32_t HC>
 struct FwdSmem {
+  static constexpr bool SM = HC > 0;
+  static constexpr uint32_t NB = SM ? 256u : 128u;  // buckets per table (16-bit entries when SM)
+  static constexpr uint32_t SURV = 5u * NT;         // pairs per round (each leaves at most one survivor)
+  using JT = typename std::conditional<NT <= 256, uint8_t, uint16_t>::type;
   union {
-    uint32_t cnt[radix_counters(kFwdThreads)];  // radix counters of the (layer, x) sort
-    float xy[2 * kFwdSmemHits];                 // then x, y in sorted order (events that fit)
+    uint32_t cnt[radix_counters(NT)];  // radix counters of the (layer, x) sort
+    float xy[2 * (SM ? HC : 1u)];      // then x, y in sorted order
   } u;
   union {
-    uint32_t cnt[radix_counters(kFwdThreads)];  // radix counters of the y sort
-    struct {                                    // then the tracks of the current chunk
-      float4 trk[kFwdThreads];                  // xm, ym, tx, ty
-      uint32_t rlo[kFwdThreads][2];             // first entries of the candidate ranges in the y order
-      uint32_t rn0[kFwdThreads];                // length of the layer-0 range
-      uint32_t poff[kFwdThreads + 1];           // first pair of each track
-      unsigned long long best[kFwdThreads];
+    uint32_t cnt[radix_counters(NT)];  // radix counters of the y sort
+    struct {                           // then the tracks of the current chunk
+      float4 trk[NT];                  // xm, ym, tx, ty
+      uint32_t rlo[NT][2];             // first entries of the candidate ranges in the y order
+      uint32_t rn0[NT];                // length of the layer-0 range
+      uint32_t poff[NT + 1];           // first pair of each track
+      unsigned long long best[NT];
     } c;
   } u2;
   // row q < kFwdL: first position of each x bucket of layer q (+ the layer's
   // end); rows kFwdL + r: first entry of each y bucket of layer r in the y order
   union {
-    uint16_t s[kFwdRows][fwd_nb(true) + 1];
-    uint32_t g[kFwdRows][fwd_nb(false) + 1];
+    uint16_t s[kFwdRows][256 + 1];
+    uint32_t g[kFwdRows][128 + 1];
   } tab;
   float vmin[kFwdRows], vinv[kFwdRows];  // bucket of v in row q: (v - vmin) * vinv, clamped
   uint32_t loff[kFwdL + 1];  // first position of each layer; [kFwdL] = end of the searched layers
@@ -167,74 +193,78 @@ struct FwdSmem {
   float wx[2];                   // candidate half-widths in x, layers 0 and 1
   uint32_t tmp[64];
   uint32_t nsv;                  // survivors of the current round
-  uint32_t sv_pc[kFwdSurv];      // their sorted positions
-  uint8_t sv_j[kFwdSurv];        // and tracks in the chunk
+  uint32_t sv_pc[SURV];          // their sorted positions
+  JT sv_j[SURV];                 // and tracks in the chunk
 };
 
-// four CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
-static_assert(sizeof(FwdSmem) + 1024 <= 228 * 1024 / kFwdCtasPerSm, "shared memory for four CTAs per SM");
-static_assert(kFwdSmemHits <= 65535u, "16-bit bucket tables");
+using FwdSmall = FwdSmem<256, kFwdSmallHits>;
+using FwdBig = FwdSmem<1024, kFwdBigHits>;
+using FwdHuge = FwdSmem<1024, 0>;
+// 228 KB of shared memory per SM, 1 KB of it reserved per CTA: four small
+// CTAs per SM, one big
+static_assert(sizeof(FwdSmall) + 1024 <= 228 * 1024 / 4, "shared memory for four CTAs per SM");
+static_assert(sizeof(FwdBig) <= 227 * 1024, "shared memory of one CTA");
+static_assert(kFwdBigHits <= 65535u, "16-bit bucket tables");
 
-template <bool SM>
+template <class S>
 __device__ __forceinline__ uint32_t fwd_bucket(float v, float vmin, float inv) {
-  constexpr uint32_t NB = fwd_nb(SM);
   const float t = fm(fs(v, vmin), inv);  // monotone in v; NaN goes to bucket 0
   if (!(t >= 0.0f)) return 0u;
-  if (t >= (float)NB) return NB - 1u;
+  if (t >= (float)S::NB) return S::NB - 1u;
   return (uint32_t)t;
 }
 
-template <bool SM>
-__device__ __forceinline__ uint32_t tab_get(const FwdSmem& S, uint32_t row, uint32_t b) {
-  if constexpr (SM) return S.tab.s[row][b];
-  else return S.tab.g[row][b];
+template <class S>
+__device__ __forceinline__ uint32_t tab_get(const S& sm, uint32_t row, uint32_t b) {
+  if constexpr (S::SM) return sm.tab.s[row][b];
+  else return sm.tab.g[row][b];
 }
 
-template <bool SM>
-__device__ __forceinline__ void tab_set(FwdSmem& S, uint32_t row, uint32_t b, uint32_t v) {
-  if constexpr (SM) S.tab.s[row][b] = (uint16_t)v;
-  else S.tab.g[row][b] = v;
+template <class S>
+__device__ __forceinline__ void tab_set(S& sm, uint32_t row, uint32_t b, uint32_t v) {
+  if constexpr (S::SM) sm.tab.s[row][b] = (uint16_t)v;
+  else sm.tab.g[row][b] = v;
 }
 
 // first entry of row q at or after which every value >= v lies
-template <bool SM>
-__device__ __forceinline__ uint32_t tab_first(const FwdSmem& S, uint32_t row, float v) {
-  return tab_get<SM>(S, row, fwd_bucket<SM>(v, S.vmin[row], S.vinv[row]));
+template <class S>
+__device__ __forceinline__ uint32_t tab_first(const S& sm, uint32_t row, float v) {
+  return tab_get(sm, row, fwd_bucket<S>(v, sm.vmin[row], sm.vinv[row]));
 }
 
 // first entry of row q before which every value <= v lies
-template <bool SM>
-__device__ __forceinline__ uint32_t tab_past(const FwdSmem& S, uint32_t row, float v) {
-  return tab_get<SM>(S, row, fwd_bucket<SM>(v, S.vmin[row], S.vinv[row]) + 1u);
+template <class S>
+__device__ __forceinline__ uint32_t tab_past(const S& sm, uint32_t row, float v) {
+  return tab_get(sm, row, fwd_bucket<S>(v, sm.vmin[row], sm.vinv[row]) + 1u);
 }
 
 // scale of row q's buckets over a sorted range [vmin, vmax]
-template <bool SM>
-__device__ __forceinline__ void fwd_bucket_scale(FwdSmem& S, uint32_t row, bool any, float vmin, float vmax) {
+template <class S>
+__device__ __forceinline__ void fwd_bucket_scale(S& sm, uint32_t row, bool any, float vmin, float vmax) {
   const float span = fs(vmax, vmin);
-  const float iv = any && span > 0.0f ? fd((float)fwd_nb(SM), span) : 0.0f;
-  S.vmin[row] = any ? vmin : 0.0f;
-  S.vinv[row] = isfinite(iv) ? iv : 0.0f;
+  const float iv = any && span > 0.0f ? fd((float)S::NB, span) : 0.0f;
+  sm.vmin[row] = any ? vmin : 0.0f;
+  sm.vinv[row] = isfinite(iv) ? iv : 0.0f;
 }
 
 // the sorted hits of one event
-template <bool SM>
+template <class S>
 struct FwdEvent {
-  const float* sx;      // x in sorted order (shared memory when SM, else global)
+  const float* sx;      // x in sorted order (shared memory when S::SM, else global)
   const float* sy;
   const uint32_t* sid;  // hit id of each sorted position (global)
-  const FwdSmem* S;
+  const S* sm;
 };
 
 // nearest hit in x to xp (ties: the smaller id) with |x - xp| <= tol and
 // |y - yp| <= tol_y in layer L; returns its sorted position or kNone
-template <bool SM>
-__device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent<SM>& V, int L, float xp, float yp, float tol,
+template <class S>
+__device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent<S>& V, int L, float xp, float yp, float tol,
                                                 float tol_y) {
   float lo_x, hi_x;
   fwd_range(xp, tol, &lo_x, &hi_x);
-  const uint32_t end = V.S->loff[L + 1];
-  uint32_t pos = tab_first<SM>(*V.S, L, lo_x);
+  const uint32_t end = V.sm->loff[L + 1];
+  uint32_t pos = tab_first(*V.sm, L, lo_x);
   while (pos < end && V.sx[pos] < lo_x) ++pos;
   uint32_t best = kNone;
   float bd = 0.0f;
@@ -279,43 +309,43 @@ struct FwdCand {
 // steps 3-5 for the candidate at sorted position pc of layer r of a track
 // whose line reaches the kick plane at (xm, ym) with slope ty: false when a
 // cut drops it
-template <bool SM>
-__device__ __forceinline__ bool fwd_candidate(const FwdEvent<SM>& V, const Fwd& F, float xm, float ym, float ty,
-                                              int r, uint32_t pc, FwdCand& C) {
+template <class S>
+__device__ __forceinline__ bool fwd_candidate(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty, int r,
+                                              uint32_t pc, FwdCand& C) {
   const velo_forward_params_t& P = F.p;
-  const FwdSmem& S = *V.S;
-  const float tk = fd(fs(V.sx[pc], xm), S.dzm[r]);
+  const S& sm = *V.sm;
+  const float tk = fd(fs(V.sx[pc], xm), sm.dzm[r]);
   uint32_t n1 = 0;
 #pragma unroll
   for (int L = 0; L < 4; ++L) {
-    C.hl[L] = fwd_nearest<SM>(V, L, fa(xm, fm(tk, S.dzm[L])), fa(ym, fm(ty, S.dzm[L])), P.tol_x, P.tol_y);
+    C.hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, sm.dzm[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x, P.tol_y);
     n1 += C.hl[L] != kNone ? 1u : 0u;
   }
   if (n1 < 2) return false;
   float a1, b1;
-  fwd_line(C.hl, V.sx, S.dz0, 0, 4, &a1, &b1);
+  fwd_line(C.hl, V.sx, sm.dz0, 0, 4, &a1, &b1);
   uint32_t n = n1;
 #pragma unroll
   for (int L = 4; L < (int)kFwdL; ++L) {
-    C.hl[L] = fwd_nearest<SM>(V, L, fa(a1, fm(b1, S.dz0[L])), fa(ym, fm(ty, S.dzm[L])), P.tol_x_far, P.tol_y);
+    C.hl[L] = fwd_nearest(V, L, fa(a1, fm(b1, sm.dz0[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x_far, P.tol_y);
     n += C.hl[L] != kNone ? 1u : 0u;
   }
   if (n < P.min_hits) return false;
   float a, b;
-  fwd_line(C.hl, V.sx, S.dz0, 0, kFwdL, &a, &b);
+  fwd_line(C.hl, V.sx, sm.dz0, 0, kFwdL, &a, &b);
   float chi2 = 0.0f;
 #pragma unroll
   for (int L = 0; L < (int)kFwdL; ++L) {
     if (C.hl[L] == kNone) continue;
-    const float res = fd(fs(fs(V.sx[C.hl[L]], a), fm(b, S.dz0[L])), P.sigma_x);
+    const float res = fd(fs(fs(V.sx[C.hl[L]], a), fm(b, sm.dz0[L])), P.sigma_x);
     chi2 = fa(chi2, fm(res, res));
   }
   const float rchi = fd(chi2, (float)(n - 2));
   if (!(rchi <= P.chi2ndf_max)) return false;
-  const float d = fs(fa(a, fm(b, S.zm0)), xm);
+  const float d = fs(fa(a, fm(b, sm.zm0)), xm);
   float ya, yb;
-  fwd_line(C.hl, V.sy, S.dz0, 0, kFwdL, &ya, &yb);
-  const float dy = fs(fa(ya, fm(yb, S.zm0)), ym);
+  fwd_line(C.hl, V.sy, sm.dz0, 0, kFwdL, &ya, &yb);
+  const float dy = fs(fa(ya, fm(yb, sm.zm0)), ym);
   const float ad = fa(fm(d, d), fm(dy, dy));
   if (!(ad <= fm(P.tol_match, P.tol_match))) return false;
   C.n = n;
@@ -340,28 +370,28 @@ __device__ __forceinline__ bool fwd_candidate(const FwdEvent<SM>& V, const Fwd& 
 // sets a candidate can end with (host arithmetic); the allowance
 // 1 mm + 2e-3 M (M the size of the coordinates involved) covers the binary32
 // rounding of both lines, its worst case being some 1e-4 M.
-template <bool SM>
-__device__ __forceinline__ bool fwd_first_station(const FwdEvent<SM>& V, const Fwd& F, float xm, float ym, float ty,
+template <class S>
+__device__ __forceinline__ bool fwd_first_station(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty,
                                                   int r, uint32_t pc) {
   const velo_forward_params_t& P = F.p;
-  const FwdSmem& S = *V.S;
-  const float tk = fd(fs(V.sx[pc], xm), S.dzm[r]);
+  const S& sm = *V.sm;
+  const float tk = fd(fs(V.sx[pc], xm), sm.dzm[r]);
   uint32_t hl[4];
   uint32_t n1 = 0;
 #pragma unroll
   for (int L = 0; L < 4; ++L) {
-    hl[L] = fwd_nearest<SM>(V, L, fa(xm, fm(tk, S.dzm[L])), fa(ym, fm(ty, S.dzm[L])), P.tol_x, P.tol_y);
+    hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, sm.dzm[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x, P.tol_y);
     n1 += hl[L] != kNone ? 1u : 0u;
   }
   if (n1 < 2) return false;
   float a1, b1;
-  fwd_line(hl, V.sx, S.dz0, 0, 4, &a1, &b1);
+  fwd_line(hl, V.sx, sm.dz0, 0, 4, &a1, &b1);
   float E = P.tol_x_far;
 #pragma unroll
   for (int L = 0; L < 4; ++L)
-    if (hl[L] != kNone) E = fmaxf(E, fabsf(fs(V.sx[hl[L]], fa(a1, fm(b1, S.dz0[L])))));
-  const float M = fa(fa(fa(fabsf(a1), fm(fabsf(b1), S.reach)), fabsf(xm)), E);
-  const float d1 = fs(fa(a1, fm(b1, S.zm0)), xm);
+    if (hl[L] != kNone) E = fmaxf(E, fabsf(fs(V.sx[hl[L]], fa(a1, fm(b1, sm.dz0[L])))));
+  const float M = fa(fa(fa(fabsf(a1), fm(fabsf(b1), sm.reach)), fabsf(xm)), E);
+  const float d1 = fs(fa(a1, fm(b1, sm.zm0)), xm);
   return fabsf(d1) <= fa(fa(P.tol_match, fm(F.lam, E)), fa(1.0f, fm(2e-3f, M)));
 }
 
@@ -377,102 +407,120 @@ __device__ __forceinline__ void fwd_write_none(const Fwd& F, uint64_t t) {
   for (int k = 0; k < (int)VELO_FWD_STATE; ++k) F.o.state[t * VELO_FWD_STATE + k] = 0.0f;
 }
 
-// Steps 1 (after the sort by (layer, x)) to 3 of one event.
-template <bool SM>
-__device__ __forceinline__ void fwd_event(const Fwd& F, FwdSmem& S, uint64_t e, uint64_t t0, uint64_t t1, uint64_t h0,
-                                          uint32_t n) {
+// Steps 1 to 3 of event e on a CTA of NT threads (S: its shared memory).
+template <int NT, class S>
+__device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
   const uint32_t tid = threadIdx.x;
   const uint64_t cap = F.o.cap_tracks;
   const FwdWork& W = F.w;
+  const uint64_t t0 = F.t.track_offsets[e], t1 = F.t.track_offsets[e + 1];
+  const uint64_t h0 = F.h.event_offsets[e];
+  const uint32_t n = (uint32_t)(F.h.event_offsets[e + 1] - h0);
   const uint32_t* lay = F.h.layer + h0;
   const float* xin = F.h.x + h0;
   const float* yin = F.h.y + h0;
+  // 1. sort by (layer, x): four passes over the ordered bits of x, one over the layer
+  for (uint32_t i = tid; i < n; i += NT) {
+    W.ka[h0 + i] = ordered_bits(xin[i]);
+    W.va[h0 + i] = i;
+  }
+  __syncthreads();
+  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n, [](uint32_t k, uint32_t) { return k & 255u; },
+                       sm.u.cnt, sm.tmp);
+  radix_pass<NT, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
+                       [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, sm.u.cnt, sm.tmp);
+  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                       [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, sm.u.cnt, sm.tmp);
+  radix_pass<NT, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n, [](uint32_t k, uint32_t) { return k >> 24; },
+                       sm.u.cnt, sm.tmp);
+  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
+                       [lay, xin](uint32_t, uint32_t id) { return fwd_layer_of(lay, xin, id); }, sm.u.cnt, sm.tmp);
   // sorted x, y, the sorted position of every id (into va, free after the
   // sort), the first position of every layer (a layer's slots after its
   // predecessor's layer get the position)
-  float* sx = SM ? S.u.xy : W.sx + h0;
-  float* sy = SM ? S.u.xy + kFwdSmemHits : W.sy + h0;
+  float* sx = S::SM ? sm.u.xy : W.sx + h0;
+  float* sy = S::SM ? sm.u.xy + n : W.sy + h0;
   const uint32_t* sid = W.vb + h0;
   uint32_t* pos_of = W.va + h0;
-  for (uint32_t q = tid; q <= kFwdL; q += kFwdThreads) S.loff[q] = n;
+  for (uint32_t q = tid; q <= kFwdL; q += NT) sm.loff[q] = n;
   __syncthreads();
-  for (uint32_t pos = tid; pos < n; pos += kFwdThreads) {
+  for (uint32_t pos = tid; pos < n; pos += NT) {
     const uint32_t id = sid[pos];
     sx[pos] = xin[id];
     sy[pos] = yin[id];
     pos_of[id] = pos;
     const uint32_t L = fwd_layer_of(lay, xin, id), Lp = pos ? fwd_layer_of(lay, xin, sid[pos - 1]) + 1u : 0u;
-    for (uint32_t q = Lp; q <= L; ++q) S.loff[q] = pos;
+    for (uint32_t q = Lp; q <= L; ++q) sm.loff[q] = pos;
   }
   __syncthreads();
   // layers 0 and 1 sorted by y: four passes over the ordered bits of y, one
   // over (layer, y not finite)
-  const uint32_t n01 = S.loff[2];
-  for (uint32_t pos = tid; pos < n01; pos += kFwdThreads) {
+  const uint32_t n01 = sm.loff[2];
+  for (uint32_t pos = tid; pos < n01; pos += NT) {
     W.yka[h0 + pos] = ordered_bits(sy[pos]);
     W.yva[h0 + pos] = pos;
   }
   __syncthreads();
-  const uint32_t l1 = S.loff[1];
+  const uint32_t l1 = sm.loff[1];
   auto ydig = [sy, l1](uint32_t, uint32_t pos) { return (pos >= l1 ? 2u : 0u) + (isfinite(sy[pos]) ? 0u : 1u); };
-  radix_pass<kFwdThreads, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
-                                [](uint32_t k, uint32_t) { return k & 255u; }, S.u2.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
-                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.u2.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
-                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.u2.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
-                                [](uint32_t k, uint32_t) { return k >> 24; }, S.u2.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01, ydig, S.u2.cnt, S.tmp);
+  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
+                       [](uint32_t k, uint32_t) { return k & 255u; }, sm.u2.cnt, sm.tmp);
+  radix_pass<NT, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
+                       [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, sm.u2.cnt, sm.tmp);
+  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
+                       [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, sm.u2.cnt, sm.tmp);
+  radix_pass<NT, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
+                       [](uint32_t k, uint32_t) { return k >> 24; }, sm.u2.cnt, sm.tmp);
+  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01, ydig, sm.u2.cnt, sm.tmp);
   const uint32_t* ypos = W.yvb + h0;
-  for (uint32_t q = tid; q < 5; q += kFwdThreads) S.yoff[q] = n01;
+  for (uint32_t q = tid; q < 5; q += NT) sm.yoff[q] = n01;
   __syncthreads();
-  for (uint32_t i = tid; i < n01; i += kFwdThreads) {
+  for (uint32_t i = tid; i < n01; i += NT) {
     const uint32_t g = ydig(0u, ypos[i]), gp = i ? ydig(0u, ypos[i - 1]) + 1u : 0u;
-    for (uint32_t q = gp; q <= g; ++q) S.yoff[q] = i;
+    for (uint32_t q = gp; q <= g; ++q) sm.yoff[q] = i;
   }
   __syncthreads();
   // bucket tables: x of every layer over its span, y of layers 0 and 1 over theirs
-  constexpr uint32_t NB = fwd_nb(SM);
+  constexpr uint32_t NB = S::NB;
   const float zmag = F.g.z_mag;
   if (tid < kFwdL) {
-    const uint32_t lo = S.loff[tid], hi = S.loff[tid + 1];
-    fwd_bucket_scale<SM>(S, tid, hi > lo, hi > lo ? sx[lo] : 0.0f, hi > lo ? sx[hi - 1] : 0.0f);
+    const uint32_t lo = sm.loff[tid], hi = sm.loff[tid + 1];
+    fwd_bucket_scale(sm, tid, hi > lo, hi > lo ? sx[lo] : 0.0f, hi > lo ? sx[hi - 1] : 0.0f);
     const float z = F.g.z_layers[tid];
-    S.dzm[tid] = fs(z, zmag);
-    S.dz0[tid] = fs(z, F.g.z_layers[0]);
+    sm.dzm[tid] = fs(z, zmag);
+    sm.dz0[tid] = fs(z, F.g.z_layers[0]);
   } else if (tid >= 32 && tid < 34) {
-    const uint32_t r = tid - 32, lo = S.yoff[2 * r], hi = S.yoff[2 * r + 1];
-    fwd_bucket_scale<SM>(S, kFwdL + r, hi > lo, hi > lo ? sy[ypos[lo]] : 0.0f, hi > lo ? sy[ypos[hi - 1]] : 0.0f);
+    const uint32_t r = tid - 32, lo = sm.yoff[2 * r], hi = sm.yoff[2 * r + 1];
+    fwd_bucket_scale(sm, kFwdL + r, hi > lo, hi > lo ? sy[ypos[lo]] : 0.0f, hi > lo ? sy[ypos[hi - 1]] : 0.0f);
   } else if (tid == 64) {
-    S.zm0 = fs(zmag, F.g.z_layers[0]);
-    S.reach = fmaxf(fabsf(S.zm0), fs(F.g.z_layers[kFwdL - 1], F.g.z_layers[0]));
+    sm.zm0 = fs(zmag, F.g.z_layers[0]);
+    sm.reach = fmaxf(fabsf(sm.zm0), fs(F.g.z_layers[kFwdL - 1], F.g.z_layers[0]));
   } else if (tid >= 96 && tid < 98) {
-    S.wx[tid - 96] = fa(fm(fd(F.g.kappa, F.p.p_min), fs(F.g.z_layers[tid - 96], zmag)), F.p.tol_x);
+    sm.wx[tid - 96] = fa(fm(fd(F.g.kappa, F.p.p_min), fs(F.g.z_layers[tid - 96], zmag)), F.p.tol_x);
   }
-  for (uint32_t i = tid; i < kFwdRows * (NB + 1); i += kFwdThreads) {
+  for (uint32_t i = tid; i < kFwdRows * (NB + 1); i += NT) {
     const uint32_t q = i / (NB + 1);  // entries past a row's last value: the row's end
-    tab_set<SM>(S, q, i % (NB + 1), q < kFwdL ? S.loff[q + 1] : S.yoff[2 * (q - kFwdL) + 1]);
+    tab_set(sm, q, i % (NB + 1), q < kFwdL ? sm.loff[q + 1] : sm.yoff[2 * (q - kFwdL) + 1]);
   }
   __syncthreads();
-  for (uint32_t pos = tid; pos < S.loff[kFwdL]; pos += kFwdThreads) {
+  for (uint32_t pos = tid; pos < sm.loff[kFwdL]; pos += NT) {
     uint32_t L = 0;
-    while (S.loff[L + 1] <= pos) ++L;
-    const uint32_t b = fwd_bucket<SM>(sx[pos], S.vmin[L], S.vinv[L]);
-    const uint32_t bp = pos > S.loff[L] ? fwd_bucket<SM>(sx[pos - 1], S.vmin[L], S.vinv[L]) + 1u : 0u;
-    for (uint32_t q = bp; q <= b; ++q) tab_set<SM>(S, L, q, pos);
+    while (sm.loff[L + 1] <= pos) ++L;
+    const uint32_t b = fwd_bucket<S>(sx[pos], sm.vmin[L], sm.vinv[L]);
+    const uint32_t bp = pos > sm.loff[L] ? fwd_bucket<S>(sx[pos - 1], sm.vmin[L], sm.vinv[L]) + 1u : 0u;
+    for (uint32_t q = bp; q <= b; ++q) tab_set(sm, L, q, pos);
   }
   for (uint32_t r = 0; r < 2; ++r)
-    for (uint32_t i = S.yoff[2 * r] + tid; i < S.yoff[2 * r + 1]; i += kFwdThreads) {
+    for (uint32_t i = sm.yoff[2 * r] + tid; i < sm.yoff[2 * r + 1]; i += NT) {
       const uint32_t q = kFwdL + r;
-      const uint32_t b = fwd_bucket<SM>(sy[ypos[i]], S.vmin[q], S.vinv[q]);
-      const uint32_t bp = i > S.yoff[2 * r] ? fwd_bucket<SM>(sy[ypos[i - 1]], S.vmin[q], S.vinv[q]) + 1u : 0u;
-      for (uint32_t b2 = bp; b2 <= b; ++b2) tab_set<SM>(S, q, b2, i);
+      const uint32_t b = fwd_bucket<S>(sy[ypos[i]], sm.vmin[q], sm.vinv[q]);
+      const uint32_t bp = i > sm.yoff[2 * r] ? fwd_bucket<S>(sy[ypos[i - 1]], sm.vmin[q], sm.vinv[q]) + 1u : 0u;
+      for (uint32_t b2 = bp; b2 <= b; ++b2) tab_set(sm, q, b2, i);
     }
   __syncthreads();
-  const FwdEvent<SM> V{sx, sy, sid, &S};
-  // 2.-3. the tracks, kFwdThreads at a time
-  for (uint64_t tc = t0; tc < t1; tc += kFwdThreads) {
+  const FwdEvent<S> V{sx, sy, sid, &sm};
+  // 2.-3. the tracks, NT at a time
+  for (uint64_t tc = t0; tc < t1; tc += NT) {
     const uint64_t t = tc + tid;
     uint32_t cnt = 0;
     bool live = false;
@@ -487,76 +535,76 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, FwdSmem& S, uint64_t e, 
         const float tx = fd(fs(x0, F.t.cluster_x[hb]), dzab), ty = fd(fs(y0, F.t.cluster_y[hb]), dzab);
         const float dzm = fs(zmag, z0);
         const float xm = fa(x0, fm(tx, dzm)), ym = fa(y0, fm(ty, dzm));
-        S.u2.c.trk[tid] = make_float4(xm, ym, tx, ty);
+        sm.u2.c.trk[tid] = make_float4(xm, ym, tx, ty);
         live = true;
         // 2. ranges of the y order holding the candidate windows of layers 0 and 1
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           float lo_y, hi_y;
-          fwd_range(fa(ym, fm(ty, S.dzm[r])), F.p.win_y, &lo_y, &hi_y);
-          const uint32_t lo = tab_first<SM>(S, kFwdL + r, lo_y);
-          const uint32_t hi = tab_past<SM>(S, kFwdL + r, hi_y);
-          S.u2.c.rlo[tid][r] = lo;
+          fwd_range(fa(ym, fm(ty, sm.dzm[r])), F.p.win_y, &lo_y, &hi_y);
+          const uint32_t lo = tab_first(sm, kFwdL + r, lo_y);
+          const uint32_t hi = tab_past(sm, kFwdL + r, hi_y);
+          sm.u2.c.rlo[tid][r] = lo;
           const uint32_t len = hi > lo ? hi - lo : 0u;
-          if (r == 0) S.u2.c.rn0[tid] = len;
+          if (r == 0) sm.u2.c.rn0[tid] = len;
           cnt += len;
         }
       } else {
         fwd_write_none(F, t);
       }
     }
-    S.u2.c.best[tid] = ~0ull;
+    sm.u2.c.best[tid] = ~0ull;
     uint32_t total;
-    const uint32_t first = block_exclusive_scan<kFwdThreads, uint32_t>(cnt, &total, S.tmp);
-    S.u2.c.poff[tid] = first;
-    if (tid == 0) S.u2.c.poff[kFwdThreads] = total;
+    const uint32_t first = block_exclusive_scan<NT, uint32_t>(cnt, &total, sm.tmp);
+    sm.u2.c.poff[tid] = first;
+    if (tid == 0) sm.u2.c.poff[NT] = total;
     __syncthreads();
-    // the (track, candidate) pairs, shared out evenly, kFwdSurv at a time:
-    // the window test, the first station and the bound, the survivors listed;
+    // the (track, candidate) pairs, shared out evenly, S::SURV at a time: the
+    // window test, the first station and the bound, the survivors listed;
     // then the survivors' far stations, fits and cuts
-    for (uint32_t q0 = 0; q0 < total; q0 += kFwdSurv) {
-      if (tid == 0) S.nsv = 0;
+    for (uint32_t q0 = 0; q0 < total; q0 += S::SURV) {
+      if (tid == 0) sm.nsv = 0;
       __syncthreads();
-      for (uint32_t q = q0 + tid; q < min(total, q0 + kFwdSurv); q += kFwdThreads) {
-        uint32_t lo = 0, hi = kFwdThreads;  // the track j with poff[j] <= q < poff[j + 1]
+      for (uint32_t q = q0 + tid; q < min(total, q0 + S::SURV); q += NT) {
+        uint32_t lo = 0, hi = NT;  // the track j with poff[j] <= q < poff[j + 1]
         while (hi - lo > 1) {
           const uint32_t mid = (lo + hi) >> 1;
-          if (S.u2.c.poff[mid] <= q) lo = mid;
+          if (sm.u2.c.poff[mid] <= q) lo = mid;
           else hi = mid;
         }
-        const uint32_t j = lo, k = q - S.u2.c.poff[j];
-        const int r = k < S.u2.c.rn0[j] ? 0 : 1;
-        const uint32_t pc = ypos[S.u2.c.rlo[j][r] + (r ? k - S.u2.c.rn0[j] : k)];
-        const float4 tr = S.u2.c.trk[j];
-        if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, S.dzm[r])))) <= S.wx[r]) ||
-            !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, S.dzm[r])))) <= F.p.win_y))
+        const uint32_t j = lo, k = q - sm.u2.c.poff[j];
+        const int r = k < sm.u2.c.rn0[j] ? 0 : 1;
+        const uint32_t pc = ypos[sm.u2.c.rlo[j][r] + (r ? k - sm.u2.c.rn0[j] : k)];
+        const float4 tr = sm.u2.c.trk[j];
+        if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, sm.dzm[r])))) <= sm.wx[r]) ||
+            !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, sm.dzm[r])))) <= F.p.win_y))
           continue;
-        if (!fwd_first_station<SM>(V, F, tr.x, tr.y, tr.w, r, pc)) continue;
-        const uint32_t slot = atomicAdd(&S.nsv, 1u);
-        S.sv_pc[slot] = pc;
-        S.sv_j[slot] = (uint8_t)j;
+        if (!fwd_first_station(V, F, tr.x, tr.y, tr.w, r, pc)) continue;
+        const uint32_t slot = atomicAdd(&sm.nsv, 1u);
+        sm.sv_pc[slot] = pc;
+        sm.sv_j[slot] = (typename S::JT)j;
       }
       __syncthreads();
-      const uint32_t nsv = S.nsv;
-      for (uint32_t i = tid; i < nsv; i += kFwdThreads) {
-        const uint32_t pc = S.sv_pc[i], j = S.sv_j[i];
-        const float4 tr = S.u2.c.trk[j];
+      const uint32_t nsv = sm.nsv;
+      for (uint32_t i = tid; i < nsv; i += NT) {
+        const uint32_t pc = sm.sv_pc[i], j = sm.sv_j[i];
+        const float4 tr = sm.u2.c.trk[j];
         FwdCand C;
-        if (fwd_candidate<SM>(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C))
-          atomicMin(&S.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
+        if (fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < sm.loff[1] ? 0 : 1, pc, C))
+          atomicMin(&sm.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
       }
       __syncthreads();
     }
     // 3. the winner of every track, recomputed and written
     if (live) {
-      const unsigned long long key = S.u2.c.best[tid];
+      const unsigned long long key = sm.u2.c.best[tid];
       if (key == ~0ull) {
         fwd_write_none(F, t);
       } else {
         const uint32_t pc = pos_of[(uint32_t)(key & ((1ull << kFwdIdBits) - 1ull))];
-        const float4 tr = S.u2.c.trk[tid];
+        const float4 tr = sm.u2.c.trk[tid];
         FwdCand C;
-        fwd_candidate<SM>(V, F, tr.x, tr.y, tr.w, pc < S.loff[1] ? 0 : 1, pc, C);
+        fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < sm.loff[1] ? 0 : 1, pc, C);
         F.o.n_found[t] = C.n;
 #pragma unroll
         for (int L = 0; L < (int)kFwdL; ++L) F.o.hits[t * kFwdL + L] = C.hl[L] != kNone ? sid[C.hl[L]] : kNone;
@@ -573,47 +621,40 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, FwdSmem& S, uint64_t e, 
   }
 }
 
-// One CTA per event; the instance with SM = true takes the events whose hits
-// fit in shared memory, the other the rest (a CTA of the wrong instance
-// returns at once).
-template <bool SM>
-__global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) k_forward(Fwd F) {
+// One 256-thread CTA per event; events of more than kFwdSmallHits hits are
+// left to k_forward_list (so are all when the result or the offsets are
+// rejected, except for writing the empty answers).
+__global__ void __launch_bounds__(256, 4) k_forward_small(Fwd F) {
   extern __shared__ __align__(16) uint8_t fwd_smem_raw[];
-  FwdSmem& S = *reinterpret_cast<FwdSmem*>(fwd_smem_raw);
+  FwdSmall& sm = *reinterpret_cast<FwdSmall*>(fwd_smem_raw);
   const uint64_t e = blockIdx.x;
-  const uint32_t tid = threadIdx.x;
   const uint32_t flag = *(const volatile uint32_t*)F.w.flag;
   if (flag & kFwdNoTracks) return;  // no track lists to read: nothing is written
-  const uint64_t t0 = F.t.track_offsets[e], t1 = F.t.track_offsets[e + 1];
   if (flag & kFwdBadOffsets) {      // hits rejected: no track has a downstream track
-    if (SM)
-      for (uint64_t t = t0 + tid; t < t1 && t < F.o.cap_tracks; t += kFwdThreads) fwd_write_none(F, t);
+    const uint64_t t0 = F.t.track_offsets[e], t1 = F.t.track_offsets[e + 1];
+    for (uint64_t t = t0 + threadIdx.x; t < t1 && t < F.o.cap_tracks; t += 256) fwd_write_none(F, t);
     return;
   }
-  const uint64_t h0 = F.h.event_offsets[e];
-  const uint32_t n = (uint32_t)(F.h.event_offsets[e + 1] - h0);
-  if ((n <= kFwdSmemHits) != SM) return;
-  const FwdWork& W = F.w;
-  // 1. sort by (layer, x): four passes over the ordered bits of x, one over the layer
-  for (uint32_t i = tid; i < n; i += kFwdThreads) {
-    W.ka[h0 + i] = ordered_bits(F.h.x[h0 + i]);
-    W.va[h0 + i] = i;
+  if (F.h.event_offsets[e + 1] - F.h.event_offsets[e] > kFwdSmallHits) return;
+  fwd_event<256>(F, sm, e);
+}
+
+// 1024-thread CTAs over the list of events above kFwdSmallHits hits (HUGE =
+// false: up to kFwdBigHits, hits in shared memory) or above kFwdBigHits
+// (HUGE = true: hits in the workspace); the lists are empty when the
+// offsets or the result are rejected.
+template <bool HUGE>
+__global__ void __launch_bounds__(1024, 1) k_forward_list(Fwd F) {
+  using S = typename std::conditional<HUGE, FwdHuge, FwdBig>::type;
+  extern __shared__ __align__(16) uint8_t fwd_smem_raw[];
+  S& sm = *reinterpret_cast<S*>(fwd_smem_raw);
+  if (*(const volatile uint32_t*)F.w.flag & kFwdNoTracks) return;
+  const uint32_t count = F.w.nlist[HUGE ? 1 : 0];
+  const uint32_t* list = HUGE ? F.w.list_huge : F.w.list_big;
+  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    fwd_event<1024>(F, sm, list[i]);
+    __syncthreads();
   }
-  __syncthreads();
-  const uint32_t* lay = F.h.layer + h0;
-  const float* xin = F.h.x + h0;
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [](uint32_t k, uint32_t) { return k & 255u; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                                [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                                [](uint32_t k, uint32_t) { return k >> 24; }, S.u.cnt, S.tmp);
-  radix_pass<kFwdThreads, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                                [lay, xin](uint32_t, uint32_t id) { return fwd_layer_of(lay, xin, id); }, S.u.cnt,
-                                S.tmp);
-  fwd_event<SM>(F, S, e, t0, t1, h0, n);
 }
 
 }  // namespace
@@ -663,6 +704,19 @@ float fwd_lambda(const velo_downstream_t& g, uint32_t min_hits) {
   return last;
 }
 
+int fwd_sm_count() {
+  static std::mutex mu;
+  static int cached[64] = {};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cached[d] && cudaDeviceGetAttribute(&cached[d], cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+    cudaGetLastError();
+    cached[d] = 148;
+  }
+  return cached[d];
+}
+
 }  // namespace
 
 extern "C" {
@@ -683,9 +737,8 @@ int velo_forward_params_default(velo_forward_params_t* p) {
 
 int velo_forward_workspace_size(uint64_t n_events, uint64_t n_hits, uint64_t* bytes) {
   if (!bytes) return VELO_EINVAL;
-  (void)n_events;
   FwdWork w;
-  *bytes = fwd_carve(nullptr, n_hits, &w);
+  *bytes = fwd_carve(nullptr, n_events, n_hits, &w);
   return VELO_OK;
 }
 
@@ -720,15 +773,20 @@ int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks
   F.g = *geometry;
   F.p = *params;
   F.o = *out;
-  if (fwd_carve(static_cast<uint8_t*>(workspace), hits->n_hits, &F.w) > workspace_bytes) return VELO_ECAPACITY;
+  if (fwd_carve(static_cast<uint8_t*>(workspace), hits->n_events, hits->n_hits, &F.w) > workspace_bytes)
+    return VELO_ECAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!set_max_smem_once(reinterpret_cast<const void*>(k_forward<true>), 2) ||
-      !set_max_smem_once(reinterpret_cast<const void*>(k_forward<false>), 3))
+  if (!set_max_smem_once(reinterpret_cast<const void*>(k_forward_small), 2) ||
+      !set_max_smem_once(reinterpret_cast<const void*>(k_forward_list<false>), 3) ||
+      !set_max_smem_once(reinterpret_cast<const void*>(k_forward_list<true>), 4))
     return VELO_ECUDA;
   k_fwd_validate<<<1, 1024, 0, s>>>(F);
   if (hits->n_events) {
-    k_forward<true><<<(uint32_t)hits->n_events, kFwdThreads, sizeof(FwdSmem), s>>>(F);
-    k_forward<false><<<(uint32_t)hits->n_events, kFwdThreads, sizeof(FwdSmem), s>>>(F);
+    // the large events first (one 1024-thread CTA per SM), then the rest
+    const uint32_t ctas = (uint32_t)std::min<uint64_t>(fwd_sm_count(), hits->n_events);
+    if (hits->n_hits > kFwdSmallHits) k_forward_list<false><<<ctas, 1024, sizeof(FwdBig), s>>>(F);
+    if (hits->n_hits > kFwdBigHits) k_forward_list<true><<<ctas, 1024, sizeof(FwdHuge), s>>>(F);
+    k_forward_small<<<(uint32_t)hits->n_events, 256, sizeof(FwdSmall), s>>>(F);
   }
   return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;
 }
