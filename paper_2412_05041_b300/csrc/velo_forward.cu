@@ -306,25 +306,37 @@ struct FwdCand {
   uint32_t hl[kFwdL];  // sorted positions, kNone = no hit
 };
 
-// steps 3-5 for the candidate at sorted position pc of layer r of a track
-// whose line reaches the kick plane at (xm, ym) with slope ty: false when a
-// cut drops it
+// Step 3's first station for the candidate at sorted position pc of layer r
+// of a track whose line reaches the kick plane at (xm, ym) with slope ty:
+// its hits hl[0..3] and the line (a1, b1) through them; false with fewer
+// than two
 template <class S>
-__device__ __forceinline__ bool fwd_candidate(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty, int r,
-                                              uint32_t pc, FwdCand& C) {
+__device__ __forceinline__ bool fwd_station1(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty, int r,
+                                             uint32_t pc, uint32_t* hl, float* a1, float* b1) {
   const velo_forward_params_t& P = F.p;
   const S& sm = *V.sm;
   const float tk = fd(fs(V.sx[pc], xm), sm.dzm[r]);
   uint32_t n1 = 0;
 #pragma unroll
   for (int L = 0; L < 4; ++L) {
-    C.hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, sm.dzm[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x, P.tol_y);
-    n1 += C.hl[L] != kNone ? 1u : 0u;
+    hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, sm.dzm[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x, P.tol_y);
+    n1 += hl[L] != kNone ? 1u : 0u;
   }
   if (n1 < 2) return false;
-  float a1, b1;
-  fwd_line(C.hl, V.sx, sm.dz0, 0, 4, &a1, &b1);
-  uint32_t n = n1;
+  fwd_line(hl, V.sx, sm.dz0, 0, 4, a1, b1);
+  return true;
+}
+
+// steps 3 (the other stations) to 5 given the first station's hits C.hl[0..3]
+// and line (a1, b1): false when a cut drops the candidate
+template <class S>
+__device__ __forceinline__ bool fwd_far(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty, float a1,
+                                        float b1, FwdCand& C) {
+  const velo_forward_params_t& P = F.p;
+  const S& sm = *V.sm;
+  uint32_t n = 0;
+#pragma unroll
+  for (int L = 0; L < 4; ++L) n += C.hl[L] != kNone ? 1u : 0u;
 #pragma unroll
   for (int L = 4; L < (int)kFwdL; ++L) {
     C.hl[L] = fwd_nearest(V, L, fa(a1, fm(b1, sm.dz0[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x_far, P.tol_y);
@@ -358,41 +370,38 @@ __device__ __forceinline__ bool fwd_candidate(const FwdEvent<S>& V, const Fwd& F
   return true;
 }
 
-// Step 3's first station for the candidate at sorted position pc of layer r,
-// and a necessary condition for passing the match cut: false when the
-// candidate certainly fails a cut.  The final x line is the least-squares
-// line of the first-station hits and the far hits; written as the
-// first-station line L1 (a1, b1) plus the least-squares line of the hits'
-// offsets e_i from L1, its distance at the kick plane is d1 + sum w_i e_i,
-// with d1 that of L1, w_i the fit's weights at the kick plane and |e_i| at
-// most E = max(first-station residuals, tol_x_far).  So |d| <= tol_match
-// needs |d1| <= tol_match + lam E, lam the largest sum |w_i| over the hit
-// sets a candidate can end with (host arithmetic); the allowance
-// 1 mm + 2e-3 M (M the size of the coordinates involved) covers the binary32
-// rounding of both lines, its worst case being some 1e-4 M.
+// steps 3-5 for the candidate at sorted position pc of layer r: false when a
+// cut drops it
 template <class S>
-__device__ __forceinline__ bool fwd_first_station(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty,
-                                                  int r, uint32_t pc) {
-  const velo_forward_params_t& P = F.p;
-  const S& sm = *V.sm;
-  const float tk = fd(fs(V.sx[pc], xm), sm.dzm[r]);
-  uint32_t hl[4];
-  uint32_t n1 = 0;
-#pragma unroll
-  for (int L = 0; L < 4; ++L) {
-    hl[L] = fwd_nearest(V, L, fa(xm, fm(tk, sm.dzm[L])), fa(ym, fm(ty, sm.dzm[L])), P.tol_x, P.tol_y);
-    n1 += hl[L] != kNone ? 1u : 0u;
-  }
-  if (n1 < 2) return false;
+__device__ __forceinline__ bool fwd_candidate(const FwdEvent<S>& V, const Fwd& F, float xm, float ym, float ty, int r,
+                                              uint32_t pc, FwdCand& C) {
   float a1, b1;
-  fwd_line(hl, V.sx, sm.dz0, 0, 4, &a1, &b1);
-  float E = P.tol_x_far;
+  if (!fwd_station1(V, F, xm, ym, ty, r, pc, C.hl, &a1, &b1)) return false;
+  return fwd_far(V, F, xm, ym, ty, a1, b1, C);
+}
+
+// A necessary condition for the candidate with first-station hits hl[0..3]
+// and line L1 = (a1, b1) to pass the match cut.  The final x line is the
+// least-squares line of the first-station hits and the far hits; written as
+// L1 plus the least-squares line of the hits' offsets e_i from L1, its
+// distance at the kick plane is d1 + sum w_i e_i, with d1 that of L1, w_i the
+// fit's weights at the kick plane and |e_i| at most E = max(first-station
+// residuals, tol_x_far).  So |d| <= tol_match needs |d1| <= tol_match + lam E,
+// lam the largest sum |w_i| over the hit sets a candidate can end with (host
+// arithmetic); the allowance 1 mm + 2e-3 M (M the size of the coordinates
+// involved) covers the binary32 rounding of both lines, its worst case being
+// some 1e-4 M.
+template <class S>
+__device__ __forceinline__ bool fwd_may_match(const FwdEvent<S>& V, const Fwd& F, float xm, const uint32_t* hl,
+                                              float a1, float b1) {
+  const S& sm = *V.sm;
+  float E = F.p.tol_x_far;
 #pragma unroll
   for (int L = 0; L < 4; ++L)
     if (hl[L] != kNone) E = fmaxf(E, fabsf(fs(V.sx[hl[L]], fa(a1, fm(b1, sm.dz0[L])))));
   const float M = fa(fa(fa(fabsf(a1), fm(fabsf(b1), sm.reach)), fabsf(xm)), E);
   const float d1 = fs(fa(a1, fm(b1, sm.zm0)), xm);
-  return fabsf(d1) <= fa(fa(P.tol_match, fm(F.lam, E)), fa(1.0f, fm(2e-3f, M)));
+  return fabsf(d1) <= fa(fa(F.p.tol_match, fm(F.lam, E)), fa(1.0f, fm(2e-3f, M)));
 }
 
 // rank key: more hits, then the smaller distance (non-negative binary32
@@ -559,13 +568,20 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
     sm.u2.c.poff[tid] = first;
     if (tid == 0) sm.u2.c.poff[NT] = total;
     __syncthreads();
-    // the (track, candidate) pairs, shared out evenly, S::SURV at a time: the
-    // window test, the first station and the bound, the survivors listed;
-    // then the survivors' far stations, fits and cuts
-    for (uint32_t q0 = 0; q0 < total; q0 += S::SURV) {
+    // the (track, candidate) pairs, shared out evenly, R at a time: the
+    // window test, the first station and the bound, the survivors listed
+    // (with their first stations, in the sort keys' workspace, dead by now,
+    // when positions fit in 16 bits: R <= n); then the survivors' far
+    // stations, fits and cuts
+    const uint32_t R = S::SM ? max(1u, min(S::SURV, n)) : S::SURV;
+    uint32_t* sv_h01 = W.ka + h0;  // first-station positions, 16 bits each (0xFFFF: none)
+    uint32_t* sv_h23 = W.kb + h0;
+    uint32_t* sv_a1 = W.yka + h0;  // and line
+    uint32_t* sv_b1 = W.ykb + h0;
+    for (uint32_t q0 = 0; q0 < total; q0 += R) {
       if (tid == 0) sm.nsv = 0;
       __syncthreads();
-      for (uint32_t q = q0 + tid; q < min(total, q0 + S::SURV); q += NT) {
+      for (uint32_t q = q0 + tid; q < min(total, q0 + R); q += NT) {
         uint32_t lo = 0, hi = NT;  // the track j with poff[j] <= q < poff[j + 1]
         while (hi - lo > 1) {
           const uint32_t mid = (lo + hi) >> 1;
@@ -579,10 +595,19 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
         if (!(fabsf(fs(sx[pc], fa(tr.x, fm(tr.z, sm.dzm[r])))) <= sm.wx[r]) ||
             !(fabsf(fs(sy[pc], fa(tr.y, fm(tr.w, sm.dzm[r])))) <= F.p.win_y))
           continue;
-        if (!fwd_first_station(V, F, tr.x, tr.y, tr.w, r, pc)) continue;
+        uint32_t hl[4];
+        float a1, b1;
+        if (!fwd_station1(V, F, tr.x, tr.y, tr.w, r, pc, hl, &a1, &b1)) continue;
+        if (!fwd_may_match(V, F, tr.x, hl, a1, b1)) continue;
         const uint32_t slot = atomicAdd(&sm.nsv, 1u);
         sm.sv_pc[slot] = pc;
         sm.sv_j[slot] = (typename S::JT)j;
+        if constexpr (S::SM) {
+          sv_h01[slot] = (hl[0] & 0xFFFFu) | hl[1] << 16;
+          sv_h23[slot] = (hl[2] & 0xFFFFu) | hl[3] << 16;
+          sv_a1[slot] = __float_as_uint(a1);
+          sv_b1[slot] = __float_as_uint(b1);
+        }
       }
       __syncthreads();
       const uint32_t nsv = sm.nsv;
@@ -590,8 +615,17 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
         const uint32_t pc = sm.sv_pc[i], j = sm.sv_j[i];
         const float4 tr = sm.u2.c.trk[j];
         FwdCand C;
-        if (fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < sm.loff[1] ? 0 : 1, pc, C))
-          atomicMin(&sm.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
+        bool ok;
+        if constexpr (S::SM) {
+          const uint32_t p01 = sv_h01[i], p23 = sv_h23[i];
+          const uint32_t p[4] = {p01 & 0xFFFFu, p01 >> 16, p23 & 0xFFFFu, p23 >> 16};
+#pragma unroll
+          for (int L = 0; L < 4; ++L) C.hl[L] = p[L] == 0xFFFFu ? kNone : p[L];
+          ok = fwd_far(V, F, tr.x, tr.y, tr.w, __uint_as_float(sv_a1[i]), __uint_as_float(sv_b1[i]), C);
+        } else {
+          ok = fwd_candidate(V, F, tr.x, tr.y, tr.w, pc < sm.loff[1] ? 0 : 1, pc, C);
+        }
+        if (ok) atomicMin(&sm.u2.c.best[j], fwd_key(C.n, C.ad, sid[pc]));
       }
       __syncthreads();
     }
