@@ -4,12 +4,13 @@
 // The first stage traces pixel-tracker tracks forwards, straight to the
 // middle of the magnet, one change of angle there, straight to the fibre
 // tracker (Sec. "HLT1 details and results").  One CTA per event:
-//   1. the event's downstream hits are sorted by (layer, x) -- four stable
-//      radix passes over the order-preserving bits of x, one over the layer
-//      -- and gathered into sorted x, y arrays (shared memory when the event
-//      fits, else its slice of the workspace), with per-layer offsets and a
-//      bucket index per layer (first position of each of its x buckets),
-//      layers 0 and 1 also in y order with a bucket index over y;
+//   1. the span of x in every layer (and of y in layers 0 and 1) cut into
+//      equal buckets; the event's downstream hits sorted by (layer, x bucket)
+//      -- two stable counting passes -- and gathered into x, y arrays
+//      (shared memory when the event fits, else its slice of the workspace)
+//      with per-layer offsets and the first position of every bucket, then
+//      by x inside every bucket (so by x in every layer); layers 0 and 1 also
+//      by (layer, y bucket);
 //   2. the tracks of the event, up to one per thread at a time: one thread
 //      per track finds its line and the ranges of its candidate windows in
 //      layers 0 and 1; a scan flattens the (track, candidate) pairs and the
@@ -107,6 +108,10 @@ __device__ __forceinline__ uint32_t ordered_bits(float v) {  // monotone in v
   return u ^ ((u >> 31) ? 0xFFFFFFFFu : 0x80000000u);
 }
 
+__device__ __forceinline__ float from_ordered_bits(uint32_t o) {
+  return __uint_as_float(o ^ ((o >> 31) ? 0x80000000u : 0xFFFFFFFFu));
+}
+
 
 // flag bits: the hit offsets are invalid / the pixel-tracker result did not
 // fit its buffers (its track lists were not written)
@@ -177,17 +182,14 @@ struct FwdSmem {
     } c;
   } u2;
   // row q < kFwdL: first position of each x bucket of layer q (+ the layer's
-  // end); rows kFwdL + r: first entry of each y bucket of layer r in the y order
+  // end); rows kFwdL + r: first entry of each y bucket of layer r in the
+  // (layer, y bucket) order of layers 0 and 1
   union {
     uint16_t s[kFwdRows][256 + 1];
     uint32_t g[kFwdRows][128 + 1];
   } tab;
   float vmin[kFwdRows], vinv[kFwdRows];  // bucket of v in row q: (v - vmin) * vinv, clamped
   uint32_t loff[kFwdL + 1];  // first position of each layer; [kFwdL] = end of the searched layers
-  // layers 0 and 1 by y (candidate search): ypos holds (layer, x)-sorted
-  // positions in (layer, finite y, y) order; yoff[2 r] .. yoff[2 r + 1] are
-  // layer r's hits with a finite y
-  uint32_t yoff[5];
   float dzm[kFwdL], dz0[kFwdL];  // z_L - z_mag, z_L - z_0
   float zm0, reach;              // z_mag - z_0; max(|z_mag - z_0|, z_11 - z_0)
   float wx[2];                   // candidate half-widths in x, layers 0 and 1
@@ -264,7 +266,7 @@ __device__ __forceinline__ uint32_t fwd_nearest(const FwdEvent<S>& V, int L, flo
   float lo_x, hi_x;
   fwd_range(xp, tol, &lo_x, &hi_x);
   const uint32_t end = V.sm->loff[L + 1];
-  uint32_t pos = tab_first(*V.sm, L, lo_x);
+  uint32_t pos = tab_first(*V.sm, L, lo_x);  // every hit with x >= lo_x lies at or after it
   while (pos < end && V.sx[pos] < lo_x) ++pos;
   uint32_t best = kNone;
   float bd = 0.0f;
@@ -428,104 +430,142 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
   const uint32_t* lay = F.h.layer + h0;
   const float* xin = F.h.x + h0;
   const float* yin = F.h.y + h0;
-  // 1. sort by (layer, x): four passes over the ordered bits of x, one over the layer
-  for (uint32_t i = tid; i < n; i += NT) {
-    W.ka[h0 + i] = ordered_bits(xin[i]);
-    W.va[h0 + i] = i;
-  }
-  __syncthreads();
-  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n, [](uint32_t k, uint32_t) { return k & 255u; },
-                       sm.u.cnt, sm.tmp);
-  radix_pass<NT, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n,
-                       [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, sm.u.cnt, sm.tmp);
-  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                       [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, sm.u.cnt, sm.tmp);
-  radix_pass<NT, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n, [](uint32_t k, uint32_t) { return k >> 24; },
-                       sm.u.cnt, sm.tmp);
-  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n,
-                       [lay, xin](uint32_t, uint32_t id) { return fwd_layer_of(lay, xin, id); }, sm.u.cnt, sm.tmp);
-  // sorted x, y, the sorted position of every id (into va, free after the
-  // sort), the first position of every layer (a layer's slots after its
-  // predecessor's layer get the position)
-  float* sx = S::SM ? sm.u.xy : W.sx + h0;
-  float* sy = S::SM ? sm.u.xy + n : W.sy + h0;
-  const uint32_t* sid = W.vb + h0;
-  uint32_t* pos_of = W.va + h0;
-  for (uint32_t q = tid; q <= kFwdL; q += NT) sm.loff[q] = n;
-  __syncthreads();
-  for (uint32_t pos = tid; pos < n; pos += NT) {
-    const uint32_t id = sid[pos];
-    sx[pos] = xin[id];
-    sy[pos] = yin[id];
-    pos_of[id] = pos;
-    const uint32_t L = fwd_layer_of(lay, xin, id), Lp = pos ? fwd_layer_of(lay, xin, sid[pos - 1]) + 1u : 0u;
-    for (uint32_t q = Lp; q <= L; ++q) sm.loff[q] = pos;
-  }
-  __syncthreads();
-  // layers 0 and 1 sorted by y: four passes over the ordered bits of y, one
-  // over (layer, y not finite)
-  const uint32_t n01 = sm.loff[2];
-  for (uint32_t pos = tid; pos < n01; pos += NT) {
-    W.yka[h0 + pos] = ordered_bits(sy[pos]);
-    W.yva[h0 + pos] = pos;
-  }
-  __syncthreads();
-  const uint32_t l1 = sm.loff[1];
-  auto ydig = [sy, l1](uint32_t, uint32_t pos) { return (pos >= l1 ? 2u : 0u) + (isfinite(sy[pos]) ? 0u : 1u); };
-  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
-                       [](uint32_t k, uint32_t) { return k & 255u; }, sm.u2.cnt, sm.tmp);
-  radix_pass<NT, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
-                       [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, sm.u2.cnt, sm.tmp);
-  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
-                       [](uint32_t k, uint32_t) { return (k >> 16) & 255u; }, sm.u2.cnt, sm.tmp);
-  radix_pass<NT, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01,
-                       [](uint32_t k, uint32_t) { return k >> 24; }, sm.u2.cnt, sm.tmp);
-  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01, ydig, sm.u2.cnt, sm.tmp);
-  const uint32_t* ypos = W.yvb + h0;
-  for (uint32_t q = tid; q < 5; q += NT) sm.yoff[q] = n01;
-  __syncthreads();
-  for (uint32_t i = tid; i < n01; i += NT) {
-    const uint32_t g = ydig(0u, ypos[i]), gp = i ? ydig(0u, ypos[i - 1]) + 1u : 0u;
-    for (uint32_t q = gp; q <= g; ++q) sm.yoff[q] = i;
-  }
-  __syncthreads();
-  // bucket tables: x of every layer over its span, y of layers 0 and 1 over theirs
   constexpr uint32_t NB = S::NB;
+  constexpr uint32_t NW = NT / 32;
   const float zmag = F.g.z_mag;
-  if (tid < kFwdL) {
-    const uint32_t lo = sm.loff[tid], hi = sm.loff[tid + 1];
-    fwd_bucket_scale(sm, tid, hi > lo, hi > lo ? sx[lo] : 0.0f, hi > lo ? sx[hi - 1] : 0.0f);
-    const float z = F.g.z_layers[tid];
-    sm.dzm[tid] = fs(z, zmag);
-    sm.dz0[tid] = fs(z, F.g.z_layers[0]);
-  } else if (tid >= 32 && tid < 34) {
-    const uint32_t r = tid - 32, lo = sm.yoff[2 * r], hi = sm.yoff[2 * r + 1];
-    fwd_bucket_scale(sm, kFwdL + r, hi > lo, hi > lo ? sy[ypos[lo]] : 0.0f, hi > lo ? sy[ypos[hi - 1]] : 0.0f);
+  // 1. the span of x in every layer and of y in layers 0 and 1 (finite values
+  // of searched hits): ordered-bit minima and maxima per warp, then over the
+  // warps; the buckets of each table divide its span evenly
+  uint32_t* mm = sm.u2.cnt;  // [NW][kFwdRows][min, max]
+  for (uint32_t i = tid; i < NW * kFwdRows * 2; i += NT) mm[i] = (i & 1u) ? 0u : ~0u;
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += NT) {
+    const uint32_t L = fwd_layer_of(lay, xin, i);
+    if (L >= kFwdL) continue;
+    uint32_t* m = mm + (warp_id() * kFwdRows + L) * 2;
+    const uint32_t o = ordered_bits(xin[i]);
+    atomicMin(m, o);
+    atomicMax(m + 1, o);
+    const float y = yin[i];
+    if (L < 2 && isfinite(y)) {
+      uint32_t* my = mm + (warp_id() * kFwdRows + kFwdL + L) * 2;
+      const uint32_t oy = ordered_bits(y);
+      atomicMin(my, oy);
+      atomicMax(my + 1, oy);
+    }
+  }
+  __syncthreads();
+  if (tid < kFwdRows) {
+    uint32_t lo = ~0u, hi = 0u;
+    for (uint32_t w = 0; w < NW; ++w) {
+      lo = min(lo, mm[(w * kFwdRows + tid) * 2]);
+      hi = max(hi, mm[(w * kFwdRows + tid) * 2 + 1]);
+    }
+    const bool any = lo <= hi;
+    fwd_bucket_scale(sm, tid, any, any ? from_ordered_bits(lo) : 0.0f, any ? from_ordered_bits(hi) : 0.0f);
+  } else if (tid >= 32 && tid < 32 + kFwdL) {
+    const float z = F.g.z_layers[tid - 32];
+    sm.dzm[tid - 32] = fs(z, zmag);
+    sm.dz0[tid - 32] = fs(z, F.g.z_layers[0]);
   } else if (tid == 64) {
     sm.zm0 = fs(zmag, F.g.z_layers[0]);
     sm.reach = fmaxf(fabsf(sm.zm0), fs(F.g.z_layers[kFwdL - 1], F.g.z_layers[0]));
   } else if (tid >= 96 && tid < 98) {
     sm.wx[tid - 96] = fa(fm(fd(F.g.kappa, F.p.p_min), fs(F.g.z_layers[tid - 96], zmag)), F.p.tol_x);
   }
-  for (uint32_t i = tid; i < kFwdRows * (NB + 1); i += NT) {
-    const uint32_t q = i / (NB + 1);  // entries past a row's last value: the row's end
-    tab_set(sm, q, i % (NB + 1), q < kFwdL ? sm.loff[q + 1] : sm.yoff[2 * (q - kFwdL) + 1]);
+  __syncthreads();
+  // 2. counting sort by (layer, x bucket): a stable pass over the bucket, one
+  // over the layer (kFwdL: not searched); the order inside a bucket is the
+  // ids' (searches scan whole buckets, the exact tests decide)
+  for (uint32_t i = tid; i < n; i += NT) {
+    const uint32_t L = fwd_layer_of(lay, xin, i);
+    W.ka[h0 + i] = (L < kFwdL ? fwd_bucket<S>(xin[i], sm.vmin[L], sm.vinv[L]) : 0u) | L << 8;
+    W.va[h0 + i] = i;
+  }
+  __syncthreads();
+  radix_pass<NT, true>(W.ka + h0, W.kb + h0, W.va + h0, W.vb + h0, n, [](uint32_t k, uint32_t) { return k & 255u; },
+                       sm.u.cnt, sm.tmp);
+  radix_pass<NT, true>(W.kb + h0, W.ka + h0, W.vb + h0, W.va + h0, n, [](uint32_t k, uint32_t) { return k >> 8; },
+                       sm.u.cnt, sm.tmp);
+  // sorted x, y, the sorted position of every id (into vb, free after the
+  // sort), the first position of every layer (a layer's slots after its
+  // predecessor's layer get the position)
+  const uint32_t* skey = W.ka + h0;  // (layer, bucket) of every sorted position
+  float* sx = S::SM ? sm.u.xy : W.sx + h0;
+  float* sy = S::SM ? sm.u.xy + n : W.sy + h0;
+  uint32_t* sid = W.va + h0;
+  uint32_t* pos_of = W.vb + h0;
+  for (uint32_t q = tid; q <= kFwdL; q += NT) sm.loff[q] = n;
+  __syncthreads();
+  for (uint32_t pos = tid; pos < n; pos += NT) {
+    const uint32_t id = sid[pos];
+    sx[pos] = xin[id];
+    sy[pos] = yin[id];
+    const uint32_t L = skey[pos] >> 8, Lp = pos ? (skey[pos - 1] >> 8) + 1u : 0u;
+    for (uint32_t q = Lp; q <= L; ++q) sm.loff[q] = pos;
+  }
+  __syncthreads();
+  // the x tables from the sorted keys: entry b of a row is the first position
+  // whose bucket is b or more (the layer's end past its last hit)
+  for (uint32_t i = tid; i < kFwdL * (NB + 1); i += NT) {
+    const uint32_t q = i / (NB + 1);
+    tab_set(sm, q, i % (NB + 1), sm.loff[q + 1]);
   }
   __syncthreads();
   for (uint32_t pos = tid; pos < sm.loff[kFwdL]; pos += NT) {
-    uint32_t L = 0;
-    while (sm.loff[L + 1] <= pos) ++L;
-    const uint32_t b = fwd_bucket<S>(sx[pos], sm.vmin[L], sm.vinv[L]);
-    const uint32_t bp = pos > sm.loff[L] ? fwd_bucket<S>(sx[pos - 1], sm.vmin[L], sm.vinv[L]) + 1u : 0u;
+    const uint32_t L = skey[pos] >> 8, b = skey[pos] & 255u;
+    const uint32_t bp = pos > sm.loff[L] ? (skey[pos - 1] & 255u) + 1u : 0u;
     for (uint32_t q = bp; q <= b; ++q) tab_set(sm, L, q, pos);
   }
-  for (uint32_t r = 0; r < 2; ++r)
-    for (uint32_t i = sm.yoff[2 * r] + tid; i < sm.yoff[2 * r + 1]; i += NT) {
-      const uint32_t q = kFwdL + r;
-      const uint32_t b = fwd_bucket<S>(sy[ypos[i]], sm.vmin[q], sm.vinv[q]);
-      const uint32_t bp = i > sm.yoff[2 * r] ? fwd_bucket<S>(sy[ypos[i - 1]], sm.vmin[q], sm.vinv[q]) + 1u : 0u;
-      for (uint32_t b2 = bp; b2 <= b; ++b2) tab_set(sm, q, b2, i);
+  __syncthreads();
+  // x order inside every bucket (insertion sort: a bucket holds a few hits),
+  // so that every layer is sorted by x; then the position of every id
+  for (uint32_t q = tid; q < kFwdL * NB; q += NT) {
+    const uint32_t L = q / NB, b = q % NB;
+    const uint32_t lo = tab_get(sm, L, b), hi = tab_get(sm, L, b + 1);
+    for (uint32_t i = lo + 1; i < hi; ++i) {
+      const float xv = sx[i], yv = sy[i];
+      const uint32_t idv = sid[i];
+      uint32_t k = i;
+      for (; k > lo && sx[k - 1] > xv; --k) {
+        sx[k] = sx[k - 1];
+        sy[k] = sy[k - 1];
+        sid[k] = sid[k - 1];
+      }
+      sx[k] = xv;
+      sy[k] = yv;
+      sid[k] = idv;
     }
+  }
+  __syncthreads();
+  for (uint32_t pos = tid; pos < n; pos += NT) pos_of[sid[pos]] = pos;
+  // 3. layers 0 and 1 by (layer, y bucket), the same way: ypos holds their
+  // (layer, x)-sorted positions, layer 0's at [0, l1), layer 1's at [l1, n01)
+  const uint32_t n01 = sm.loff[2], l1 = sm.loff[1];
+  for (uint32_t pos = tid; pos < n01; pos += NT) {
+    const uint32_t r = pos >= l1 ? 1u : 0u;
+    W.yka[h0 + pos] = fwd_bucket<S>(sy[pos], sm.vmin[kFwdL + r], sm.vinv[kFwdL + r]) | r << 8;
+    W.yva[h0 + pos] = pos;
+  }
+  __syncthreads();
+  radix_pass<NT, true>(W.yka + h0, W.ykb + h0, W.yva + h0, W.yvb + h0, n01,
+                       [](uint32_t k, uint32_t) { return k & 255u; }, sm.u2.cnt, sm.tmp);
+  radix_pass<NT, true>(W.ykb + h0, W.yka + h0, W.yvb + h0, W.yva + h0, n01, [](uint32_t k, uint32_t) { return k >> 8; },
+                       sm.u2.cnt, sm.tmp);
+  const uint32_t* ypos = W.yva + h0;
+  const uint32_t* ykey = W.yka + h0;
+  // 4. the y tables the same way (the order inside a y bucket does not
+  // matter: candidate ranges are whole buckets, the exact tests decide)
+  for (uint32_t i = tid; i < 2 * (NB + 1); i += NT) {
+    const uint32_t r = i / (NB + 1);
+    tab_set(sm, kFwdL + r, i % (NB + 1), r ? n01 : l1);
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n01; i += NT) {
+    const uint32_t r = ykey[i] >> 8, b = ykey[i] & 255u;
+    const uint32_t bp = i > (r ? l1 : 0u) ? (ykey[i - 1] & 255u) + 1u : 0u;
+    for (uint32_t q = bp; q <= b; ++q) tab_set(sm, kFwdL + r, q, i);
+  }
   __syncthreads();
   const FwdEvent<S> V{sx, sy, sid, &sm};
   // 2.-3. the tracks, NT at a time
