@@ -117,7 +117,7 @@ __device__ __forceinline__ float from_ordered_bits(uint32_t o) {
 // fit its buffers (its track lists were not written)
 constexpr uint32_t kFwdBadOffsets = 1u, kFwdNoTracks = 2u;
 constexpr uint32_t kFwdIdBits = 29;        // hit ids in a rank key: events hold fewer than 2^29 hits
-constexpr uint32_t kFwdSmallHits = 4096;   // events up to this size: 256-thread CTAs, hits in shared memory
+constexpr uint32_t kFwdSmallHits = 4864;   // events up to this size: 256-thread CTAs, hits in shared memory
 constexpr uint32_t kFwdBigHits = 16384;    // up to this size: 1024-thread CTAs, hits in shared memory
 constexpr uint32_t kFwdRows = kFwdL + 2;   // bucket tables: x of every layer, y of layers 0 and 1
 
@@ -165,8 +165,6 @@ template <int NT, uint32_t HC>
 struct FwdSmem {
   static constexpr bool SM = HC > 0;
   static constexpr uint32_t NB = SM ? 256u : 128u;  // buckets per table (16-bit entries when SM)
-  static constexpr uint32_t SURV = 5u * NT;         // pairs per round (each leaves at most one survivor)
-  using JT = typename std::conditional<NT <= 256, uint8_t, uint16_t>::type;
   union {
     uint32_t cnt[radix_counters(NT)];  // radix counters of the (layer, x) sort
     float xy[2 * (SM ? HC : 1u)];      // then x, y in sorted order
@@ -195,8 +193,6 @@ struct FwdSmem {
   float wx[2];                   // candidate half-widths in x, layers 0 and 1
   uint32_t tmp[64];
   uint32_t nsv;                  // survivors of the current round
-  uint32_t sv_pc[SURV];          // their sorted positions
-  JT sv_j[SURV];                 // and tracks in the chunk
 };
 
 using FwdSmall = FwdSmem<256, kFwdSmallHits>;
@@ -608,12 +604,15 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
     sm.u2.c.poff[tid] = first;
     if (tid == 0) sm.u2.c.poff[NT] = total;
     __syncthreads();
-    // the (track, candidate) pairs, shared out evenly, R at a time: the
-    // window test, the first station and the bound, the survivors listed
-    // (with their first stations, in the sort keys' workspace, dead by now,
-    // when positions fit in 16 bits: R <= n); then the survivors' far
-    // stations, fits and cuts
-    const uint32_t R = S::SM ? max(1u, min(S::SURV, n)) : S::SURV;
+    // the (track, candidate) pairs, shared out evenly, n at a time: the
+    // window test, the first station and the bound, the survivors listed in
+    // the event's workspace entries that are dead by now (at most one per
+    // pair, so at most n); then the survivors' far stations, fits and cuts.
+    // With positions of 16 bits (hits in shared memory) a survivor keeps its
+    // first station too.
+    const uint32_t R = max(1u, n);
+    uint32_t* sv_pj = W.yvb + h0;  // position, | track in the chunk << 16 when S::SM
+    uint32_t* sv_j = W.ka + h0;    // track in the chunk (hits in the workspace)
     uint32_t* sv_h01 = W.ka + h0;  // first-station positions, 16 bits each (0xFFFF: none)
     uint32_t* sv_h23 = W.kb + h0;
     uint32_t* sv_a1 = W.yka + h0;  // and line
@@ -640,19 +639,21 @@ __device__ __forceinline__ void fwd_event(const Fwd& F, S& sm, uint64_t e) {
         if (!fwd_station1(V, F, tr.x, tr.y, tr.w, r, pc, hl, &a1, &b1)) continue;
         if (!fwd_may_match(V, F, tr.x, hl, a1, b1)) continue;
         const uint32_t slot = atomicAdd(&sm.nsv, 1u);
-        sm.sv_pc[slot] = pc;
-        sm.sv_j[slot] = (typename S::JT)j;
         if constexpr (S::SM) {
+          sv_pj[slot] = pc | j << 16;
           sv_h01[slot] = (hl[0] & 0xFFFFu) | hl[1] << 16;
           sv_h23[slot] = (hl[2] & 0xFFFFu) | hl[3] << 16;
           sv_a1[slot] = __float_as_uint(a1);
           sv_b1[slot] = __float_as_uint(b1);
+        } else {
+          sv_pj[slot] = pc;
+          sv_j[slot] = j;
         }
       }
       __syncthreads();
       const uint32_t nsv = sm.nsv;
       for (uint32_t i = tid; i < nsv; i += NT) {
-        const uint32_t pc = sm.sv_pc[i], j = sm.sv_j[i];
+        const uint32_t pc = S::SM ? sv_pj[i] & 0xFFFFu : sv_pj[i], j = S::SM ? sv_pj[i] >> 16 : sv_j[i];
         const float4 tr = sm.u2.c.trk[j];
         FwdCand C;
         bool ok;
