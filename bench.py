@@ -255,10 +255,21 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_events_per_step": n, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                              "sample": f"{n} events of the C2 workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo), or 'unknown'."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def cpu_baseline(cfg):
@@ -280,7 +291,7 @@ def cpu_baseline(cfg):
     t0 = time.perf_counter()
     oracle.reconstruct(b1.offsets, b1.pixels, b1.geometry, op, n_threads=1)
     t1 = time.perf_counter() - t0
-    return {"value": n_done / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": n_done / t_total, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"first {n_done} of the 10k C2 events, all {cores} host threads, {t_total:.1f} s wall",
             "one_thread": {"value": 48 / t1, "unit": UNIT, "sample": f"first 48 C2 events, 1 thread, {t1:.1f} s"}}
 
