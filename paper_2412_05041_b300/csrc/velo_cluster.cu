@@ -43,14 +43,24 @@ struct ClusterSmem {
 
 constexpr uint32_t kRootFlag = 0x80000000u;
 constexpr uint32_t kRowSortMax = 32;  // longest row sorted by insertion (else the full radix sort)
+// Events of at least this many words (kept in the workspace) index the first
+// sorted position of every (module, row): 32 modules x 2048 rows.
+constexpr uint32_t kRowTable = 1u << 16;
 
 __device__ __forceinline__ uint32_t vload(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 
-__device__ __forceinline__ uint32_t uf_find(const uint32_t* parent, uint32_t a) {
-  for (;;) {  // parent[x] < x for every non-root: at most a steps
+// Root of a, halving the path on the way: every node passed is linked to its
+// grandparent.  parent[x] < x for every non-root and every write lowers a
+// parent to a node of the same component (atomicMin, as the unions write),
+// so the walk ends at the root within a steps and the forest stays one.
+__device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t a) {
+  for (;;) {
     const uint32_t p = vload(parent + a);
     if (p == a) return a;
-    a = p;
+    const uint32_t gp = vload(parent + p);
+    if (gp == p) return p;
+    atomicMin(parent + a, gp);
+    a = gp;
   }
 }
 
@@ -186,74 +196,136 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   // root of pass a has no earlier neighbour, and each union keeps the smaller
   // root, so every component ends with its smallest sorted position, i.e. its
   // smallest (module, row, col), as root -- whatever the thread order.
-  for (uint32_t i = tid; i < n; i += NT) {
-    const uint32_t k = A[i] & kKeyMask;
-    const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
-    const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
-    const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
-    const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
-    bool done = false, dup = false, left = false, up_left = false, up = false, up_right = false;
-    uint32_t nb_min = i;
-    int64_t j = (int64_t)i - 1;
-    for (int steps = 0; steps < 16; ++steps, --j) {
-      if (j < 0) {
-        done = true;
-        break;
-      }
-      const uint32_t kj = A[j] & kKeyMask;
-      if (kj < lo_all) {
-        done = true;
-        break;
-      }
-      const bool is_dup = kj == k, is_left = c > 0u && kj == k - 1u;
-      const bool is_prev = r > 0u && kj >= lo_k && kj <= hi_k;
-      if (is_dup || is_left || is_prev) nb_min = (uint32_t)j;  // scanning down: the last one found is the smallest
-      dup |= is_dup;
-      left |= is_left;
-      if (is_prev) {
-        const uint32_t pc = kj & 2047u;  // previous-row column c-1, c or c+1
-        up_left |= pc + 1u == c;
-        up |= pc == c;
-        up_right |= pc == c + 1u;
-      }
-    }
-    B[i] = nb_min;
-    if (!done || (up_right && !up && (left || up_left) && !dup)) A[i] |= 0x80000000u;
-  }
-  __syncthreads();
   bool ok = true;
-  for (uint32_t i = tid; i < n; i += NT) {
-    if (!(A[i] >> 31)) continue;
-    const uint32_t k = A[i] & kKeyMask;
-    const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
-    const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
-    const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
-    const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
-    bool done = false;
-    int64_t j = (int64_t)i - 1;
-    for (int steps = 0; steps < 16; ++steps, --j) {
-      if (j < 0) {
-        done = true;
-        break;
-      }
-      const uint32_t kj = A[j] & kKeyMask;
-      if (kj < lo_all) {
-        done = true;
-        break;
-      }
-      if (kj == k || (c > 0u && kj == k - 1u) || (r > 0u && kj >= lo_k && kj <= hi_k))
-        ok &= uf_unite(B, i, (uint32_t)j);
+  if (!PS && n >= kRowTable) {
+    // Large events (words in the workspace): a table of the first sorted
+    // position of every (module, row) -- in the hit-sort scratch, free until
+    // then -- gives the previous row's words directly, so every word finds
+    // all its earlier neighbours (duplicates and the left neighbour just
+    // before it, the previous row by bisection of that row) and only the
+    // V-shaped ones are united in pass b.
+    uint32_t* rt = W.sc + p0;
+    for (uint32_t q = tid; q < kRowTable; q += NT) rt[q] = n;
+    __syncthreads();
+    for (uint32_t pos = tid; pos < n; pos += NT) {
+      const uint32_t mr = (A[pos] & kKeyMask) >> 11, mp = pos ? ((A[pos - 1] & kKeyMask) >> 11) + 1u : 0u;
+      for (uint32_t q = mp; q <= mr; ++q) rt[q] = pos;
     }
-    if (!done) {  // past 16 steps (unions are idempotent: a neighbour seen twice is harmless)
-      // duplicates of k and the left neighbour (k - 1) are the words just before i
-      for (int64_t jj = (int64_t)i - 1; jj >= 0; --jj) {
-        const uint32_t kj = A[jj] & kKeyMask;
-        if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)jj);
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t k = A[i] & kKeyMask;
+      const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
+      bool dup = false, left = false, up_left = false, up = false, up_right = false;
+      uint32_t nb_min = i;
+      for (int64_t j = (int64_t)i - 1; j >= 0; --j) {  // duplicates, then the left neighbour's copies
+        const uint32_t kj = A[j] & kKeyMask;
+        if (kj == k) dup = true;
+        else if (c > 0u && kj == k - 1u) left = true;
         else break;
+        nb_min = (uint32_t)j;
       }
-      if (r > 0u) {  // previous row, columns c-1 .. c+1 of the same module
-        uint32_t jj = lower_bound_by(0u, i, [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
-        for (; jj < i && (A[jj] & kKeyMask) <= hi_k; ++jj) ok &= uf_unite(B, i, jj);
+      if (r > 0u) {
+        const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u), hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
+        const uint32_t mr = k >> 11;
+        uint32_t j = lower_bound_by(rt[mr - 1u], rt[mr], [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+        if (j < rt[mr] && (A[j] & kKeyMask) <= hi_k) nb_min = j;  // the smallest earlier neighbour
+        for (; j < rt[mr]; ++j) {
+          const uint32_t pc = A[j] & 2047u;  // previous-row column c-1, c or c+1
+          if ((A[j] & kKeyMask) > hi_k) break;
+          up_left |= pc + 1u == c;
+          up |= pc == c;
+          up_right |= pc == c + 1u;
+        }
+      }
+      B[i] = nb_min;
+      if (up_right && !up && (left || up_left) && !dup) A[i] |= 0x80000000u;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += NT) {
+      if (!(A[i] >> 31)) continue;
+      const uint32_t k = A[i] & kKeyMask;
+      const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
+      for (int64_t j = (int64_t)i - 1; j >= 0; --j) {
+        const uint32_t kj = A[j] & kKeyMask;
+        if (kj != k && !(c > 0u && kj == k - 1u)) break;
+        ok &= uf_unite(B, i, (uint32_t)j);
+      }
+      if (r > 0u) {
+        const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u), hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
+        const uint32_t mr = k >> 11;
+        uint32_t j = lower_bound_by(rt[mr - 1u], rt[mr], [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+        for (; j < rt[mr] && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j);
+      }
+    }
+  } else {
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t k = A[i] & kKeyMask;
+      const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
+      const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
+      const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
+      const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
+      bool done = false, dup = false, left = false, up_left = false, up = false, up_right = false;
+      uint32_t nb_min = i;
+      int64_t j = (int64_t)i - 1;
+      for (int steps = 0; steps < 16; ++steps, --j) {
+        if (j < 0) {
+          done = true;
+          break;
+        }
+        const uint32_t kj = A[j] & kKeyMask;
+        if (kj < lo_all) {
+          done = true;
+          break;
+        }
+        const bool is_dup = kj == k, is_left = c > 0u && kj == k - 1u;
+        const bool is_prev = r > 0u && kj >= lo_k && kj <= hi_k;
+        if (is_dup || is_left || is_prev) nb_min = (uint32_t)j;  // scanning down: the last one found is the smallest
+        dup |= is_dup;
+        left |= is_left;
+        if (is_prev) {
+          const uint32_t pc = kj & 2047u;  // previous-row column c-1, c or c+1
+          up_left |= pc + 1u == c;
+          up |= pc == c;
+          up_right |= pc == c + 1u;
+        }
+      }
+      B[i] = nb_min;
+      if (!done || (up_right && !up && (left || up_left) && !dup)) A[i] |= 0x80000000u;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += NT) {
+      if (!(A[i] >> 31)) continue;
+      const uint32_t k = A[i] & kKeyMask;
+      const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
+      const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
+      const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
+      const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
+      bool done = false;
+      int64_t j = (int64_t)i - 1;
+      for (int steps = 0; steps < 16; ++steps, --j) {
+        if (j < 0) {
+          done = true;
+          break;
+        }
+        const uint32_t kj = A[j] & kKeyMask;
+        if (kj < lo_all) {
+          done = true;
+          break;
+        }
+        if (kj == k || (c > 0u && kj == k - 1u) || (r > 0u && kj >= lo_k && kj <= hi_k))
+          ok &= uf_unite(B, i, (uint32_t)j);
+      }
+      if (!done) {  // past 16 steps (unions are idempotent: a neighbour seen twice is harmless)
+        // duplicates of k and the left neighbour (k - 1) are the words just before i
+        for (int64_t jj = (int64_t)i - 1; jj >= 0; --jj) {
+          const uint32_t kj = A[jj] & kKeyMask;
+          if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)jj);
+          else break;
+        }
+        if (r > 0u) {  // previous row, columns c-1 .. c+1 of the same module
+          uint32_t jj = lower_bound_by(0u, i, [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+          for (; jj < i && (A[jj] & kKeyMask) <= hi_k; ++jj) ok &= uf_unite(B, i, jj);
+        }
       }
     }
   }
@@ -263,7 +335,23 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
     return kNone;
   }
-  for (uint32_t i = tid; i < n; i += NT) B[i] = uf_find(B, i);
+  // every word to its root; the unions are done, so the walks halve their
+  // paths with plain stores (each link moves to an ancestor)
+  for (uint32_t i = tid; i < n; i += NT) {
+    uint32_t a = i;
+    for (;;) {
+      const uint32_t p = B[a];
+      if (p == a) break;
+      const uint32_t gp = B[p];
+      if (gp == p) {
+        a = p;
+        break;
+      }
+      B[a] = gp;
+      a = gp;
+    }
+    B[i] = a;
+  }
   __syncthreads();
 
   // 4. cluster ids: rank of each root among the roots (chunked block scan)

@@ -215,15 +215,16 @@ __device__ __forceinline__ Ranges window_ranges(const float* keys, uint32_t lo, 
 
 // Bucketed index of one module's sorted keys, so that a search bisects one
 // bucket of a few hits instead of the module: bucket b holds the keys in
-// [b/16, (b+1)/16) (the last one also a key rounded up to 4), tab[b] is the
-// first module-local index of a key in bucket b or later, tab[64] the count.
-// Keys below v sit in v's bucket or earlier and keys of later buckets are
-// above v, so the first key >= v (or > v) lies in [tab[b], tab[b+1]] and the
-// answer is the one the bisection of the whole module gives.
-constexpr uint32_t kKeyBuckets = 64;
+// [b/S, (b+1)/S), S = kKeyBuckets / 4 (the last one also a key rounded up to
+// 4), tab[b] is the first module-local index of a key in bucket b or later,
+// tab[kKeyBuckets] the count.  Keys below v sit in v's bucket or earlier and
+// keys of later buckets are above v, so the first key >= v (or > v) lies in
+// [tab[b], tab[b+1]] and the answer is the one the bisection of the whole
+// module gives.
+constexpr uint32_t kKeyBuckets = 128;
 __device__ __forceinline__ uint32_t key_bucket(float v) {
-  const float t = v * 16.0f;  // exact: a power of two
-  return t <= 0.0f ? 0u : (t >= 63.0f ? 63u : (uint32_t)t);
+  const float t = v * (float)(kKeyBuckets / 4);  // exact: a power of two
+  return t <= 0.0f ? 0u : (t >= (float)(kKeyBuckets - 1) ? kKeyBuckets - 1 : (uint32_t)t);
 }
 
 struct KeyIndex {
