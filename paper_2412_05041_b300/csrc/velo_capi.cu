@@ -152,12 +152,12 @@ int sm_count() {
 
 }  // namespace
 
-bool set_max_smem_once(const void* func, int slot) {
+bool set_max_smem_once(const void* func, int slot, uint32_t bytes) {
   const int d = current_device();
   if (d < 0 || d >= kMaxDev) return false;
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_smem_set[d] & (1u << slot)) return true;
-  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPerBlock) != cudaSuccess) {
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
     cudaGetLastError();  // do not leave the failure as the sticky last error
     return false;
   }

@@ -106,7 +106,7 @@ int output_blocks_per_sm();
 // host helpers (velo_capi.cu): raise a kernel's dynamic shared-memory limit
 // once per device (slot = a small id per kernel instance; occupancy with
 // slot < 0 leaves the limit alone), resident CTAs per SM
-bool set_max_smem_once(const void* func, int slot);
+bool set_max_smem_once(const void* func, int slot, uint32_t bytes = kSmemPerBlock);
 int occupancy(const void* func, int threads, uint32_t smem, int slot);
 
 }  // namespace velo

@@ -44,6 +44,11 @@ __host__ __device__ constexpr uint32_t seed_chunk() {
 // tuned block size; a step of such an event keeps 1024 threads busy.
 constexpr uint32_t kWideClusters = 20000;
 constexpr int kWideThreads = 1024;
+// Modules of up to this many hits get, in heavy events, a second order of
+// their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
+// of k_track_wide: r^2 f32 + module-local index u16 per hit).
+constexpr uint32_t kRadialCap = 8192;
+constexpr uint32_t kRadialBytes = kRadialCap * 6u;
 
 template <uint32_t C>
 struct SeedArrays {
@@ -149,7 +154,8 @@ __device__ __forceinline__ float cut_chi2ndf(uint32_t n, const float* st, float 
 // WIDE: this instance tracks the events of kWideClusters clusters or more
 // (and only those); the other instance every other event.
 template <int NT, bool WIDE>
-__device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, TrackSmem<NT>& S) {
+__device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, TrackSmem<NT>& S, float* rr2,
+                                          uint16_t* rord) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const Par P = L.par;  // by value: kept in registers, not re-read through a reference
@@ -220,6 +226,34 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const uint32_t clo = S.mod_off[m > 0 ? m - 1 : 0], chi = S.mod_off[min((uint32_t)m + 2u, M)];
     for (uint32_t pos = clo + tid; pos < chi; pos += NT) claim[pos] = ~0ull;
     __syncthreads();
+    // (heavy events) the hits of module m - 1 inside each key bucket by r^2,
+    // so that a dense h2 window visits only the hits of the radial band a seed
+    // can reach (read by the seeding of this step, after the extension's
+    // barriers)
+    bool radial = false;
+    if constexpr (WIDE) {
+      if (m >= 1) {
+        const uint32_t lo = S.mod_off[m - 1];
+        radial = S.mod_off[m] - lo <= kRadialCap;
+        if (radial) {
+          const uint16_t* tab = S.ktab[(m - 1) % 3];
+          for (uint32_t b = tid; b < kKeyBuckets; b += NT) {
+            const uint32_t s0 = tab[b], s1 = tab[b + 1];
+            for (uint32_t i = s0; i < s1; ++i) {  // insertion by r^2
+              const float x = hx[lo + i], y = hy[lo + i];
+              const float r2 = fa(fm(x, x), fm(y, y));
+              uint32_t k = i;
+              for (; k > s0 && rr2[k - 1] > r2; --k) {
+                rr2[k] = rr2[k - 1];
+                rord[k] = rord[k - 1];
+              }
+              rr2[k] = r2;
+              rord[k] = (uint16_t)i;
+            }
+          }
+        }
+      }
+    }
 
     // ---- extension into module m (against the used flags of the step start);
     // a hit within the cut lies within sqrt(max_scatter_fwd) of the prediction
@@ -372,28 +406,75 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
         const unsigned long long lid0 = hid[q0] - lo0;
         Ranges R2 = unpack_ranges(S.sd.r2[i], lo2);
-        if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
-          R2 = narrowed_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2, (x1 - alpha * x0) / one_m_alpha,
-                               (y1 - alpha * y0) / one_m_alpha, seed_reach);
         const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
         unsigned long long best = ~0ull;
-        for (int part2 = 0; part2 < 2; ++part2) {
-          const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
-          for (uint32_t q2 = s2; q2 < e2; ++q2) {
-            const float ex = fa(ux[q2], c0x), ey = fa(uy[q2], c0y);
-            if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) continue;
-            if (dmod4(hk[q2], k1) > P.win_seed) continue;
-            const float x2 = hx[q2], y2 = hy[q2];
-            const float dx02 = fs(x0, x2), dy02 = fs(y0, y2);
-            const float tx = fd(dx02, dz02), ty = fd(dy02, dz02);
-            if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
-            const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
-            const float dx = fs(xp, x1), dy = fs(yp, y1);
-            const float sc = fa(fm(dx, dx), fm(dy, dy));
-            if (sc > P.max_scatter_seed) continue;
-            const unsigned long long cand =
-                (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(hid[q2] - lo2);
-            best = cand < best ? cand : best;
+        auto try_h2 = [&](uint32_t q2) {
+          const float ex = fa(ux[q2], c0x), ey = fa(uy[q2], c0y);
+          if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) return;
+          if (dmod4(hk[q2], k1) > P.win_seed) return;
+          const float x2 = hx[q2], y2 = hy[q2];
+          const float dx02 = fs(x0, x2), dy02 = fs(y0, y2);
+          const float tx = fd(dx02, dz02), ty = fd(dy02, dz02);
+          if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) return;
+          const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
+          const float dx = fs(xp, x1), dy = fs(yp, y1);
+          const float sc = fa(fm(dx, dx), fm(dy, dy));
+          if (sc > P.max_scatter_seed) return;
+          const unsigned long long cand =
+              (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(hid[q2] - lo2);
+          best = cand < best ? cand : best;
+        };
+        bool searched = false;
+        if constexpr (WIDE) {
+          // A dense window in a heavy event: an h2 within the scatter cut lies
+          // within seed_reach of the point (px, py), so its key within `half`
+          // of the point's (as for narrowed_ranges) and its radius within
+          // seed_reach of the point's: the key buckets of that interval,
+          // each bisected by r^2, hold every such h2 (the exact tests decide).
+          if (radial && seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove) {
+            const float px = (x1 - alpha * x0) / one_m_alpha, py = (y1 - alpha * y0) / one_m_alpha;
+            const float rp = sqrtf(px * px + py * py);
+            const float half = 1.5708f * seed_reach / rp * 1.01f + 1e-4f;
+            if (rp > 2.0f * seed_reach && half < P.win_seed) {
+              const float kp = pseudo_angle(px, py), ka = kp - half - 1e-5f, kb = kp + half + 1e-5f;
+              const float rlo = fmaxf(rp - seed_reach, 0.0f), rhi = rp + seed_reach;
+              const float r2lo = rlo * rlo * (1.0f - 1e-5f) - 1e-6f, r2hi = rhi * rhi * (1.0f + 1e-5f) + 1e-6f;
+              const uint16_t* tab = S.ktab[(m - 1) % 3];
+              uint32_t b0[2], b1[2];
+              int nr = 2;
+              if (ka < 0.0f) {
+                b0[0] = 0;
+                b1[0] = key_bucket(kb);
+                b0[1] = key_bucket(ka + 4.0f);
+                b1[1] = kKeyBuckets - 1;
+              } else if (kb >= 4.0f) {
+                b0[0] = 0;
+                b1[0] = key_bucket(kb - 4.0f);
+                b0[1] = key_bucket(ka);
+                b1[1] = kKeyBuckets - 1;
+              } else {
+                nr = 1;
+                b0[0] = key_bucket(ka);
+                b1[0] = key_bucket(kb);
+              }
+              for (int g = 0; g < nr; ++g)
+                for (uint32_t b = b0[g]; b <= b1[g]; ++b) {
+                  const uint32_t s1 = tab[b + 1];
+                  for (uint32_t k = lower_bound_by(tab[b], s1, [&](uint32_t x) { return rr2[x] < r2lo; });
+                       k < s1 && rr2[k] <= r2hi; ++k)
+                    try_h2(lo2 + rord[k]);
+                }
+              searched = true;
+            }
+          }
+        }
+        if (!searched) {
+          if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
+            R2 = narrowed_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2,
+                                 (x1 - alpha * x0) / one_m_alpha, (y1 - alpha * y0) / one_m_alpha, seed_reach);
+          for (int part2 = 0; part2 < 2; ++part2) {
+            const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
+            for (uint32_t q2 = s2; q2 < e2; ++q2) try_h2(q2);
           }
         }
         if (best != ~0ull) atomicMin(&S.sd.best[i], best);
@@ -463,15 +544,18 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 template <int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   __shared__ TrackSmem<NT> S;
-  track_one<NT, false>(L, blockIdx.x, S);
+  track_one<NT, false>(L, blockIdx.x, S, nullptr, nullptr);
 }
 
 // The heavy events: a small grid of kWideThreads-thread CTAs strides over
 // the batch and tracks the events of kWideClusters clusters or more.
 __global__ void __launch_bounds__(kWideThreads, 2048 / kWideThreads) k_track_wide(Launch L) {
   __shared__ TrackSmem<kWideThreads> S;
+  extern __shared__ __align__(16) uint8_t radial_raw[];
+  float* rr2 = reinterpret_cast<float*>(radial_raw);
+  uint16_t* rord = reinterpret_cast<uint16_t*>(radial_raw + 4u * kRadialCap);
   for (uint64_t e = blockIdx.x; e < L.n_events; e += gridDim.x) {
-    track_one<kWideThreads, true>(L, e, S);
+    track_one<kWideThreads, true>(L, e, S, rr2, rord);
     __syncthreads();  // shared memory is reused by the next event
   }
 }
@@ -732,7 +816,8 @@ int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
     default: return VELO_EINVAL;
   }
-  k_track_wide<<<std::min<uint32_t>(grid, 1024u), kWideThreads, 0, s>>>(L);
+  if (!set_max_smem_once(reinterpret_cast<const void*>(k_track_wide), 5, kRadialBytes)) return VELO_ECUDA;
+  k_track_wide<<<std::min<uint32_t>(grid, 1024u), kWideThreads, kRadialBytes, s>>>(L);
   k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
 }
