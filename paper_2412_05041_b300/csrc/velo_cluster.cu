@@ -335,23 +335,9 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
     return kNone;
   }
-  // every word to its root; the unions are done, so the walks halve their
-  // paths with plain stores (each link moves to an ancestor)
-  for (uint32_t i = tid; i < n; i += NT) {
-    uint32_t a = i;
-    for (;;) {
-      const uint32_t p = B[a];
-      if (p == a) break;
-      const uint32_t gp = B[p];
-      if (gp == p) {
-        a = p;
-        break;
-      }
-      B[a] = gp;
-      a = gp;
-    }
-    B[i] = a;
-  }
+  // every word to its root (the walks halve their paths with atomicMin, so a
+  // word whose root is already written keeps it: the root is the smallest)
+  for (uint32_t i = tid; i < n; i += NT) B[i] = uf_find(B, i);
   __syncthreads();
 
   // 4. cluster ids: rank of each root among the roots (chunked block scan)

@@ -29,6 +29,8 @@
 #include "velo_internal.cuh"
 #include "velo_mlp.cuh"
 
+#include <cooperative_groups.h>
+
 namespace velo {
 
 namespace {
@@ -44,6 +46,10 @@ __host__ __device__ constexpr uint32_t seed_chunk() {
 // tuned block size; a step of such an event keeps 1024 threads busy.
 constexpr uint32_t kWideClusters = 20000;
 constexpr int kWideThreads = 1024;
+// CTAs (a thread-block cluster) per heavy event: every CTA runs the module
+// loop; the parallel loops of a step are shared out over the cluster's
+// threads and a cluster barrier orders their global-memory results.
+constexpr uint32_t kWideCluster = 8;
 // Modules of up to this many hits get, in heavy events, a second order of
 // their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
 // of k_track_wide: r^2 f32 + module-local index u16 per hit).
@@ -151,6 +157,15 @@ __device__ __forceinline__ float cut_chi2ndf(uint32_t n, const float* st, float 
 
 }  // namespace
 
+// Loads of workspace values another CTA of the cluster may have written
+// (WIDE): from L2, past this SM's L1, which is not kept coherent with the
+// other SMs' writes.
+template <bool L2ONLY, class T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (L2ONLY) return __ldcg(p);
+  else return *p;
+}
+
 // WIDE: this instance tracks the events of kWideClusters clusters or more
 // (and only those); the other instance every other event.
 template <int NT, bool WIDE>
@@ -160,6 +175,18 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   const uint32_t tid = threadIdx.x;
   const Par P = L.par;  // by value: kept in registers, not re-read through a reference
   const uint32_t M = L.geo.n_modules;
+  // the threads that share the event: this CTA, or (WIDE) its cluster
+  constexpr uint32_t CS = WIDE ? kWideCluster : 1u;
+  uint32_t rank = 0;
+  if constexpr (WIDE) rank = cooperative_groups::this_cluster().block_rank();
+  const uint32_t gt = rank * NT + tid, GT = CS * NT;
+  // (WIDE) the cluster barrier releases each CTA's writes and acquires the
+  // others' at cluster scope; reads of the other CTAs' workspace values go
+  // through L2 (ldx)
+  auto bar = [&]() {
+    if constexpr (WIDE) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+  };
   // largest |x| or |y| of a hit (centroids lie on the sensor: x0 .. x0 + pitch n_cols)
   const float coord_max = fmaxf(fmaxf(fabsf(L.geo.x0), fabsf(L.geo.x0 + L.geo.pitch * (float)L.geo.n_cols)),
                                 fmaxf(fabsf(L.geo.y0), fabsf(L.geo.y0 + L.geo.pitch * (float)L.geo.n_rows)));
@@ -197,11 +224,11 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   uint32_t* pick = W.trk_pick + tb;
   unsigned long long* pick_key = W.trk_pick_key + tb;
 
-  for (uint32_t i = tid; i < H; i += NT) {
+  for (uint32_t i = gt; i < H; i += GT) {
     used[i] = 0;
     first_of[i] = kNone;
   }
-  __syncthreads();  // mod_off
+  bar();  // mod_off
   // bucketed key index of module j into slot j % 3: entries past the last
   // bucket hold the count, every hit fills the buckets from its predecessor's
   // (exclusive) to its own
@@ -224,8 +251,8 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   for (int m = (int)M - 2; m >= 0; --m) {
     if (m >= 1) index_module((uint32_t)m - 1u);  // its slot held module m + 2, done with at step m + 1
     const uint32_t clo = S.mod_off[m > 0 ? m - 1 : 0], chi = S.mod_off[min((uint32_t)m + 2u, M)];
-    for (uint32_t pos = clo + tid; pos < chi; pos += NT) claim[pos] = ~0ull;
-    __syncthreads();
+    for (uint32_t pos = clo + gt; pos < chi; pos += GT) claim[pos] = ~0ull;
+    bar();
     // (heavy events) the hits of module m - 1 inside each key bucket by r^2,
     // so that a dense h2 window visits only the hits of the radial band a seed
     // can reach (read by the seeding of this step, after the extension's
@@ -260,15 +287,15 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const float fwd_reach = sqrtf(P.max_scatter_fwd) * 1.01f + 1e-3f;
     const float zm = S.z[m];
     const uint32_t mlo = S.mod_off[m], mhi = S.mod_off[m + 1];
-    for (uint32_t t = tid; t < n_tr; t += NT) {
-      const uint32_t mt = meta[t];
+    for (uint32_t t = gt; t < n_tr; t += GT) {
+      const uint32_t mt = ldx<WIDE>(meta + t);
       uint32_t pk = kNone;
       if (mt & kTrkActive) {
         const int la = (int)((mt >> 16) & 255u), lb = (int)(mt >> 24);
         if (la - m - 1 > (int)P.max_skipped) {
           meta[t] = mt & ~kTrkActive;
         } else if (la > m) {
-          const uint32_t a = ta[t], b = tbk[t];
+          const uint32_t a = ldx<WIDE>(ta + t), b = ldx<WIDE>(tbk + t);
           const float xa = hx[a], ya = hy[a], ka = hk[a], xb = hx[b], yb = hy[b];
           const float za = S.z[la], zb = S.z[lb];
           const float dzab = fs(za, zb);
@@ -285,7 +312,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
               const float dx = fs(xp, hx[pos]), dy = fs(yp, hy[pos]);
               const float d2 = fa(fm(dx, dx), fm(dy, dy));
               if (d2 > P.max_scatter_fwd) continue;
-              if (used[pos]) continue;
+              if (ldx<WIDE>(used + pos)) continue;
               if (dmod4(hk[pos], ka) > P.win_fwd) continue;
               const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | hid[pos];
               if (cand < best) {
@@ -303,10 +330,10 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       }
       pick[t] = pk;
     }
-    __syncthreads();
-    for (uint32_t t = tid; t < n_tr; t += NT) {
+    bar();
+    for (uint32_t t = gt; t < n_tr; t += GT) {
       const uint32_t pk = pick[t];
-      if (pk == kNone || claim[pk] != pick_key[t]) continue;
+      if (pk == kNone || ldx<WIDE>(claim + pk) != pick_key[t]) continue;
       const uint32_t mt = meta[t];
       const uint32_t n = mt & 255u, la = (mt >> 16) & 255u;
       prev[pk] = ta[t];
@@ -315,7 +342,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       meta[t] = (n + 1u) | kTrkActive | ((uint32_t)m << 16) | (la << 24);
       used[pk] = 1;
     }
-    __syncthreads();
+    bar();
     if (m == 0) break;
 
     // ---- seeding with the middle hit on m.  The (h0, h2) pairs of all middle
@@ -356,7 +383,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const float ap = fm(rcp_dz02, dz12), oma = fs(1.0f, ap);
     float* ux = W.cl_x + p0;  // (1 - a') x2, (1 - a') y2 of the hits of module m - 1 (the
     float* uy = W.cl_y + p0;  // clustering's centroid scratch, free during tracking)
-    for (uint32_t q = lo2 + tid; q < hi2; q += NT) {
+    for (uint32_t q = lo2 + gt; q < hi2; q += GT) {
       ux[q] = fm(oma, hx[q]);
       uy[q] = fm(oma, hy[q]);
     }
@@ -371,8 +398,12 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         uint32_t c = 0;
         if (i < cn) {
           const uint32_t p1 = cbase + i;
-          S.sd.best[i] = ~0ull;
-          if (!used[p1]) {
+          if (WIDE) {
+            if (rank == 0) seedkey[p1] = ~0ull;  // the cluster's per-h1 minimum lives in global memory
+          } else {
+            S.sd.best[i] = ~0ull;
+          }
+          if (!ldx<WIDE>(used + p1)) {
             const float k1 = hk[p1];
             const Ranges R0 = window_ranges(KeyIndex{hk, lo0, S.ktab[(m + 1) % 3]}, k1, P.win_seed);
             S.sd.r0[i] = pack_ranges(R0, lo0);
@@ -391,8 +422,8 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         if (i < cn) S.sd.ioff[i] = run;
         run += cnt[k];
       }
-      __syncthreads();
-      for (uint32_t j = tid; j < n_items; j += NT) {
+      bar();  // (WIDE) the u terms and the reset minima of every CTA
+      for (uint32_t j = gt; j < n_items; j += GT) {
         // middle hit of item j: the last i with ioff[i] <= j (empty entries
         // share the offset of the next one, so that i owns item j)
         const uint32_t i = lower_bound_by(0u, cn, [&](uint32_t x) { return S.sd.ioff[x] <= j; }) - 1u;
@@ -400,7 +431,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const Ranges R0 = unpack_ranges(S.sd.r0[i], lo0);
         const uint32_t kk = j - S.sd.ioff[i], na = R0.a1 - R0.a0;
         const uint32_t q0 = kk < na ? R0.a0 + kk : R0.b0 + (kk - na);
-        if (used[q0]) continue;
+        if (ldx<WIDE>(used + q0)) continue;
         const float k1 = hk[p1];
         if (dmod4(hk[q0], k1) > P.win_seed) continue;
         const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
@@ -409,7 +440,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
         unsigned long long best = ~0ull;
         auto try_h2 = [&](uint32_t q2) {
-          const float ex = fa(ux[q2], c0x), ey = fa(uy[q2], c0y);
+          const float ex = fa(ldx<WIDE>(ux + q2), c0x), ey = fa(ldx<WIDE>(uy + q2), c0y);
           if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) return;
           if (dmod4(hk[q2], k1) > P.win_seed) return;
           const float x2 = hx[q2], y2 = hy[q2];
@@ -477,12 +508,12 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
             for (uint32_t q2 = s2; q2 < e2; ++q2) try_h2(q2);
           }
         }
-        if (best != ~0ull) atomicMin(&S.sd.best[i], best);
+        if (best != ~0ull) atomicMin(WIDE ? &seedkey[p1] : &S.sd.best[i], best);
       }
-      __syncthreads();
-      for (uint32_t i = tid; i < cn; i += NT) {  // seeds claim their h0 and h2
+      bar();
+      for (uint32_t i = gt; i < cn; i += GT) {  // seeds claim their h0 and h2
         const uint32_t p1 = cbase + i;
-        const unsigned long long key = S.sd.best[i];
+        const unsigned long long key = WIDE ? ldx<WIDE>(seedkey + p1) : S.sd.best[i];
         unsigned long long skey = ~0ull;
         if (key != ~0ull) {
           const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
@@ -495,25 +526,26 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         }
         seedkey[p1] = skey;
       }
-      __syncthreads();
+      bar();
     }
     for (uint32_t base = mlo; base < mhi; base += NT) {
       const uint32_t p1 = base + tid;
       bool surv = false;
       uint32_t b0 = 0, b2 = 0;
       if (p1 < mhi) {
-        const unsigned long long skey = seedkey[p1];
+        const unsigned long long skey = ldx<WIDE>(seedkey + p1);
         if (skey != ~0ull) {
-          b0 = seed_h0[p1];
-          b2 = seed_h2[p1];
-          surv = claim[b0] == skey && claim[b2] == skey;
+          b0 = ldx<WIDE>(seed_h0 + p1);
+          b2 = ldx<WIDE>(seed_h2 + p1);
+          surv = ldx<WIDE>(claim + b0) == skey && ldx<WIDE>(claim + b2) == skey;
         }
       }
       uint32_t tot;
       const uint32_t r = block_exclusive_scan<NT, uint32_t>(surv ? 1u : 0u, &tot, S.tmp);
       // tracks hold >= 3 hits each and never share one, so n_tr <= H / 3 <= the
-      // event's track slice (n / 3); the test only guards the slice bound.
-      if (surv && n_tr + r < track_cap) {
+      // event's track slice (n / 3); the test only guards the slice bound.  Every
+      // CTA of a cluster counts the same survivors; the first one writes them.
+      if (surv && n_tr + r < track_cap && rank == 0) {
         const uint32_t t = n_tr + r;
         ta[t] = b2;
         tbk[t] = p1;
@@ -527,10 +559,10 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       }
       n_tr = min(n_tr + tot, track_cap);
     }
-    __syncthreads();
+    bar();
   }
 
-  if (tid == 0) W.ev_ntracks_all[e] = n_tr;
+  if (rank == 0 && tid == 0) W.ev_ntracks_all[e] = n_tr;
 }
 
 
@@ -547,16 +579,17 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   track_one<NT, false>(L, blockIdx.x, S, nullptr, nullptr);
 }
 
-// The heavy events: a small grid of kWideThreads-thread CTAs strides over
-// the batch and tracks the events of kWideClusters clusters or more.
-__global__ void __launch_bounds__(kWideThreads, 2048 / kWideThreads) k_track_wide(Launch L) {
+// The heavy events: a small grid of clusters of kWideCluster CTAs of
+// kWideThreads threads strides over the batch and tracks the events of
+// kWideClusters clusters or more, one cluster per event.
+__global__ void __cluster_dims__(kWideCluster, 1, 1) __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
   __shared__ TrackSmem<kWideThreads> S;
   extern __shared__ __align__(16) uint8_t radial_raw[];
   float* rr2 = reinterpret_cast<float*>(radial_raw);
   uint16_t* rord = reinterpret_cast<uint16_t*>(radial_raw + 4u * kRadialCap);
-  for (uint64_t e = blockIdx.x; e < L.n_events; e += gridDim.x) {
+  for (uint64_t e = blockIdx.x / kWideCluster; e < L.n_events; e += gridDim.x / kWideCluster) {
     track_one<kWideThreads, true>(L, e, S, rr2, rord);
-    __syncthreads();  // shared memory is reused by the next event
+    cooperative_groups::this_cluster().sync();  // shared memory and the workspace are reused by the next event
   }
 }
 
@@ -817,7 +850,8 @@ int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     default: return VELO_EINVAL;
   }
   if (!set_max_smem_once(reinterpret_cast<const void*>(k_track_wide), 5, kRadialBytes)) return VELO_ECUDA;
-  k_track_wide<<<std::min<uint32_t>(grid, 1024u), kWideThreads, kRadialBytes, s>>>(L);
+  const uint32_t wide_grid = std::min<uint32_t>(grid, 128u) * kWideCluster;  // a cluster per event, at most 128
+  k_track_wide<<<wide_grid, kWideThreads, kRadialBytes, s>>>(L);
   k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
 }

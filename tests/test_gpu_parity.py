@@ -310,6 +310,22 @@ def test_mc_quality_matches_oracle():
     assert m["efficiency"] >= 0.99 and m["ghost_rate"] <= 0.05
 
 
+def test_heavy_ion_events_repeatedly_match_oracle():
+    """Two heavy-ion-like events (1 PV, 10000 tracks, ~350k words: the
+    clustering's (module, row) table and the tracking's CTA clusters), three
+    runs: every run identical to the oracle (catches races that show only
+    now and then)."""
+    from dataclasses import replace
+    cfg = replace(velogen.C2, seed=9, n_events=2, fixed_pvs=1, fixed_tracks=10000)
+    b = velogen.generate(cfg)
+    vp, op = params(cfg.ms_theta)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    for _ in range(3):
+        g = gpu_run(b.offsets, b.pixels, b.geometry, vp, labels=True)
+        assert_same(g, r)
+        assert_labels(g["pixel_cluster"].cpu().numpy(), r["pixel_cluster"], b.offsets, b.offsets)
+
+
 def test_fp32_peak_measurement():
     """The FP32 ceiling helper returns a rate in the range a B300-class GPU can
     reach (148 SMs x 128 FMA lanes x 2 flops at 1-2.1 GHz: 38-80 TFLOP/s)."""
