@@ -29,6 +29,7 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   const uint64_t T = P / 3 + 1;
   ws->flag = c.take<uint32_t>(4);
   ws->queue = c.take<uint32_t>(4);
+  ws->wide_list = c.take<uint32_t>(E);
   ws->ev_nclusters = c.take<uint32_t>(E);
   ws->ev_modoff = c.take<uint32_t>(E * kModOffStride);
   ws->ev_ntracks_all = c.take<uint32_t>(E);
@@ -151,6 +152,11 @@ int sm_count() {
 }
 
 }  // namespace
+
+int device_sm_count() {
+  const int n = sm_count();
+  return n > 0 ? n : 148;
+}
 
 bool set_max_smem_once(const void* func, int slot, uint32_t bytes) {
   const int d = current_device();

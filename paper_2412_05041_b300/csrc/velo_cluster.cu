@@ -523,6 +523,7 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   if (tid == 0) {
     W.ev_nclusters[e] = n_clusters;
     L.out.status[e] = VELO_EVT_OK;
+    if (n_clusters >= kWideClusters) W.wide_list[atomicAdd(W.queue + 3, 1u)] = (uint32_t)e;
   }
 }
 

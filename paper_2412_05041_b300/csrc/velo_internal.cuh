@@ -18,6 +18,10 @@ constexpr uint32_t kSmemPerBlock = 227u * 1024u; // largest dynamic allocation o
 // (15 * 4095 * 23552 < 2^32); larger ones use 64 bits.
 constexpr uint32_t kNarrowPixels = 23552;
 constexpr uint32_t kModOffStride = 33;  // per-event module offsets, n_modules + 1 <= 33
+// Events with at least this many clusters (heavy-ion-like: some 2000 tracks
+// and more) are tracked by clusters of CTAs (k_track_wide), listed by the
+// clustering kernel in wide_list (count in queue[3]).
+constexpr uint32_t kWideClusters = 20000;
 
 // Per-track metadata word: n_hits (8 bits) | active (1 bit) << 8 |
 // module of the last (most upstream) hit << 16 | module of the one before << 24.
@@ -29,7 +33,8 @@ constexpr uint32_t kTrkActive = 1u << 8;
 // event has at most n_e clusters and n_e / 3 tracks, so slices never overlap.
 struct Workspace {
   uint32_t* flag;            // [1] offsets invalid
-  uint32_t* queue;           // [4] work-queue counters of the persistent kernels
+  uint32_t* queue;           // [4] work-queue counters of the persistent kernels; [3] wide_list count
+  uint32_t* wide_list;       // [E] events of kWideClusters clusters or more (any order)
   uint32_t* ev_nclusters;    // [E]
   uint32_t* ev_modoff;       // [E * 33] cluster-id (= sorted position) offsets per module
   uint32_t* ev_ntracks_all;  // [E] tracks built (kept or not)
@@ -108,5 +113,6 @@ int output_blocks_per_sm();
 // slot < 0 leaves the limit alone), resident CTAs per SM
 bool set_max_smem_once(const void* func, int slot, uint32_t bytes = kSmemPerBlock);
 int occupancy(const void* func, int threads, uint32_t smem, int slot);
+int device_sm_count();  // SMs of the current device (148 if it cannot be read)
 
 }  // namespace velo

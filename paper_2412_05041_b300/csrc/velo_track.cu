@@ -41,10 +41,9 @@ __host__ __device__ constexpr uint32_t seed_chunk() {
   return NT > 512 ? (uint32_t)NT : 512u;
 }
 
-// Events with at least this many clusters (heavy-ion-like: some 2000 tracks
-// and more) are tracked by CTAs of kWideThreads threads, the others by the
-// tuned block size; a step of such an event keeps 1024 threads busy.
-constexpr uint32_t kWideClusters = 20000;
+// Events with at least kWideClusters clusters (heavy-ion-like) are tracked
+// by clusters of CTAs of kWideThreads threads, the others by the tuned block
+// size.
 constexpr int kWideThreads = 1024;
 // CTAs (a thread-block cluster) per heavy event: every CTA runs the module
 // loop; the parallel loops of a step are shared out over the cluster's
@@ -579,16 +578,17 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   track_one<NT, false>(L, blockIdx.x, S, nullptr, nullptr);
 }
 
-// The heavy events: a small grid of clusters of kWideCluster CTAs of
-// kWideThreads threads strides over the batch and tracks the events of
-// kWideClusters clusters or more, one cluster per event.
+// The heavy events: one wave of clusters of kWideCluster CTAs of
+// kWideThreads threads takes the events of kWideClusters clusters or more
+// from the list the clustering kernel made, one cluster per event.
 __global__ void __cluster_dims__(kWideCluster, 1, 1) __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
   __shared__ TrackSmem<kWideThreads> S;
   extern __shared__ __align__(16) uint8_t radial_raw[];
   float* rr2 = reinterpret_cast<float*>(radial_raw);
   uint16_t* rord = reinterpret_cast<uint16_t*>(radial_raw + 4u * kRadialCap);
-  for (uint64_t e = blockIdx.x / kWideCluster; e < L.n_events; e += gridDim.x / kWideCluster) {
-    track_one<kWideThreads, true>(L, e, S, rr2, rord);
+  const uint32_t count = *(const volatile uint32_t*)(L.ws.queue + 3);
+  for (uint32_t i = blockIdx.x / kWideCluster; i < count; i += gridDim.x / kWideCluster) {
+    track_one<kWideThreads, true>(L, L.ws.wide_list[i], S, rr2, rord);
     cooperative_groups::this_cluster().sync();  // shared memory and the workspace are reused by the next event
   }
 }
@@ -850,7 +850,8 @@ int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     default: return VELO_EINVAL;
   }
   if (!set_max_smem_once(reinterpret_cast<const void*>(k_track_wide), 5, kRadialBytes)) return VELO_ECUDA;
-  const uint32_t wide_grid = std::min<uint32_t>(grid, 128u) * kWideCluster;  // a cluster per event, at most 128
+  // one wave: a cluster per kWideCluster SMs (one 1024-thread CTA per SM)
+  const uint32_t wide_grid = std::max<uint32_t>(1u, (uint32_t)device_sm_count() / kWideCluster) * kWideCluster;
   k_track_wide<<<wide_grid, kWideThreads, kRadialBytes, s>>>(L);
   k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
