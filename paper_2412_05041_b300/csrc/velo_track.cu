@@ -527,34 +527,46 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       }
       bar();
     }
-    for (uint32_t base = mlo; base < mhi; base += NT) {
-      const uint32_t p1 = base + tid;
-      bool surv = false;
-      uint32_t b0 = 0, b2 = 0;
-      if (p1 < mhi) {
-        const unsigned long long skey = ldx<WIDE>(seedkey + p1);
-        if (skey != ~0ull) {
-          b0 = ldx<WIDE>(seed_h0 + p1);
-          b2 = ldx<WIDE>(seed_h2 + p1);
-          surv = ldx<WIDE>(claim + b0) == skey && ldx<WIDE>(claim + b2) == skey;
+    // surviving seeds become tracks in the order of h1: two consecutive
+    // middle hits per thread, one block scan per 2 NT of them
+    for (uint32_t base = mlo; base < mhi; base += 2u * NT) {
+      bool surv[2];
+      uint32_t b0[2], b2[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t p1 = base + 2u * tid + (uint32_t)k;
+        surv[k] = false;
+        b0[k] = b2[k] = 0;
+        if (p1 < mhi) {
+          const unsigned long long skey = ldx<WIDE>(seedkey + p1);
+          if (skey != ~0ull) {
+            b0[k] = ldx<WIDE>(seed_h0 + p1);
+            b2[k] = ldx<WIDE>(seed_h2 + p1);
+            surv[k] = ldx<WIDE>(claim + b0[k]) == skey && ldx<WIDE>(claim + b2[k]) == skey;
+          }
         }
       }
       uint32_t tot;
-      const uint32_t r = block_exclusive_scan<NT, uint32_t>(surv ? 1u : 0u, &tot, S.tmp);
-      // tracks hold >= 3 hits each and never share one, so n_tr <= H / 3 <= the
-      // event's track slice (n / 3); the test only guards the slice bound.  Every
-      // CTA of a cluster counts the same survivors; the first one writes them.
-      if (surv && n_tr + r < track_cap && rank == 0) {
-        const uint32_t t = n_tr + r;
-        ta[t] = b2;
-        tbk[t] = p1;
-        meta[t] = 3u | kTrkActive | ((uint32_t)(m - 1) << 16) | ((uint32_t)m << 24);
-        prev[b2] = p1;
-        prev[p1] = b0;
-        prev[b0] = kNone;
-        used[b0] = 1;
-        used[p1] = 1;
-        used[b2] = 1;
+      uint32_t r = block_exclusive_scan<NT, uint32_t>((surv[0] ? 1u : 0u) + (surv[1] ? 1u : 0u), &tot, S.tmp);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!surv[k]) continue;
+        // tracks hold >= 3 hits each and never share one, so n_tr <= H / 3 <= the
+        // event's track slice (n / 3); the test only guards the slice bound.  Every
+        // CTA of a cluster counts the same survivors; the first one writes them.
+        if (n_tr + r < track_cap && rank == 0) {
+          const uint32_t t = n_tr + r, p1 = base + 2u * tid + (uint32_t)k;
+          ta[t] = b2[k];
+          tbk[t] = p1;
+          meta[t] = 3u | kTrkActive | ((uint32_t)(m - 1) << 16) | ((uint32_t)m << 24);
+          prev[b2[k]] = p1;
+          prev[p1] = b0[k];
+          prev[b0[k]] = kNone;
+          used[b0[k]] = 1;
+          used[p1] = 1;
+          used[b2[k]] = 1;
+        }
+        ++r;
       }
       n_tr = min(n_tr + tot, track_cap);
     }
