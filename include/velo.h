@@ -289,7 +289,6 @@ int velo_mlp_loss_grad(const float* x, const float* y, uint64_t n, const float* 
 int velo_mlp_adam_step(float* w, const float* grad, float* m, float* v, uint32_t n_weights, float lr, float beta1,
                        float beta2, float eps, uint32_t step, void* stream);
 
-/* Name of a VELO_* return code. */
 /* ---- Forward tracking: pixel-tracker tracks traced to a downstream tracker
  *
  * The first stage traces pixel-tracker tracks forwards: straight to the
@@ -372,8 +371,8 @@ int velo_forward_workspace_size(uint64_t n_events, uint64_t n_hits, uint64_t* by
  * or inconsistent argument (a parameter or z that is not finite, z_layers not
  * ascending behind z_mag, min_hits outside [3, 12], a non-positive p_min,
  * sigma_x or kappa), VELO_ECAPACITY for a small workspace.  Event offsets
- * that do not start at 0, decrease, end past n_hits or give an event 2^31
- * hits leave every track without a downstream track (n 0, no hits, state
+ * that do not start at 0, decrease, end past n_hits or give an event 2^29
+ * hits or more leave every track without a downstream track (n 0, no hits, state
  * 0); a track of fewer than two hits never has one; a result whose totals
  * exceed its capacities (no track lists written) makes velo_forward write
  * nothing. */
@@ -390,6 +389,7 @@ int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks
  * if a CUDA call fails. */
 int velo_measure_fp32_peak(double* flops_per_s, void* stream);
 
+/* Name of a VELO_* return code. */
 const char* velo_strerror(int code);
 
 /* Library version (major * 10000 + minor * 100 + patch). */
