@@ -34,7 +34,7 @@ template <int NT>
 struct ClusterSmem {
   uint32_t cnt[radix_counters(NT)];
   uint32_t tmp[64];
-  uint32_t mod_count[VELO_MAX_MODULES];
+  uint32_t mod_count[VELO_MAX_MODULES];  // first cluster id of each module (kNone: no word)
   uint32_t mod_off[kModOffStride];
   uint32_t flag;
   uint32_t next;  // event taken from the work queue
@@ -140,12 +140,16 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   // a stable sort by the full key leaves it.  If a row has more than
   // kRowSortMax words, the whole array is sorted again by the full key (4
   // passes; stable, from an order that still keeps equal keys in input order).
-  radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
-                        [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 11) & 255u; }, S.cnt, S.tmp);
-  radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
-                        [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 19; }, S.cnt, S.tmp);
-  bool long_row = false;
-  for (uint32_t pos = tid; pos < n; pos += NT) {
+  // (Events of kRowTable words or more -- dense modules, long rows -- take
+  // the full sort at once.)
+  bool long_row = !PS && n >= kRowTable;
+  if (!long_row) {
+    radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                          [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 11) & 255u; }, S.cnt, S.tmp);
+    radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
+                          [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 19; }, S.cnt, S.tmp);
+  }
+  for (uint32_t pos = tid; pos < n && !(!PS && n >= kRowTable); pos += NT) {
     // rows only permute inside themselves, so another thread's sort never
     // changes the (module, row) read here
     const uint32_t mr = (A[pos] & kKeyMask) >> 11;
@@ -340,41 +344,52 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   for (uint32_t i = tid; i < n; i += NT) B[i] = uf_find(B, i);
   __syncthreads();
 
-  // 4. cluster ids: rank of each root among the roots (chunked block scan)
-  const uint32_t ch = (n + NT - 1) / NT;
-  const uint32_t lo = min(n, tid * ch), hi = min(n, lo + ch);
-  uint32_t nroot = 0;
-  for (uint32_t i = lo; i < hi; ++i) nroot += (B[i] == i);
-  uint32_t n_clusters;
-  uint32_t rank = block_exclusive_scan<NT, uint32_t>(nroot, &n_clusters, S.tmp);
-  // roots per module: a chunk is sorted, so count per run of one module and
-  // add once per run (not once per root onto 26 shared counters)
-  uint32_t run_mod = 0, run_cnt = 0;
-  for (uint32_t i = lo; i < hi; ++i)
-    if (B[i] == i) {
-      B[i] = rank++ | kRootFlag;
-      const uint32_t m = (A[i] >> 22) & 31u;
-      if (m != run_mod && run_cnt) {
-        atomicAdd(&S.mod_count[run_mod], run_cnt);
-        run_cnt = 0;
-      }
-      run_mod = m;
-      ++run_cnt;
-    }
-  if (run_cnt) atomicAdd(&S.mod_count[run_mod], run_cnt);
-  __syncthreads();
-  for (uint32_t i = lo; i < hi; ++i) {
-    const uint32_t v = B[i];
-    B[i] = (v & kRootFlag) ? (v & ~kRootFlag) : (vload(B + v) & ~kRootFlag);
+  // 4. cluster ids: rank of each root among the roots.  Every warp takes a
+  // contiguous chunk, 32 words at a time (coalesced): a ballot counts its
+  // roots, a block scan over the warps gives each chunk its first rank, a
+  // second ballot pass numbers the roots.  Then every word takes its root's
+  // rank; the first word of a module is a root (no earlier neighbour there),
+  // so its rank is the module's first cluster id.
+  constexpr uint32_t NW = NT / 32;
+  const uint32_t lane = lane_id(), wid = warp_id();
+  const uint32_t cw = ((n + NW - 1) / NW + 31u) & ~31u;
+  const uint32_t wlo = min(n, wid * cw), whi = min(n, wlo + cw);
+  uint32_t wroots = 0;
+  for (uint32_t base = wlo; base < whi; base += 32) {
+    const uint32_t i = base + lane;
+    wroots += __popc(__ballot_sync(kFull, i < whi && B[i] == i));
   }
+  uint32_t n_clusters;
+  uint32_t rank = block_exclusive_scan<NT, uint32_t>(lane == 0 ? wroots : 0u, &n_clusters, S.tmp);
+  rank = __shfl_sync(kFull, rank, 0);
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t base = wlo; base < whi; base += 32) {
+    const uint32_t i = base + lane;
+    const bool root = i < whi && B[i] == i;
+    const uint32_t bal = __ballot_sync(kFull, root);
+    if (root) B[i] = (rank + __popc(bal & lt)) | kRootFlag;
+    rank += __popc(bal);
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += NT) {
+    const uint32_t v = B[i];
+    const uint32_t id = (v & kRootFlag) ? (v & ~kRootFlag) : (vload(B + v) & ~kRootFlag);
+    B[i] = id;
+    const uint32_t m = (A[i] >> 22) & 31u;
+    if (i == 0 || m != ((A[i - 1] >> 22) & 31u)) S.mod_count[m] = id;  // the module's first cluster id
+  }
+  __syncthreads();
   if (tid == 0) {
-    uint32_t o = 0;
-    for (uint32_t m = 0; m < M; ++m) {
-      S.mod_off[m] = o;
-      if (S.mod_count[m] > VELO_MAX_MODULE_CLUSTERS) S.flag = 3u;
-      o += S.mod_count[m];
-    }
+    uint32_t o = n_clusters;
     S.mod_off[M] = o;
+    for (int m = (int)M - 1; m >= 0; --m) {
+      const uint32_t f = S.mod_count[m];
+      if (f != kNone) {
+        if (o - f > VELO_MAX_MODULE_CLUSTERS) S.flag = 3u;
+        o = f;
+      }
+      S.mod_off[m] = o;  // an empty module starts where the next one does
+    }
   }
   __syncthreads();
   if (S.flag) {
@@ -543,7 +558,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   }
   const uint32_t n = (uint32_t)(p1 - p0);
   if (tid == 0) S.flag = offsets_ok ? 0u : 1u;
-  if (tid < VELO_MAX_MODULES) S.mod_count[tid] = 0;
+  if (tid < VELO_MAX_MODULES) S.mod_count[tid] = kNone;
   __syncthreads();
 
   // 1. load + validate
