@@ -53,7 +53,7 @@ constexpr uint32_t kWideCluster = 8;
 // their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
 // of k_track_wide: r^2 f32 + module-local index u16 per hit).
 constexpr uint32_t kRadialCap = 8192;
-constexpr uint32_t kRadialBytes = kRadialCap * 6u;
+constexpr uint32_t kRadialBytes = kRadialCap * 10u;  // + r^2 in key order while the order is built
 
 template <uint32_t C>
 struct SeedArrays {
@@ -262,20 +262,26 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const uint32_t lo = S.mod_off[m - 1];
         radial = S.mod_off[m] - lo <= kRadialCap;
         if (radial) {
+          // r^2 of every hit in key order, then each hit's place in its bucket:
+          // the hits of the bucket before it in (r^2, key-order index) order
           const uint16_t* tab = S.ktab[(m - 1) % 3];
-          for (uint32_t b = tid; b < kKeyBuckets; b += NT) {
-            const uint32_t s0 = tab[b], s1 = tab[b + 1];
-            for (uint32_t i = s0; i < s1; ++i) {  // insertion by r^2
-              const float x = hx[lo + i], y = hy[lo + i];
-              const float r2 = fa(fm(x, x), fm(y, y));
-              uint32_t k = i;
-              for (; k > s0 && rr2[k - 1] > r2; --k) {
-                rr2[k] = rr2[k - 1];
-                rord[k] = rord[k - 1];
-              }
-              rr2[k] = r2;
-              rord[k] = (uint16_t)i;
+          const uint32_t n2 = S.mod_off[m] - lo;
+          float* rkey = reinterpret_cast<float*>(rord + kRadialCap);
+          for (uint32_t i = tid; i < n2; i += NT) {
+            const float x = hx[lo + i], y = hy[lo + i];
+            rkey[i] = fa(fm(x, x), fm(y, y));
+          }
+          __syncthreads();
+          for (uint32_t i = tid; i < n2; i += NT) {
+            const uint32_t b = key_bucket(hk[lo + i]), s0 = tab[b], s1 = tab[b + 1];
+            const float r2 = rkey[i];
+            uint32_t c = 0;
+            for (uint32_t j = s0; j < s1; ++j) {
+              const float r2j = rkey[j];
+              c += (r2j < r2 || (r2j == r2 && j < i)) ? 1u : 0u;
             }
+            rr2[s0 + c] = r2;
+            rord[s0 + c] = (uint16_t)i;
           }
         }
       }
