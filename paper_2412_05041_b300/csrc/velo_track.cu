@@ -53,7 +53,11 @@ constexpr uint32_t kWideCluster = 8;
 // their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
 // of k_track_wide: r^2 f32 + module-local index u16 per hit).
 constexpr uint32_t kRadialCap = 8192;
-constexpr uint32_t kRadialBytes = kRadialCap * 10u;  // + r^2 in key order while the order is built
+// dynamic shared memory of k_track_wide: the radial order (r^2 f32, index
+// u16, r^2 in key order f32 while it is built), the u terms of the h2 module
+// (2 f32) and the used flags of the h0 module (1 bit) -- per CTA, so that the
+// triplet loop reads none of them from another SM through L2
+constexpr uint32_t kRadialBytes = kRadialCap * 18u + kRadialCap / 8u;
 
 template <uint32_t C>
 struct SeedArrays {
@@ -388,9 +392,32 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const float ap = fm(rcp_dz02, dz12), oma = fs(1.0f, ap);
     float* ux = W.cl_x + p0;  // (1 - a') x2, (1 - a') y2 of the hits of module m - 1 (the
     float* uy = W.cl_y + p0;  // clustering's centroid scratch, free during tracking)
-    for (uint32_t q = lo2 + gt; q < hi2; q += GT) {
-      ux[q] = fm(oma, hx[q]);
-      uy[q] = fm(oma, hy[q]);
+    // (WIDE, modules of up to kRadialCap hits) every CTA keeps its own copy of
+    // the u terms of module m - 1 and of the used flags of module m + 1
+    bool local = false;
+    float *sux = nullptr, *suy = nullptr;
+    uint32_t* sused = nullptr;
+    if constexpr (WIDE) {
+      local = radial && hi0 - lo0 <= kRadialCap;
+      sux = reinterpret_cast<float*>(rord + kRadialCap) + kRadialCap;
+      suy = sux + kRadialCap;
+      sused = reinterpret_cast<uint32_t*>(suy + kRadialCap);
+    }
+    if (local) {
+      for (uint32_t q = tid; q < hi2 - lo2; q += NT) {
+        sux[q] = fm(oma, hx[lo2 + q]);
+        suy[q] = fm(oma, hy[lo2 + q]);
+      }
+      for (uint32_t base = 0; base < hi0 - lo0; base += NT) {
+        const uint32_t q = base + tid;
+        const uint32_t bal = __ballot_sync(kFull, q < hi0 - lo0 && ldx<WIDE>(used + lo0 + q));
+        if (lane_id() == 0 && base + warp_id() * 32u < hi0 - lo0) sused[(base >> 5) + warp_id()] = bal;
+      }
+    } else {
+      for (uint32_t q = lo2 + gt; q < hi2; q += GT) {
+        ux[q] = fm(oma, hx[q]);
+        uy[q] = fm(oma, hy[q]);
+      }
     }
     constexpr uint32_t kChunk = seed_chunk<NT>();
     for (uint32_t cbase = mlo; cbase < mhi; cbase += kChunk) {
@@ -436,7 +463,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const Ranges R0 = unpack_ranges(S.sd.r0[i], lo0);
         const uint32_t kk = j - S.sd.ioff[i], na = R0.a1 - R0.a0;
         const uint32_t q0 = kk < na ? R0.a0 + kk : R0.b0 + (kk - na);
-        if (ldx<WIDE>(used + q0)) continue;
+        if (local ? (sused[(q0 - lo0) >> 5] >> ((q0 - lo0) & 31u)) & 1u : ldx<WIDE>(used + q0)) continue;
         const float k1 = hk[p1];
         if (dmod4(hk[q0], k1) > P.win_seed) continue;
         const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
@@ -445,7 +472,8 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
         unsigned long long best = ~0ull;
         auto try_h2 = [&](uint32_t q2) {
-          const float ex = fa(ldx<WIDE>(ux + q2), c0x), ey = fa(ldx<WIDE>(uy + q2), c0y);
+          const float ex = fa(local ? sux[q2 - lo2] : ldx<WIDE>(ux + q2), c0x),
+                      ey = fa(local ? suy[q2 - lo2] : ldx<WIDE>(uy + q2), c0y);
           if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) return;
           if (dmod4(hk[q2], k1) > P.win_seed) return;
           const float x2 = hx[q2], y2 = hy[q2];
