@@ -128,6 +128,7 @@ Par make_par(const velo_params_t* p) {
 constexpr int kMaxDev = 64;
 std::mutex g_mu;
 uint32_t g_smem_set[kMaxDev] = {};  // bit per kernel slot: dynamic shared-memory limit raised
+uint32_t g_cluster_set[kMaxDev] = {};  // bit per kernel slot: clusters above 8 CTAs allowed
 struct OccKey {
   int dev;
   const void* func;
@@ -168,6 +169,19 @@ bool set_max_smem_once(const void* func, int slot, uint32_t bytes) {
     return false;
   }
   g_smem_set[d] |= 1u << slot;
+  return true;
+}
+
+bool allow_large_clusters_once(const void* func, int slot) {
+  const int d = current_device();
+  if (d < 0 || d >= kMaxDev) return false;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_cluster_set[d] & (1u << slot)) return true;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  g_cluster_set[d] |= 1u << slot;
   return true;
 }
 

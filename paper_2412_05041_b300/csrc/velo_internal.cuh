@@ -114,5 +114,6 @@ int output_blocks_per_sm();
 bool set_max_smem_once(const void* func, int slot, uint32_t bytes = kSmemPerBlock);
 int occupancy(const void* func, int threads, uint32_t smem, int slot);
 int device_sm_count();  // SMs of the current device (148 if it cannot be read)
+bool allow_large_clusters_once(const void* func, int slot);  // thread-block clusters of up to 16 CTAs
 
 }  // namespace velo

@@ -48,7 +48,7 @@ constexpr int kWideThreads = 1024;
 // CTAs (a thread-block cluster) per heavy event: every CTA runs the module
 // loop; the parallel loops of a step are shared out over the cluster's
 // threads and a cluster barrier orders their global-memory results.
-constexpr uint32_t kWideCluster = 8;
+constexpr uint32_t kWideCluster = 16;  // above the portable 8: allowed per kernel at the first launch
 // Modules of up to this many hits get, in heavy events, a second order of
 // their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
 // of k_track_wide: r^2 f32 + module-local index u16 per hit).
@@ -895,7 +895,9 @@ int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
     default: return VELO_EINVAL;
   }
-  if (!set_max_smem_once(reinterpret_cast<const void*>(k_track_wide), 5, kRadialBytes)) return VELO_ECUDA;
+  if (!set_max_smem_once(reinterpret_cast<const void*>(k_track_wide), 5, kRadialBytes) ||
+      !allow_large_clusters_once(reinterpret_cast<const void*>(k_track_wide), 0))
+    return VELO_ECUDA;
   // one wave: a cluster per kWideCluster SMs (one 1024-thread CTA per SM)
   const uint32_t wide_grid = std::max<uint32_t>(1u, (uint32_t)device_sm_count() / kWideCluster) * kWideCluster;
   k_track_wide<<<wide_grid, kWideThreads, kRadialBytes, s>>>(L);
