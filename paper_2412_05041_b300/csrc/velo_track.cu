@@ -30,6 +30,7 @@
 #include "velo_mlp.cuh"
 
 #include <cooperative_groups.h>
+#include <mutex>
 
 namespace velo {
 
@@ -47,8 +48,10 @@ __host__ __device__ constexpr uint32_t seed_chunk() {
 constexpr int kWideThreads = 1024;
 // CTAs (a thread-block cluster) per heavy event: every CTA runs the module
 // loop; the parallel loops of a step are shared out over the cluster's
-// threads and a cluster barrier orders their global-memory results.
-constexpr uint32_t kWideCluster = 16;  // above the portable 8: allowed per kernel at the first launch
+// threads and a cluster barrier orders their global-memory results.  16 (a
+// non-portable size) where the device can place such a cluster, else the
+// portable 8; the kernel reads the size at run time.
+constexpr uint32_t kWideClusterMax = 16, kWideClusterPortable = 8;
 // Modules of up to this many hits get, in heavy events, a second order of
 // their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
 // of k_track_wide: r^2 f32 + module-local index u16 per hit).
@@ -179,9 +182,11 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   const Par P = L.par;  // by value: kept in registers, not re-read through a reference
   const uint32_t M = L.geo.n_modules;
   // the threads that share the event: this CTA, or (WIDE) its cluster
-  constexpr uint32_t CS = WIDE ? kWideCluster : 1u;
-  uint32_t rank = 0;
-  if constexpr (WIDE) rank = cooperative_groups::this_cluster().block_rank();
+  uint32_t CS = 1, rank = 0;
+  if constexpr (WIDE) {
+    CS = cooperative_groups::this_cluster().num_blocks();
+    rank = cooperative_groups::this_cluster().block_rank();
+  }
   const uint32_t gt = rank * NT + tid, GT = CS * NT;
   // (WIDE) the cluster barrier releases each CTA's writes and acquires the
   // others' at cluster scope; reads of the other CTAs' workspace values go
@@ -624,16 +629,17 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   track_one<NT, false>(L, blockIdx.x, S, nullptr, nullptr);
 }
 
-// The heavy events: one wave of clusters of kWideCluster CTAs of
-// kWideThreads threads takes the events of kWideClusters clusters or more
+// The heavy events: one wave of clusters of CTAs of kWideThreads threads
+// (cluster size chosen at the launch) takes the events of kWideClusters clusters or more
 // from the list the clustering kernel made, one cluster per event.
-__global__ void __cluster_dims__(kWideCluster, 1, 1) __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
+__global__ void __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
   __shared__ TrackSmem<kWideThreads> S;
   extern __shared__ __align__(16) uint8_t radial_raw[];
   float* rr2 = reinterpret_cast<float*>(radial_raw);
   uint16_t* rord = reinterpret_cast<uint16_t*>(radial_raw + 4u * kRadialCap);
   const uint32_t count = *(const volatile uint32_t*)(L.ws.queue + 3);
-  for (uint32_t i = blockIdx.x / kWideCluster; i < count; i += gridDim.x / kWideCluster) {
+  const uint32_t cs = cooperative_groups::this_cluster().num_blocks();
+  for (uint32_t i = blockIdx.x / cs; i < count; i += gridDim.x / cs) {
     track_one<kWideThreads, true>(L, L.ws.wide_list[i], S, rr2, rord);
     cooperative_groups::this_cluster().sync();  // shared memory and the workspace are reused by the next event
   }
@@ -889,18 +895,61 @@ __global__ void __launch_bounds__(kScanThreads) k_validate_offsets(Launch L) {
   }
 }
 
+// Cluster size of k_track_wide on the current device (once per device): 16
+// if one such cluster of 1024-thread CTAs with their shared memory can be
+// resident, else 8; 0 if the kernel's attributes cannot be set.
+uint32_t wide_cluster_size() {
+  static std::mutex mu;
+  static uint32_t size[64] = {};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (size[d]) return size[d];
+  const void* f = reinterpret_cast<const void*>(k_track_wide);
+  if (!set_max_smem_once(f, 5, kRadialBytes)) return 0;
+  uint32_t cs = kWideClusterPortable;
+  if (allow_large_clusters_once(f, 0)) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kWideClusterMax;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kWideClusterMax);
+    cfg.blockDim = dim3(kWideThreads);
+    cfg.dynamicSmemBytes = kRadialBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_track_wide, &cfg) == cudaSuccess && n >= 1) cs = kWideClusterMax;
+    cudaGetLastError();
+  }
+  size[d] = cs;
+  return cs;
+}
+
 int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
   switch (nt) {
     case 128: k_track<128><<<grid, 128, 0, s>>>(L); break;
     case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
     default: return VELO_EINVAL;
   }
-  if (!set_max_smem_once(reinterpret_cast<const void*>(k_track_wide), 5, kRadialBytes) ||
-      !allow_large_clusters_once(reinterpret_cast<const void*>(k_track_wide), 0))
-    return VELO_ECUDA;
-  // one wave: a cluster per kWideCluster SMs (one 1024-thread CTA per SM)
-  const uint32_t wide_grid = std::max<uint32_t>(1u, (uint32_t)device_sm_count() / kWideCluster) * kWideCluster;
-  k_track_wide<<<wide_grid, kWideThreads, kRadialBytes, s>>>(L);
+  const uint32_t cs = wide_cluster_size();
+  if (!cs) return VELO_ECUDA;
+  // one wave: a cluster per cs SMs (one 1024-thread CTA per SM)
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(std::max<uint32_t>(1u, (uint32_t)device_sm_count() / cs) * cs);
+  cfg.blockDim = dim3(kWideThreads);
+  cfg.dynamicSmemBytes = kRadialBytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_track_wide, L) != cudaSuccess) return VELO_ECUDA;
   k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
 }
