@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-forward", action="store_true", help="skip the forward-tracking measurement")
     ap.add_argument("--forward-only", action="store_true",
                     help="only the forward-tracking measurement (one JSON line of its own; for profiling)")
+    ap.add_argument("--no-heavy", action="store_true", help="skip the heavy-ion-like event measurement")
+    ap.add_argument("--heavy-only", action="store_true",
+                    help="only the heavy-ion-like event measurement (one JSON line of its own; for profiling)")
     return ap.parse_args()
 
 
@@ -369,6 +372,36 @@ def run_serving(args, dev, vp, tuning):
             "p50_latency_ms": poi["p50_latency_ms"], "p99_latency_ms": poi["p99_latency_ms"]}
 
 
+def run_heavy(args, dev, vp):
+    """Heavy-ion-like events (1 PV, 10000 tracks, ~350k pixel words each), four
+    per batch: the stage times of one batch (the four events run side by side,
+    so a stage's time is about one event's latency), K timed batches."""
+    import torch
+
+    import paper_2412_05041_b300 as velo
+    import velogen
+    from dataclasses import replace
+    b = velogen.generate(replace(velogen.C2, seed=9, n_events=4, fixed_pvs=1, fixed_tracks=10000))
+    off = torch.from_numpy(b.offsets.view(np.int64)).to(dev)
+    pix = torch.from_numpy(b.pixels.view(np.int32)).to(dev)
+    R = velo.Reconstructor(b.geometry, vp, max_events=b.n_events, max_pixels=pix.numel(), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        R.run(off, pix, stream)
+    K = max(3, args.steps)
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    for k in range(K):
+        R.run(off, pix, stream, marks=marks[k])
+    torch.cuda.synchronize(dev)
+    stage = {s_: float(np.median([marks[k][i].elapsed_time(marks[k][i + 1]) for k in range(K)]))
+             for i, s_ in enumerate(STAGES)}
+    total = float(np.median([marks[k][0].elapsed_time(marks[k][4]) for k in range(K)]))
+    return {"workload": "4 heavy-ion-like events (1 PV, 10000 tracks each), one batch",
+            "words_per_event": [int(x) for x in np.diff(b.offsets.astype(np.int64))],
+            "clusters": int(R.totals[0]), "tracks": int(R.totals[1]), "batch_ms": total, "stage_ms": stage,
+            "batches": K}
+
+
 def run_forward(args, dev, vp, n_ev):
     """Forward tracking of the pixel-tracker tracks of n_ev pile-up-5.5 events
     to twelve downstream layers (invented geometry, 20 noise hits per layer):
@@ -446,10 +479,11 @@ def run_ours(args):
     cfg = velogen.C2
     n_ev = args.events
     first, n_ev = shard(rank, world, n_ev)
-    if args.forward_only:
-        out = run_forward(args, dev, velo.default_params(**params_values(cfg.ms_theta)), n_ev)
+    if args.forward_only or args.heavy_only:
+        vp0 = velo.default_params(**params_values(cfg.ms_theta))
+        out = run_forward(args, dev, vp0, n_ev) if args.forward_only else run_heavy(args, dev, vp0)
         if rank == 0:
-            print(json.dumps({"forward": out}))
+            print(json.dumps({"forward" if args.forward_only else "heavy_events": out}))
         if world > 1:
             dist.destroy_process_group()
         return
@@ -577,6 +611,13 @@ def run_ours(args):
         except Exception as exc:
             serving = {"error": repr(exc)[:300]}
 
+    heavy = None
+    if world == 1 and not args.no_heavy:
+        try:
+            heavy = run_heavy(args, dev, vp)
+        except Exception as exc:
+            heavy = {"error": repr(exc)[:300]}
+
     forward = None
     if world == 1 and not args.no_forward:
         try:
@@ -643,6 +684,7 @@ def run_ours(args):
         "batched": batched,
         "serving": serving,
         "forward": forward,
+        "heavy_events": heavy,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfg)
