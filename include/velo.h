@@ -184,7 +184,7 @@ int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometr
 /* Block shapes of the persistent kernels (events of any size are spread over
  * the SMs by work queues; these choose how).  Any valid setting gives the same
  * results bit for bit; speed depends on the workload (autotuned by the Python
- * layer).  velo_tuning_default: 1024 / largest tier / 256 / all resident. */
+ * layer).  velo_tuning_default: 1024 / largest tier / 256 / all resident / 0. */
 typedef struct velo_tuning {
   uint32_t cluster_threads;      /* 512 (two CTAs per SM) or 1024 (one) */
   uint32_t cluster_smem_pixels;  /* words per event sorted in shared memory, 0 = the most that fits;
@@ -194,6 +194,9 @@ typedef struct velo_tuning {
                                     persistent; k = at most k per SM, persistent; VELO_CTAS_PER_EVENT =
                                     one CTA per event, scheduled by the hardware as CTAs finish (the
                                     tracking kernel always runs one CTA per event) */
+  uint32_t wide_cluster;         /* CTAs (a thread-block cluster of 1024-thread CTAs) tracking each event of
+                                    20000 clusters or more: 0 = the largest the device can place (16, else
+                                    8), or 8 or 16 (VELO_EINVAL if the device cannot place it) */
 } velo_tuning_t;
 #define VELO_CTAS_PER_EVENT 0xFFFFFFFFu
 int velo_tuning_default(velo_tuning_t* t);

@@ -285,6 +285,7 @@ int velo_tuning_default(velo_tuning_t* t) {
   t->cluster_smem_pixels = 0;
   t->track_threads = 256;
   t->ctas_per_sm = 0;
+  t->wide_cluster = 0;
   return VELO_OK;
 }
 
@@ -300,7 +301,8 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   velo_tuning_default(&tu);
   if (tuning) tu = *tuning;
   if ((tu.cluster_threads != 512 && tu.cluster_threads != 1024) ||
-      (tu.track_threads != 128 && tu.track_threads != 256))
+      (tu.track_threads != 128 && tu.track_threads != 256) ||
+      (tu.wide_cluster != 0 && tu.wide_cluster != 8 && tu.wide_cluster != 16))
     return VELO_EINVAL;
   const uint32_t max_tier = cluster_max_tier((int)tu.cluster_threads);
   const uint32_t tier = tu.cluster_smem_pixels ? tu.cluster_smem_pixels : max_tier;
@@ -335,7 +337,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   if (E) rc = launch_cluster(L, (int)tu.cluster_threads, grid(cluster_blocks_per_sm((int)tu.cluster_threads, tier)), s);
   if (rc != VELO_OK) return rc;
   mark(1);
-  if (E) rc = launch_track(L, (int)tu.track_threads, (uint32_t)E, s);  // one CTA per event
+  if (E) rc = launch_track(L, (int)tu.track_threads, (uint32_t)E, tu.wide_cluster, s);  // one CTA per event
   if (rc != VELO_OK) return rc;
   mark(2);
   k_scan<<<1, kScanThreads, 0, s>>>(L);

@@ -100,7 +100,7 @@ bool carve_workspace(void* base, uint64_t bytes, uint64_t E, uint64_t P, Workspa
 __global__ void k_validate_offsets(Launch L);
 __global__ void k_scan(Launch L);
 int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s);
-int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s);
+int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, cudaStream_t s);
 int launch_output(const Launch& L, uint32_t grid, cudaStream_t s);
 uint32_t cluster_smem_bytes(int nt, uint32_t tier);
 uint32_t cluster_max_tier(int nt);

@@ -928,14 +928,16 @@ uint32_t wide_cluster_size() {
   return cs;
 }
 
-int launch_track(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
+int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, cudaStream_t s) {
   switch (nt) {
     case 128: k_track<128><<<grid, 128, 0, s>>>(L); break;
     case 256: k_track<256><<<grid, 256, 0, s>>>(L); break;
     default: return VELO_EINVAL;
   }
-  const uint32_t cs = wide_cluster_size();
-  if (!cs) return VELO_ECUDA;
+  const uint32_t cs_max = wide_cluster_size();
+  if (!cs_max) return VELO_ECUDA;
+  if (wide_cluster > cs_max) return VELO_EINVAL;  // the device cannot place such a cluster
+  const uint32_t cs = wide_cluster ? wide_cluster : cs_max;
   // one wave: a cluster per cs SMs (one 1024-thread CTA per SM)
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

@@ -43,7 +43,8 @@ def test_every_block_shape_gives_the_same_bytes_and_the_oracle():
     o, p = dev(off, pix)
     ref = to_numpy(velo.reconstruct(o, p, geo, velo.default_params(), pixel_labels=True))
     for t in autotune.candidates() + [velo.default_tuning(cluster_threads=1024, cluster_smem_pixels=4096),
-                                      velo.default_tuning(cluster_threads=512, cluster_smem_pixels=2048)]:
+                                      velo.default_tuning(cluster_threads=512, cluster_smem_pixels=2048),
+                                      velo.default_tuning(wide_cluster=8), velo.default_tuning(wide_cluster=16)]:
         got = to_numpy(velo.reconstruct(o, p, geo, velo.default_params(), pixel_labels=True, tuning=t))
         for k in ref:
             np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{t.as_dict()} {k}")
