@@ -107,3 +107,22 @@ def test_autotuner_picks_a_verified_shape(tmp_path, monkeypatch):
     assert best.as_dict() == min(table, key=lambda x: x[1])[0]
     best2, _ = autotune.tune(o, p, geo, velo.default_params())  # from the cache
     assert best2.as_dict() == best.as_dict()
+
+
+def test_host_form_with_heavy_events():
+    """The pipelined host form (chunks with workspaces of their own, each
+    listing its heavy events) gives the bytes of the device form on a batch
+    with heavy-ion-like events, whatever the chunking."""
+    off, pix, geo = uneven_batch(n=90, seed=5)
+    o, p = dev(off, pix)
+    ref = to_numpy(velo.reconstruct(o, p, geo, velo.default_params(), pixel_labels=True))
+    H = velo.HostReconstructor(geo, velo.default_params(), max_events=len(off) - 1, max_pixels=len(pix),
+                               pixel_labels=True)
+    off_h = torch.from_numpy(off.view(np.int64)).pin_memory()
+    pix_h = torch.from_numpy(pix.view(np.int32)).pin_memory()
+    for chunks in (1, 3, 0):
+        H.set_chunks(chunks)
+        got = H.run(off_h, pix_h)
+        for k in ("status", "cluster_offsets", "cluster_x", "cluster_y", "cluster_z", "track_offsets",
+                  "track_hit_offsets", "track_hits", "track_states", "pixel_cluster"):
+            np.testing.assert_array_equal(np.asarray(got[k]), ref[k], err_msg=f"chunks {chunks} {k}")
