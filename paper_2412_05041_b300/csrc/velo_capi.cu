@@ -342,7 +342,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   mark(2);
   k_scan<<<1, kScanThreads, 0, s>>>(L);
   mark(3);
-  if (E) rc = launch_output(L, grid(output_blocks_per_sm()), s);
+  if (E) rc = launch_output(L, grid(output_blocks_per_sm(L.out.track_features != nullptr)), s);
   if (rc != VELO_OK) return rc;
   mark(4);
   return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;

@@ -106,7 +106,7 @@ uint32_t cluster_smem_bytes(int nt, uint32_t tier);
 uint32_t cluster_max_tier(int nt);
 int cluster_blocks_per_sm(int nt, uint32_t tier);
 int track_blocks_per_sm(int nt);
-int output_blocks_per_sm();
+int output_blocks_per_sm(bool features);
 
 // host helpers (velo_capi.cu): raise a kernel's dynamic shared-memory limit
 // once per device (slot = a small id per kernel instance; occupancy with

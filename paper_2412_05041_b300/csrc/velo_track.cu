@@ -88,6 +88,7 @@ struct TrackSmem {
 };
 
 constexpr int kFitThreads = 256;
+static_assert(VELO_STATE_STRIDE % 4 == 0, "states move in 16-byte pieces");
 
 struct FitSmem {
   uint32_t hit_fill;  // hit ids of the event's tracks staged so far
@@ -716,9 +717,10 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
       if (keep) {
         first_of[hid[ta[t]]] = t;
         if (P.use_mlp) st[19] = W.trk_logit[tb + t];
-        float* so = W.trk_state + (tb + t) * VELO_STATE_STRIDE;
+        float4* so = reinterpret_cast<float4*>(W.trk_state + (tb + t) * VELO_STATE_STRIDE);  // 16-byte aligned
 #pragma unroll
-        for (int k = 0; k < VELO_STATE_STRIDE; ++k) so[k] = st[k];
+        for (int k = 0; k < VELO_STATE_STRIDE / 4; ++k)
+          so[k] = make_float4(st[4 * k], st[4 * k + 1], st[4 * k + 2], st[4 * k + 3]);
         const uint32_t slot = atomicAdd(&S.hit_fill, n);
         W.trk_pick[tb + t] = slot;
         for (uint32_t j = 0; j < n; ++j) hit_stage[slot + j] = ids[j];
@@ -726,33 +728,58 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
     }
   }
   __syncthreads();
-  unsigned long long run = 0;
-  for (uint32_t base = 0; base < H; base += kFitThreads) {
-    const uint32_t id = base + tid;
-    uint32_t t = kNone;
-    unsigned long long v = 0;
-    if (id < H) {
-      t = first_of[id];
-      if (t != kNone) v = (1ull << 32) | (meta[t] & 255u);
+  // Ranks: kept tracks in the order of their first cluster id.  Every warp
+  // takes a contiguous chunk of the ids, 32 at a time (coalesced): ballots
+  // and a warp scan count its tracks and their hits, one block scan over the
+  // warps gives each chunk its first rank and first hit.
+  constexpr uint32_t NW = kFitThreads / 32;
+  const uint32_t lane = lane_id(), wid = warp_id();
+  const uint32_t cw = ((H + NW - 1) / NW + 31u) & ~31u;
+  const uint32_t wlo = min(H, wid * cw), whi = min(H, wlo + cw);
+  uint32_t wtr = 0, wht = 0;
+  for (uint32_t b0 = wlo; b0 < whi; b0 += 32) {
+    const uint32_t id = b0 + lane;
+    const uint32_t t = id < whi ? first_of[id] : kNone;
+    wtr += __popc(__ballot_sync(kFull, t != kNone));
+    wht += __reduce_add_sync(kFull, t != kNone ? meta[t] & 255u : 0u);
+  }
+  unsigned long long tot;
+  const unsigned long long ex = block_exclusive_scan<kFitThreads, unsigned long long>(
+      lane == 0 ? ((unsigned long long)wtr << 32) | wht : 0ull, &tot, S.tmp64);
+  uint32_t rr = (uint32_t)(__shfl_sync(kFull, ex, 0) >> 32), rh = (uint32_t)__shfl_sync(kFull, ex, 0);
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t b0 = wlo; b0 < whi; b0 += 32) {
+    const uint32_t id = b0 + lane;
+    const uint32_t t = id < whi ? first_of[id] : kNone;
+    const uint32_t nh = t != kNone ? meta[t] & 255u : 0u;
+    uint32_t x = nh;  // inclusive warp scan of the hit counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= (uint32_t)o) x += y;
     }
-    unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan<kFitThreads, unsigned long long>(v, &tot, S.tmp64) + run;
+    const uint32_t bal = __ballot_sync(kFull, t != kNone);
     if (t != kNone) {
-      rank[t] = (uint32_t)(ex >> 32);
-      hoff[t] = (uint32_t)ex;
+      rank[t] = rr + __popc(bal & lt);
+      hoff[t] = rh + x - nh;
     }
-    run += tot;
+    rr += __popc(bal);
+    rh += __shfl_sync(kFull, x, 31);
   }
   if (tid == 0) {
-    W.ev_ntracks[e] = (uint32_t)(run >> 32);
-    W.ev_nhits[e] = (uint32_t)run;
+    W.ev_ntracks[e] = (uint32_t)(tot >> 32);
+    W.ev_nhits[e] = (uint32_t)tot;
   }
 }
 
 // Compaction: clusters and kept tracks of event e into the caller's CSR
-// arrays (offsets from k_scan); the states are recomputed by the same fit.
+// arrays (offsets from k_scan).  Without features the states and hit ids are
+// the ones k_fit staged; with them (FEAT) every kept track is gathered and
+// fitted again for its features.
+template <bool FEAT>
 __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, uint32_t* mod_off, float* mz) {
   constexpr int NT = kOutputThreads;
+  constexpr int U = 4;  // cluster words in flight per thread
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
@@ -764,16 +791,39 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   __syncthreads();
   const uint32_t H = W.ev_nclusters[e];
   const uint64_t co = L.out.cluster_offsets[e];
-  for (uint32_t pos = tid; pos < H; pos += NT) {  // sorted hits -> clusters in id order
-    const uint32_t id = W.h_id[p0 + pos];
-    L.out.cluster_x[co + id] = W.h_x[p0 + pos];
-    L.out.cluster_y[co + id] = W.h_y[p0 + pos];
-    L.out.cluster_z[co + id] = mz[module_of_pos(mod_off, M, pos)];
+  // clusters in id order (coalesced stores), each read from its sorted
+  // position (h_pos: id -> position; the reads stay within the module's few
+  // cache lines); the loads of U ids are issued before their stores.  The
+  // module offsets hold for ids as for positions (the hit sort keeps every
+  // module's clusters together).
+  for (uint32_t id0 = tid; id0 < H; id0 += U * NT) {
+    float x[U], y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t id = id0 + u * NT;
+      if (id < H) {
+        const uint32_t pos = W.h_pos[p0 + id];
+        x[u] = W.h_x[p0 + pos];
+        y[u] = W.h_y[p0 + pos];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t id = id0 + u * NT;
+      if (id < H) {
+        L.out.cluster_x[co + id] = x[u];
+        L.out.cluster_y[co + id] = y[u];
+        L.out.cluster_z[co + id] = mz[module_of_pos(mod_off, M, id)];
+      }
+    }
   }
   const uint32_t nt = W.ev_ntracks_all[e];
   const uint64_t to = L.out.track_offsets[e];
   const uint64_t hb = W.ev_hitbase[e];
-  if (!L.out.track_features) {  // states and hit ids as k_fit staged them
+  if (!FEAT) {  // states and hit ids as k_fit staged them
+    // states in 16-byte pieces when the caller's array allows it (the
+    // workspace copy always does)
+    const bool v4 = (reinterpret_cast<uintptr_t>(L.out.track_states) & 15u) == 0u;
     for (uint32_t t = tid; t < nt; t += NT) {
       const uint32_t r = W.trk_rank[tb + t];
       if (r == kNone) continue;
@@ -784,8 +834,14 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
       for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = W.sa[p0 + slot + j];
       const float* si = W.trk_state + (tb + t) * VELO_STATE_STRIDE;
       float* o = L.out.track_states + dst * VELO_STATE_STRIDE;
+      if (v4) {
 #pragma unroll
-      for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = si[k];
+        for (int k = 0; k < VELO_STATE_STRIDE / 4; ++k)
+          reinterpret_cast<float4*>(o)[k] = reinterpret_cast<const float4*>(si)[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = si[k];
+      }
     }
     return;
   }
@@ -798,13 +854,11 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
     fit_track(n, xs, ys, zs, L.par.sigma, L.par.ms_theta, st);
     if (L.par.use_mlp) st[19] = W.trk_logit[tb + t];
     const uint64_t dst = to + r;
-    if (L.out.track_features) {
-      float f[VELO_N_FEATURES];
-      candidate_features(n, xs, ys, zs, mods, st, cut_chi2ndf(n, st, L.par.ms_theta), f);
-      float* of = L.out.track_features + dst * VELO_N_FEATURES;
+    float f[VELO_N_FEATURES];
+    candidate_features(n, xs, ys, zs, mods, st, cut_chi2ndf(n, st, L.par.ms_theta), f);
+    float* of = L.out.track_features + dst * VELO_N_FEATURES;
 #pragma unroll
-      for (int k = 0; k < VELO_N_FEATURES; ++k) of[k] = f[k];
-    }
+    for (int k = 0; k < VELO_N_FEATURES; ++k) of[k] = f[k];
     const uint64_t h0 = hb + W.trk_hoff[tb + t];
     L.out.track_hit_offsets[dst] = h0;
     for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = ids[j];
@@ -814,7 +868,11 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   }
 }
 
-__global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
+// Persistent: events from the work queue.  The plain form is small (eight
+// CTAs per SM keep more loads in flight); the form with features carries the
+// fit's arrays.
+template <bool FEAT>
+__global__ void __launch_bounds__(kOutputThreads, FEAT ? 1 : 6) k_output(Launch L) {
   __shared__ uint32_t mod_off[kModOffStride];
   __shared__ float mz[VELO_MAX_MODULES];
   __shared__ uint32_t next;
@@ -826,7 +884,7 @@ __global__ void __launch_bounds__(kOutputThreads) k_output(Launch L) {
     const uint32_t e = next;
     __syncthreads();
     if (e >= L.n_events) break;
-    output_one(L, e, mod_off, mz);
+    output_one<FEAT>(L, e, mod_off, mz);
     __syncthreads();
   }
 }
@@ -965,10 +1023,14 @@ int track_blocks_per_sm(int nt) {
 }
 
 int launch_output(const Launch& L, uint32_t grid, cudaStream_t s) {
-  k_output<<<grid, kOutputThreads, 0, s>>>(L);
+  if (L.out.track_features) k_output<true><<<grid, kOutputThreads, 0, s>>>(L);
+  else k_output<false><<<grid, kOutputThreads, 0, s>>>(L);
   return VELO_OK;
 }
 
-int output_blocks_per_sm() { return occupancy(reinterpret_cast<const void*>(k_output), kOutputThreads, 0, -1); }
+int output_blocks_per_sm(bool features) {
+  return features ? occupancy(reinterpret_cast<const void*>(k_output<true>), kOutputThreads, 0, -1)
+                  : occupancy(reinterpret_cast<const void*>(k_output<false>), kOutputThreads, 0, -1);
+}
 
 }  // namespace velo
