@@ -603,6 +603,13 @@ def run_ours(args):
         e2e = {"value": world * n_ev / el, "unit": UNIT, "h2d_bytes_per_step": int(8 * (n_ev + 1) + 4 * P),
                "d2h_bytes_per_step": int(H.bytes_out()), "ms_per_step": 1000 * el, "pipeline": "auto chunks",
                "serial_value": world * n_ev / el_serial}
+        # the same with tracks-only results (no cluster coordinates copied back)
+        del H
+        H = velo.HostReconstructor(b.geometry, vp, max_events=n_ev, max_pixels=P, clusters=False)
+        el_t = host_time(0)
+        e2e["tracks_only"] = {"value": world * n_ev / el_t, "d2h_bytes_per_step": int(H.bytes_out()),
+                              "ms_per_step": 1000 * el_t}
+        del H
 
     serving = None
     if world == 1 and not args.no_serving:

@@ -236,7 +236,9 @@ void velo_result_free(velo_result_t* result);
  * host.  Work starts after what `stream` holds at the call; the call
  * returns once every result is in the host buffers.  Page-locked host
  * buffers are needed for the overlap (pageable ones work, with the copies
- * serialised).  Only the used part of each output is copied back.  Offsets
+ * serialised).  Only the used part of each output is copied back; cluster_x,
+ * cluster_y and cluster_z may be NULL (the clusters are still found and
+ * tracked, their coordinates are not copied back: tracks-only results).  Offsets
  * that the device form rejects are passed to it unchanged, in one chunk, so
  * every event then fails as there.  velo_context_set_pipeline sets the most
  * chunks per call: 0 = automatic (about 12.6M pixel words per chunk, at most

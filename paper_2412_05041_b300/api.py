@@ -163,10 +163,12 @@ class HostReconstructor:
     """Host-memory form (``velo_reconstruct_host``): a library context owns the
     device buffers; inputs and outputs are pinned host tensors.  A batch is cut
     into up to `chunks` chunks of whole events (0 = the library's choice, 1 =
-    no overlap) whose copies overlap with the kernels of the others."""
+    no overlap) whose copies overlap with the kernels of the others.  With
+    ``clusters=False`` the cluster coordinates are not copied back (tracks,
+    their hit ids and the cluster offsets still are)."""
 
     def __init__(self, geometry, params=None, max_events: int = 1, max_pixels: int = 1, pixel_labels: bool = False,
-                 chunks: int = 0):
+                 chunks: int = 0, clusters: bool = True):
         self.geo = geometry_struct(geometry)
         self.params = params if params is not None else default_params()
         self.ctx = ctypes.c_void_p()
@@ -180,7 +182,9 @@ class HostReconstructor:
 
         self.status = pin(E, torch.int32)
         self.cluster_offsets = pin(E + 1, torch.int64)
-        self.cluster_x, self.cluster_y, self.cluster_z = (pin(s.cap_clusters, torch.float32) for _ in range(3))
+        self.clusters = bool(clusters)
+        self.cluster_x, self.cluster_y, self.cluster_z = (
+            (pin(s.cap_clusters, torch.float32) if self.clusters else None) for _ in range(3))
         self.pixel_cluster = pin(max_pixels, torch.int32) if pixel_labels else None
         self.track_offsets = pin(E + 1, torch.int64)
         self.track_hit_offsets = pin(s.cap_tracks + 1, torch.int64)
@@ -204,8 +208,8 @@ class HostReconstructor:
         """Host bytes the last call copied back (status, offsets, clusters, tracks)."""
         nc, nt, nh, _ = (int(v) for v in self.totals[:4])
         E = self.n_events
-        return 32 + 4 * E + 16 * (E + 1) + 12 * nc + 8 * (nt + 1) + 4 * nh + 4 * STATE_STRIDE * nt + (
-            4 * self.n_pixels if self.pixel_cluster is not None else 0)
+        return (32 + 4 * E + 16 * (E + 1) + (12 * nc if self.clusters else 0) + 8 * (nt + 1) + 4 * nh +
+                4 * STATE_STRIDE * nt + (4 * self.n_pixels if self.pixel_cluster is not None else 0))
 
     def run(self, offsets: torch.Tensor, pixels: torch.Tensor, stream=None) -> dict:
         """offsets (int64) and pixels (int32) in host memory, pinned for full copy speed."""
@@ -216,10 +220,11 @@ class HostReconstructor:
               "velo_reconstruct_host")
         self.n_events, self.n_pixels = E, P
         nc, nt, nh, nf = (int(v) for v in self.totals[:4])
-        r = dict(status=self.status[:E], cluster_offsets=self.cluster_offsets[:E + 1], cluster_x=self.cluster_x[:nc],
-                 cluster_y=self.cluster_y[:nc], cluster_z=self.cluster_z[:nc], track_offsets=self.track_offsets[:E + 1],
-                 track_hit_offsets=self.track_hit_offsets[:nt + 1], track_hits=self.track_hits[:nh],
-                 track_states=self.track_states[:nt], n_failed=nf)
+        r = dict(status=self.status[:E], cluster_offsets=self.cluster_offsets[:E + 1],
+                 track_offsets=self.track_offsets[:E + 1], track_hit_offsets=self.track_hit_offsets[:nt + 1],
+                 track_hits=self.track_hits[:nh], track_states=self.track_states[:nt], n_failed=nf)
+        if self.clusters:
+            r.update(cluster_x=self.cluster_x[:nc], cluster_y=self.cluster_y[:nc], cluster_z=self.cluster_z[:nc])
         if self.pixel_cluster is not None:
             r["pixel_cluster"] = self.pixel_cluster[:P]
         return r

@@ -216,6 +216,27 @@ def _host(a, dt):
     return torch.from_numpy(np.ascontiguousarray(a).view(dt)).pin_memory()
 
 
+def test_host_form_tracks_only():
+    """Without the cluster coordinates the host form returns the same tracks,
+    hit ids and offsets, and copies 12 bytes per cluster less."""
+    b = velogen.generate(velogen.C2, n_events=80, first_event=700)
+    vp, op = params(5e-4)
+    off, pix = _host(b.offsets, np.int64), _host(b.pixels, np.int32)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    H = velo.HostReconstructor(b.geometry, vp, max_events=80, max_pixels=len(b.pixels), chunks=3)
+    T = velo.HostReconstructor(b.geometry, vp, max_events=80, max_pixels=len(b.pixels), chunks=3, clusters=False)
+    g, t = H.run(off, pix), T.run(off, pix)
+    assert_same(g, r)
+    assert "cluster_x" not in t and T.cluster_x is None
+    for k, v in t.items():
+        if k == "n_failed":
+            assert v == g[k]
+        else:
+            assert torch.equal(v, g[k]), k
+    nc = int(g["cluster_offsets"][-1])
+    assert H.bytes_out() - T.bytes_out() == 12 * nc
+
+
 def test_host_form_chunks_agree_with_oracle():
     """The pipelined host form cuts a batch into chunks of whole events; the
     results (offsets moved to batch-wide values) must not depend on the cut."""
