@@ -5,8 +5,9 @@
 // clustering.  One CTA per event at a time (1024 threads and one CTA per SM,
 // or 512 threads and two; persistent, events from a work queue):
 //   1. load and validate the event's words (coalesced, 4 B per thread);
-//   2. stable sort by the 27-bit (module, row, col) key in shared memory:
-//      2 radix passes by (module, row), then each row by insertion;
+//   2. sort by the 27-bit (module, row, col) key in shared memory: one
+//      counting pass by (module, row) (2 radix passes where the counters do
+//      not fit), then each row by insertion;
 //   3. union-find over 8-connected neighbours found in the sorted array
 //      (they sit just before a word): every word links to its smallest
 //      earlier neighbour, and the few whose earlier neighbours are not
@@ -133,17 +134,62 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   uint32_t* A = PS ? region : W.sa + p0;
   uint32_t* B = PS ? region + n : W.sb + p0;
 
-  // 2. stable sort by (module, row, col).  Two LSD passes sort by (module,
-  // row) (A->B->A); the words of one row -- a few in a pile-up event -- then
-  // go in column order by a stable insertion sort, run by the thread that owns
-  // the row's first word.  Both steps are stable, so the array ends exactly as
-  // a stable sort by the full key leaves it.  If a row has more than
+  // 2. sort by (module, row, col).  First by (module, row): in shared memory,
+  // when a 16-bit counter per (module, row) fits after the two word arrays,
+  // by one counting pass (counts, their exclusive scan, and a scatter whose
+  // atomics give the words of a row their places in arbitrary order); else by
+  // two stable LSD passes (A->B->A).  Then the words of every row -- a few in
+  // a pile-up event -- go in column order by an insertion sort, run by the
+  // thread that owns the row's first word.  If a row has more than
   // kRowSortMax words, the whole array is sorted again by the full key (4
-  // passes; stable, from an order that still keeps equal keys in input order).
-  // (Events of kRowTable words or more -- dense modules, long rows -- take
-  // the full sort at once.)
+  // passes).  (Events of kRowTable words or more -- dense modules, long rows
+  // -- take the full sort at once.)  Words with equal keys (duplicates) may
+  // end in any order among themselves, and nothing that follows depends on
+  // it: they share one cluster, their charges add without order, and every
+  // label is found by key.
   bool long_row = !PS && n >= kRowTable;
-  if (!long_row) {
+  bool counted = false;
+  if constexpr (PS) {
+    const uint32_t nrow = L.geo.n_rows;
+    const uint32_t cw = (M * nrow + 1u) / 2u;  // u32 words of 16-bit counter pairs
+    if (n < 65536u && 2u * n + cw <= 2u * tier) {
+      counted = true;
+      uint32_t* C = region + 2 * n;
+      for (uint32_t q = tid; q < cw; q += NT) C[q] = 0u;
+      __syncthreads();
+      for (uint32_t i = tid; i < n; i += NT) {
+        const uint32_t w = A[i], b = ((w >> 22) & 31u) * nrow + ((w >> 11) & 2047u);
+        atomicAdd(C + (b >> 1), 1u << ((b & 1u) << 4));
+      }
+      __syncthreads();
+      // exclusive scan of the counts in (module, row) order: a chunk of an odd
+      // number of words per thread (no bank conflicts), one block scan
+      const uint32_t per = ((cw + NT - 1) / NT) | 1u;
+      const uint32_t q0 = min(cw, tid * per), q1 = min(cw, q0 + per);
+      uint32_t sum = 0;
+      for (uint32_t q = q0; q < q1; ++q) {
+        const uint32_t v = C[q];
+        sum += (v & 0xFFFFu) + (v >> 16);
+      }
+      uint32_t total;
+      uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &total, S.tmp);
+      for (uint32_t q = q0; q < q1; ++q) {  // prefixes < n < 2^16
+        const uint32_t v = C[q], lo = run, hi = run + (v & 0xFFFFu);
+        run = hi + (v >> 16);
+        C[q] = lo | hi << 16;
+      }
+      __syncthreads();
+      for (uint32_t i = tid; i < n; i += NT) {
+        const uint32_t w = A[i], b = ((w >> 22) & 31u) * nrow + ((w >> 11) & 2047u), sh = (b & 1u) << 4;
+        B[(atomicAdd(C + (b >> 1), 1u << sh) >> sh) & 0xFFFFu] = w;
+      }
+      __syncthreads();
+      uint32_t* t = A;  // the sorted words are in B: swap the roles
+      A = B;
+      B = t;
+    }
+  }
+  if (!long_row && !counted) {
     radix_pass<NT, false>(A, B, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
                           [](uint32_t k, uint32_t) { return ((k & kKeyMask) >> 11) & 255u; }, S.cnt, S.tmp);
     radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,

@@ -820,7 +820,7 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   const uint32_t nt = W.ev_ntracks_all[e];
   const uint64_t to = L.out.track_offsets[e];
   const uint64_t hb = W.ev_hitbase[e];
-  if (!FEAT) {  // states and hit ids as k_fit staged them
+  if constexpr (!FEAT) {  // states and hit ids as k_fit staged them
     // states in 16-byte pieces when the caller's array allows it (the
     // workspace copy always does)
     const bool v4 = (reinterpret_cast<uintptr_t>(L.out.track_states) & 15u) == 0u;
@@ -843,32 +843,32 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
         for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = si[k];
       }
     }
-    return;
-  }
-  for (uint32_t t = tid; t < nt; t += NT) {  // with the features: gathered and fitted again
-    const uint32_t r = W.trk_rank[tb + t];
-    if (r == kNone) continue;
-    float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
-    uint32_t ids[VELO_MAX_MODULES], mods[VELO_MAX_MODULES];
-    const uint32_t n = gather_track(W, p0, tb, t, mod_off, mz, M, xs, ys, zs, mods, ids);
-    fit_track(n, xs, ys, zs, L.par.sigma, L.par.ms_theta, st);
-    if (L.par.use_mlp) st[19] = W.trk_logit[tb + t];
-    const uint64_t dst = to + r;
-    float f[VELO_N_FEATURES];
-    candidate_features(n, xs, ys, zs, mods, st, cut_chi2ndf(n, st, L.par.ms_theta), f);
-    float* of = L.out.track_features + dst * VELO_N_FEATURES;
+  } else {
+    for (uint32_t t = tid; t < nt; t += NT) {  // with the features: gathered and fitted again
+      const uint32_t r = W.trk_rank[tb + t];
+      if (r == kNone) continue;
+      float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
+      uint32_t ids[VELO_MAX_MODULES], mods[VELO_MAX_MODULES];
+      const uint32_t n = gather_track(W, p0, tb, t, mod_off, mz, M, xs, ys, zs, mods, ids);
+      fit_track(n, xs, ys, zs, L.par.sigma, L.par.ms_theta, st);
+      if (L.par.use_mlp) st[19] = W.trk_logit[tb + t];
+      const uint64_t dst = to + r;
+      float f[VELO_N_FEATURES];
+      candidate_features(n, xs, ys, zs, mods, st, cut_chi2ndf(n, st, L.par.ms_theta), f);
+      float* of = L.out.track_features + dst * VELO_N_FEATURES;
 #pragma unroll
-    for (int k = 0; k < VELO_N_FEATURES; ++k) of[k] = f[k];
-    const uint64_t h0 = hb + W.trk_hoff[tb + t];
-    L.out.track_hit_offsets[dst] = h0;
-    for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = ids[j];
-    float* o = L.out.track_states + dst * VELO_STATE_STRIDE;
+      for (int k = 0; k < VELO_N_FEATURES; ++k) of[k] = f[k];
+      const uint64_t h0 = hb + W.trk_hoff[tb + t];
+      L.out.track_hit_offsets[dst] = h0;
+      for (uint32_t j = 0; j < n; ++j) L.out.track_hits[h0 + j] = ids[j];
+      float* o = L.out.track_states + dst * VELO_STATE_STRIDE;
 #pragma unroll
-    for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = st[k];
+      for (int k = 0; k < VELO_STATE_STRIDE; ++k) o[k] = st[k];
+    }
   }
 }
 
-// Persistent: events from the work queue.  The plain form is small (eight
+// Persistent: events from the work queue.  The plain form is small (six
 // CTAs per SM keep more loads in flight); the form with features carries the
 // fit's arrays.
 template <bool FEAT>
