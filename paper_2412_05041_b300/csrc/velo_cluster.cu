@@ -17,9 +17,11 @@
 //   4. cluster id = exclusive scan of root flags (canonical, order-free);
 //   5. integer charge sums per cluster with atomics (exact, so the order of
 //      the additions does not matter) and the binary32 centroid;
-//   6. pseudo-angle key and a stable block radix sort of the hits by
-//      (module, key, id): 3 passes over (module, 19-bit fixed-point key),
-//      then the rare runs of equal fixed-point keys by insertion.
+//   6. pseudo-angle key and the sort of the hits by (module, key, id): in
+//      shared memory one counting pass by (module, top 8 key bits) and an
+//      insertion sort of every bucket (about one hit); else a stable block
+//      radix sort, 3 passes over (module, 19-bit fixed-point key), then the
+//      rare runs of equal fixed-point keys by insertion.
 // Events larger than the shared-memory tier run the same code on their
 // slice of the global workspace (generic pointers).
 #include <type_traits>
@@ -43,7 +45,10 @@ struct ClusterSmem {
 };
 
 constexpr uint32_t kRootFlag = 0x80000000u;
-constexpr uint32_t kRowSortMax = 32;  // longest row sorted by insertion (else the full radix sort)
+constexpr uint32_t kRowSortMax = 32;
+// key buckets per module of the counting hit sort: 2^8 (about one hit each
+// at pile-up 5.5)
+constexpr uint32_t kHitBucketBits = 8;  // longest row sorted by insertion (else the full radix sort)
 // Events of at least this many words (kept in the workspace) index the first
 // sorted position of every (module, row): 32 modules x 2048 rows.
 constexpr uint32_t kRowTable = 1u << 16;
@@ -493,8 +498,8 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
 // sums), through shared memory when HS.
 template <int NT, bool HS>
 __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
-                                           const uint64_t p0, const uint32_t n, const uint32_t n_clusters,
-                                           const uint32_t* acc32) {
+                                           const uint32_t tier, const uint64_t p0, const uint32_t n,
+                                           const uint32_t n_clusters, const uint32_t* acc32) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
@@ -515,6 +520,20 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   float* ck = HS ? reinterpret_cast<float*>(W.sc + p0) : W.h_key + p0;
   const Geo& g = L.geo;
   const uint32_t* mo = S.mod_off;
+  // In shared memory, when 16-bit counters of 2^kHitBucketBits key buckets
+  // per module fit at the region's end (clear of the charge sums, which the
+  // centroid pass reads), the hit sort is one counting pass by (module, top
+  // key bits) and an insertion sort of every bucket -- about one hit each
+  // -- by (key, id).
+  const uint32_t cwh = (M << kHitBucketBits) / 2u;  // u32 words of 16-bit counter pairs
+  const uint32_t c0 = 2u * tier - cwh;
+  const bool counted = HS && n_clusters < 65536u && 2u * tier >= cwh && c0 >= 3u * n_clusters &&
+                       (acc32 != region + 2 * n || c0 >= 2u * n + 3u * n_clusters);
+  uint32_t* C = region + c0;
+  if (counted) {
+    for (uint32_t q = tid; q < cwh; q += NT) C[q] = 0u;
+    __syncthreads();
+  }
   for (uint32_t id = tid; id < n_clusters; id += NT) {
     float u, v;
     if (narrow) {
@@ -535,48 +554,99 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
     const float key = pseudo_angle(x, y);
     cx[id] = x;
     cy[id] = y;
-    ck[id] = key;
-    KA[id] = module_of(mo, M, id) << 19 | hit_key_fixed(key);
-    VA[id] = (V)id;
-  }
-  __syncthreads();
-
-  // 6. hits sorted by (module, key, id).  The ids enter in ascending order,
-  // and three stable LSD passes sort them by (module, fixed-point key): the
-  // fixed-point value never decreases with the key, so only hits of one
-  // module with equal fixed-point keys can still be out of (key, id) order;
-  // those runs (rare: a few per event) are put in order by insertion.
-  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k & 255u; }, S.cnt, S.tmp);
-  radix_pass<NT, true>(KB, KA, VB, VA, n_clusters, [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.cnt,
-                       S.tmp);
-  radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k >> 16; }, S.cnt, S.tmp);
-  for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
-    const uint32_t c = KB[pos];
-    if ((pos > 0 && KB[pos - 1] == c) || pos + 1 >= n_clusters || KB[pos + 1] != c) continue;
-    uint32_t end = pos + 2;  // this thread owns the run [pos, end)
-    while (end < n_clusters && KB[end] == c) ++end;
-    for (uint32_t a = pos + 1; a < end; ++a) {
-      const uint32_t id = VB[a];
-      const unsigned long long kv = (unsigned long long)__float_as_uint(ck[id]) << 32 | id;
-      uint32_t b = a;
-      for (; b > pos; --b) {
-        const uint32_t o = VB[b - 1];
-        if (((unsigned long long)__float_as_uint(ck[o]) << 32 | o) <= kv) break;
-        VB[b] = (V)o;
-      }
-      VB[b] = (V)id;
+    if (counted) {  // key bits and bucket (< 2^16) of every cluster
+      const uint32_t b = module_of(mo, M, id) << kHitBucketBits | hit_key_fixed(key) >> (19 - kHitBucketBits);
+      KA[id] = __float_as_uint(key);
+      VA[id] = (V)b;
+      atomicAdd(C + (b >> 1), 1u << ((b & 1u) << 4));
+    } else {
+      ck[id] = key;
+      KA[id] = module_of(mo, M, id) << 19 | hit_key_fixed(key);
+      VA[id] = (V)id;
     }
   }
   __syncthreads();
-  // the keys in sorted order through KA (dead after the last pass): in the
-  // global tier ck is h_key itself, read by id
-  for (uint32_t pos = tid; pos < n_clusters; pos += NT) KA[pos] = __float_as_uint(ck[VB[pos]]);
-  __syncthreads();
+  if (counted) {
+    // exclusive scan of the bucket counts (a chunk of an odd number of words
+    // per thread, one block scan), the scatter of (key, id) into KB, VB, and
+    // every bucket [end of the previous one, its end) in (key, id) order
+    const uint32_t per = ((cwh + NT - 1) / NT) | 1u;
+    const uint32_t q0 = min(cwh, tid * per), q1 = min(cwh, q0 + per);
+    uint32_t sum = 0;
+    for (uint32_t q = q0; q < q1; ++q) {
+      const uint32_t v = C[q];
+      sum += (v & 0xFFFFu) + (v >> 16);
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &total, S.tmp);
+    for (uint32_t q = q0; q < q1; ++q) {  // prefixes < n_clusters < 2^16
+      const uint32_t v = C[q], lo = run, hi = run + (v & 0xFFFFu);
+      run = hi + (v >> 16);
+      C[q] = lo | hi << 16;
+    }
+    __syncthreads();
+    for (uint32_t id = tid; id < n_clusters; id += NT) {
+      const uint32_t b = VA[id], sh = (b & 1u) << 4;
+      const uint32_t slot = (atomicAdd(C + (b >> 1), 1u << sh) >> sh) & 0xFFFFu;
+      KB[slot] = KA[id];
+      VB[slot] = (V)id;
+    }
+    __syncthreads();
+    for (uint32_t b = tid; b < 2u * cwh; b += NT) {  // C now holds every bucket's end
+      const uint32_t end = (C[b >> 1] >> ((b & 1u) << 4)) & 0xFFFFu;
+      const uint32_t beg = b ? (C[(b - 1) >> 1] >> (((b - 1) & 1u) << 4)) & 0xFFFFu : 0u;
+      for (uint32_t a = beg + 1; a < end; ++a) {
+        const uint32_t ka = KB[a];
+        const V va = VB[a];
+        uint32_t q = a;
+        for (; q > beg && (KB[q - 1] > ka || (KB[q - 1] == ka && VB[q - 1] > va)); --q) {
+          KB[q] = KB[q - 1];
+          VB[q] = VB[q - 1];
+        }
+        KB[q] = ka;
+        VB[q] = va;
+      }
+    }
+    __syncthreads();
+  } else {
+    // 6. hits sorted by (module, key, id).  The ids enter in ascending order,
+    // and three stable LSD passes sort them by (module, fixed-point key): the
+    // fixed-point value never decreases with the key, so only hits of one
+    // module with equal fixed-point keys can still be out of (key, id) order;
+    // those runs (rare: a few per event) are put in order by insertion.
+    radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k & 255u; }, S.cnt, S.tmp);
+    radix_pass<NT, true>(KB, KA, VB, VA, n_clusters, [](uint32_t k, uint32_t) { return (k >> 8) & 255u; }, S.cnt,
+                         S.tmp);
+    radix_pass<NT, true>(KA, KB, VA, VB, n_clusters, [](uint32_t k, uint32_t) { return k >> 16; }, S.cnt, S.tmp);
+    for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
+      const uint32_t c = KB[pos];
+      if ((pos > 0 && KB[pos - 1] == c) || pos + 1 >= n_clusters || KB[pos + 1] != c) continue;
+      uint32_t end = pos + 2;  // this thread owns the run [pos, end)
+      while (end < n_clusters && KB[end] == c) ++end;
+      for (uint32_t a = pos + 1; a < end; ++a) {
+        const uint32_t id = VB[a];
+        const unsigned long long kv = (unsigned long long)__float_as_uint(ck[id]) << 32 | id;
+        uint32_t b = a;
+        for (; b > pos; --b) {
+          const uint32_t o = VB[b - 1];
+          if (((unsigned long long)__float_as_uint(ck[o]) << 32 | o) <= kv) break;
+          VB[b] = (V)o;
+        }
+        VB[b] = (V)id;
+      }
+    }
+    __syncthreads();
+    // the keys in sorted order through KA (dead after the last pass): in the
+    // global tier ck is h_key itself, read by id
+    for (uint32_t pos = tid; pos < n_clusters; pos += NT) KA[pos] = __float_as_uint(ck[VB[pos]]);
+    __syncthreads();
+  }
+  const uint32_t* KS = counted ? KB : KA;  // the keys (bits) in sorted order
   for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
     const uint32_t id = VB[pos];
     W.h_x[p0 + pos] = cx[id];
     W.h_y[p0 + pos] = cy[id];
-    W.h_key[p0 + pos] = __uint_as_float(KA[pos]);
+    W.h_key[p0 + pos] = __uint_as_float(KS[pos]);
     W.h_id[p0 + pos] = id;
     W.h_pos[p0 + id] = pos;
   }
@@ -629,8 +699,8 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n, &sums)
                                         : pixel_phases<NT, false>(L, e, S, region, tier, p0, n, &sums);
   if (n_clusters == kNone) return;
-  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, p0, n, n_clusters, sums);
-  else hit_phases<NT, false>(L, e, S, region, p0, n, n_clusters, sums);
+  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, tier, p0, n, n_clusters, sums);
+  else hit_phases<NT, false>(L, e, S, region, tier, p0, n, n_clusters, sums);
 }
 
 // Persistent: every CTA takes events from the work queue until it is empty,
