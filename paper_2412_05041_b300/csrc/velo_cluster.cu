@@ -200,22 +200,45 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
                           [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 19; }, S.cnt, S.tmp);
   }
-  for (uint32_t pos = tid; pos < n && !(!PS && n >= kRowTable); pos += NT) {
-    // rows only permute inside themselves, so another thread's sort never
-    // changes the (module, row) read here
-    const uint32_t mr = (A[pos] & kKeyMask) >> 11;
-    if (pos > 0 && ((A[pos - 1] & kKeyMask) >> 11) == mr) continue;  // not the row's first word
-    uint32_t end = pos + 1;
-    while (end < n && end - pos <= kRowSortMax && ((A[end] & kKeyMask) >> 11) == mr) ++end;
-    if (end - pos > kRowSortMax) {
-      long_row = true;
-      continue;
+  // Every warp takes 32 consecutive words at a time.  A row that starts and
+  // ends among them is ordered by the warp at once: each word's place is the
+  // row's first lane plus the number of the row's words with a smaller key,
+  // or an equal key in a lower lane (the row's lanes are contiguous).  A row
+  // that goes on past the 32 words is sorted by insertion, by the thread that
+  // owns its first word.  Rows only permute inside themselves, so the rows
+  // read next to a window never change while others sort theirs.
+  for (uint32_t pos0 = tid & ~31u; pos0 < n && !(!PS && n >= kRowTable); pos0 += NT) {
+    const uint32_t lane = lane_id(), pos = pos0 + lane;
+    const bool valid = pos < n;
+    const uint32_t w = valid ? A[pos] : 0u, k = w & kKeyMask;
+    const uint32_t mr = valid ? k >> 11 : 0x80000000u | lane;  // invalid lanes match nothing
+    const uint32_t same = __match_any_sync(kFull, mr);
+    const uint32_t first = __ffs(same) - 1u, cnt = __popc(same);
+    const bool starts = first > 0u || pos0 == 0u || ((A[pos0 - 1] & kKeyMask) >> 11) != mr;
+    const bool ends = first + cnt < 32u || pos0 + 32u >= n || ((A[pos0 + 32] & kKeyMask) >> 11) != mr;
+    const bool inside = valid && starts && ends;
+    const uint32_t rounds = __reduce_max_sync(kFull, inside ? cnt : 0u);
+    uint32_t at = first;
+    for (uint32_t t = 0; t < rounds; ++t) {
+      const uint32_t j = t < cnt ? first + t : lane;
+      const uint32_t kj = __shfl_sync(kFull, k, j);
+      at += t < cnt && (kj < k || (kj == k && j < lane));
     }
-    for (uint32_t a = pos + 1; a < end; ++a) {
-      const uint32_t w = A[a], k = w & kKeyMask;
-      uint32_t b = a;
-      for (; b > pos && (A[b - 1] & kKeyMask) > k; --b) A[b] = A[b - 1];
-      A[b] = w;
+    __syncwarp();
+    if (inside && cnt > 1u) A[pos0 + at] = w;
+    if (valid && starts && !ends && lane == first) {  // the row goes on past the window
+      uint32_t end = pos + 1;
+      while (end < n && end - pos <= kRowSortMax && ((A[end] & kKeyMask) >> 11) == mr) ++end;
+      if (end - pos > kRowSortMax) {
+        long_row = true;
+      } else {
+        for (uint32_t a = pos + 1; a < end; ++a) {
+          const uint32_t wa = A[a], ka = wa & kKeyMask;
+          uint32_t b = a;
+          for (; b > pos && (A[b - 1] & kKeyMask) > ka; --b) A[b] = A[b - 1];
+          A[b] = wa;
+        }
+      }
     }
   }
   if (__syncthreads_or(long_row)) {
@@ -313,39 +336,35 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
       }
     }
   } else {
+    // Every earlier word j in reach has d = k - key(j) <= span = k - lo_all;
+    // d = 0 is a duplicate, 1 the left neighbour (c > 0), 2047 / 2048 / 2049
+    // the previous row's columns c+1 (c+1 < n_cols), c, c-1 (c > 0): bits 0-4
+    // of `seen` (a previous row is in reach only when r > 0).
     for (uint32_t i = tid; i < n; i += NT) {
       const uint32_t k = A[i] & kKeyMask;
       const uint32_t c = k & 2047u, r = (k >> 11) & 2047u;
-      const uint32_t lo_k = r > 0u ? k - 2048u - (c > 0u ? 1u : 0u) : 0u;
-      const uint32_t hi_k = r > 0u ? k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u) : 0u;
-      const uint32_t lo_all = r > 0u ? lo_k : (c > 0u ? k - 1u : k);
-      bool done = false, dup = false, left = false, up_left = false, up = false, up_right = false;
-      uint32_t nb_min = i;
-      int64_t j = (int64_t)i - 1;
-      for (int steps = 0; steps < 16; ++steps, --j) {
-        if (j < 0) {
+      const uint32_t span = r > 0u ? 2048u + (c > 0u ? 1u : 0u) : (c > 0u ? 1u : 0u);
+      const uint32_t allow = 9u | (c > 0u ? 18u : 0u) | (c + 1u < L.geo.n_cols ? 4u : 0u);
+      bool done = false;
+      uint32_t seen = 0, nb_min = i, j = i;
+      for (int steps = 0; steps < 16; ++steps) {
+        if (j == 0u) {
           done = true;
           break;
         }
-        const uint32_t kj = A[j] & kKeyMask;
-        if (kj < lo_all) {
+        --j;
+        const uint32_t d = k - (A[j] & kKeyMask);
+        if (d > span) {
           done = true;
           break;
         }
-        const bool is_dup = kj == k, is_left = c > 0u && kj == k - 1u;
-        const bool is_prev = r > 0u && kj >= lo_k && kj <= hi_k;
-        if (is_dup || is_left || is_prev) nb_min = (uint32_t)j;  // scanning down: the last one found is the smallest
-        dup |= is_dup;
-        left |= is_left;
-        if (is_prev) {
-          const uint32_t pc = kj & 2047u;  // previous-row column c-1, c or c+1
-          up_left |= pc + 1u == c;
-          up |= pc == c;
-          up_right |= pc == c + 1u;
-        }
+        const uint32_t bit = (d <= 1u ? 1u << d : (d - 2047u <= 2u ? 4u << (d - 2047u) : 0u)) & allow;
+        if (bit) nb_min = j;  // scanning down: the last one found is the smallest
+        seen |= bit;
       }
       B[i] = nb_min;
-      if (!done || (up_right && !up && (left || up_left) && !dup)) A[i] |= 0x80000000u;
+      // the V shape: up-right without up, with left or up-left, no duplicate
+      if (!done || ((seen & 29u) == 4u + (seen & 16u) && (seen & 18u) != 0u)) A[i] |= 0x80000000u;
     }
     __syncthreads();
     for (uint32_t i = tid; i < n; i += NT) {
