@@ -28,8 +28,9 @@ struct Carver {
 void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   const uint64_t T = P / 3 + 1;
   ws->flag = c.take<uint32_t>(4);
-  ws->queue = c.take<uint32_t>(4);
+  ws->queue = c.take<uint32_t>(8);
   ws->wide_list = c.take<uint32_t>(E);
+  ws->order = c.take<uint32_t>(E);
   ws->ev_nclusters = c.take<uint32_t>(E);
   ws->ev_modoff = c.take<uint32_t>(E * kModOffStride);
   ws->ev_ntracks_all = c.take<uint32_t>(E);

@@ -736,6 +736,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cluster(Launch L) {
     __syncthreads();
     if (e >= L.n_events) break;
     cluster_one<NT>(L, e, S, region, L.cluster_tier);
+    if (threadIdx.x == 0) {  // the event's place in the tracking order (its count was written by this thread)
+      const bool large = L.ws.ev_nclusters[e] >= kLargeEvent;
+      const uint32_t at =
+          large ? atomicAdd(L.ws.queue + 4, 1u) : (uint32_t)L.n_events - 1u - atomicAdd(L.ws.queue + 5, 1u);
+      L.ws.order[at] = e;
+    }
     __syncthreads();
   }
 }

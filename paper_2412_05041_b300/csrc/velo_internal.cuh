@@ -22,6 +22,10 @@ constexpr uint32_t kModOffStride = 33;  // per-event module offsets, n_modules +
 // and more) are tracked by clusters of CTAs (k_track_wide), listed by the
 // clustering kernel in wide_list (count in queue[3]).
 constexpr uint32_t kWideClusters = 20000;
+// The tracking kernel takes the events of at least this many clusters first
+// (listed at the front of `order` by the clustering kernel, the others from
+// the back), so that the last CTAs to start are small events.
+constexpr uint32_t kLargeEvent = 8192;
 
 // Per-track metadata word: n_hits (8 bits) | active (1 bit) << 8 |
 // module of the last (most upstream) hit << 16 | module of the one before << 24.
@@ -33,8 +37,10 @@ constexpr uint32_t kTrkActive = 1u << 8;
 // event has at most n_e clusters and n_e / 3 tracks, so slices never overlap.
 struct Workspace {
   uint32_t* flag;            // [1] offsets invalid
-  uint32_t* queue;           // [4] work-queue counters of the persistent kernels; [3] wide_list count
+  uint32_t* queue;           // [8] work-queue counters of the persistent kernels; [3] wide_list count,
+                             // [4] / [5] events listed at the front / back of order
   uint32_t* wide_list;       // [E] events of kWideClusters clusters or more (any order)
+  uint32_t* order;           // [E] events in the tracking kernel's order: kLargeEvent clusters or more first
   uint32_t* ev_nclusters;    // [E]
   uint32_t* ev_modoff;       // [E * 33] cluster-id (= sorted position) offsets per module
   uint32_t* ev_ntracks_all;  // [E] tracks built (kept or not)

@@ -624,10 +624,11 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 // registers: with the fit in a kernel of its own (k_fit), 8 CTAs of 256
 // threads per SM (32 registers, a few bytes spilled) measured 8 % faster
 // than 6 (40 registers), which was 6 % faster than 5 and 8 % faster than 4.
+// CTA b tracks event order[b]: the large events start first.
 template <int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   __shared__ TrackSmem<NT> S;
-  track_one<NT, false>(L, blockIdx.x, S, nullptr, nullptr);
+  track_one<NT, false>(L, L.ws.order[blockIdx.x], S, nullptr, nullptr);
 }
 
 // The heavy events: one wave of clusters of CTAs of kWideThreads threads
@@ -944,7 +945,7 @@ __global__ void __launch_bounds__(kScanThreads) k_validate_offsets(Launch L) {
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     *L.ws.flag = bad ? 1u : 0u;
-    for (int q = 0; q < 4; ++q) L.ws.queue[q] = 0u;  // the persistent kernels' work queues
+    for (int q = 0; q < 8; ++q) L.ws.queue[q] = 0u;  // the persistent kernels' work queues
   }
   if (bad) {
     for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.out.status[e] = VELO_EVT_BADWORD;
