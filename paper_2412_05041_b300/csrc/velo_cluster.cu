@@ -212,8 +212,13 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     const bool valid = pos < n;
     const uint32_t w = valid ? A[pos] : 0u, k = w & kKeyMask;
     const uint32_t mr = valid ? k >> 11 : 0x80000000u | lane;  // invalid lanes match nothing
-    const uint32_t same = __match_any_sync(kFull, mr);
-    const uint32_t first = __ffs(same) - 1u, cnt = __popc(same);
+    // the row's lanes are contiguous: a ballot of the lanes that start a
+    // group (a row other than the lane below's) bounds every lane's row
+    const uint32_t below = __shfl_up_sync(kFull, mr, 1);
+    const uint32_t heads = __ballot_sync(kFull, lane == 0u || below != mr);
+    const uint32_t upto = lane == 31u ? kFull : (2u << lane) - 1u;
+    const uint32_t first = 31u - __clz(heads & upto), above = heads & ~upto;
+    const uint32_t cnt = (above ? (uint32_t)__ffs(above) - 1u : 32u) - first;
     const bool starts = first > 0u || pos0 == 0u || ((A[pos0 - 1] & kKeyMask) >> 11) != mr;
     const bool ends = first + cnt < 32u || pos0 + 32u >= n || ((A[pos0 + 32] & kKeyMask) >> 11) != mr;
     const bool inside = valid && starts && ends;
