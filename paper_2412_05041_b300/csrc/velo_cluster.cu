@@ -699,6 +699,15 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   const uint32_t n = (uint32_t)(p1 - p0);
   if (tid == 0) S.flag = offsets_ok ? 0u : 1u;
   if (tid < VELO_MAX_MODULES) S.mod_count[tid] = kNone;
+  // the words of event e + gridDim.x (taken, most likely, in the next round
+  // by some CTA) into L2 meanwhile, one 128-byte line per thread at a time
+  // (the offsets are valid: every range lies inside the pixel array)
+  if (offsets_ok && e + gridDim.x < L.n_events) {
+    const uint64_t q0 = L.off[e + gridDim.x], q1 = L.off[e + gridDim.x + 1];
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(L.pix + q0) & ~uintptr_t(127);
+    const uintptr_t a1 = reinterpret_cast<uintptr_t>(L.pix + q1);
+    for (uintptr_t a = a0 + 128u * tid; a < a1; a += 128u * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
   __syncthreads();
 
   // 1. load + validate
