@@ -21,7 +21,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ("test_oracle_cluster.py", "test_oracle_fit.py", "test_oracle_track.py", "test_oracle_mlp.py",
-             "test_oracle_forward.py")
+             "test_oracle_forward.py", "test_oracle_bruteforce.py")
 
 # (name, exact source text, replacement): each text occurs once in velo_oracle.cpp
 MUTATIONS = [
@@ -63,6 +63,13 @@ MUTATIONS = [
      "(s == best.s && (h0 < best.h0 ||", "(s == best.s && (h0 > best.h0 ||"),
     ("seeding uses used h0",
      "        if (used[h0]) continue;\n", ""),
+    ("seeding h2 window measured from h0",
+     "if (dmod4(H.key[h2], H.key[h1]) > p->win_seed) continue;",
+     "if (dmod4(H.key[h2], H.key[h0]) > p->win_seed) continue;"),
+    ("seeding scatter against the extension cut",
+     "if (s > p->max_scatter_seed) continue;", "if (s > p->max_scatter_fwd) continue;"),
+    ("extension window centred on the older hit",
+     "if (dmod4(H.key[h], H.key[a]) > p->win_fwd) continue;", "if (dmod4(H.key[h], H.key[b]) > p->win_fwd) continue;"),
     ("seed survives without its h2 claim",
      "if (sclaim[s.h0] != k || sclaim[s.h2] != k) continue;", "if (sclaim[s.h0] != k) continue;"),
     ("bfloat16 rounding half away from zero",
