@@ -185,7 +185,7 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
   const uint64_t E = ev->n_events, P = ev->n_pixels;
   const uint64_t* off = ev->event_offsets;
 
-  // ---- chunks of whole events with about equal word counts, and their workspace regions
+  // ---- chunks of whole events (the middle ones of about equal word counts), their workspace regions
   const bool valid = offsets_valid(off, E, P);
   uint32_t K = c->max_chunks;
   if (K == 0)
@@ -202,7 +202,10 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
       q.e0 = k ? ch[k - 1].e1 : 0;
       q.e1 = E;
       if (k + 1 < K) {
-        const uint64_t target = (P * (k + 1) + K - 1) / K;
+        // word shares 1 : 2 : ... : 2 : 1 (K >= 3): a short first chunk starts the
+        // kernels early, a short last chunk leaves little to copy out at the end
+        const uint64_t parts = K >= 3 ? 2ull * K - 2 : K, upto = K >= 3 ? 2ull * k + 1 : k + 1;
+        const uint64_t target = (P * upto + parts - 1) / parts;
         uint64_t e1 = (uint64_t)(std::lower_bound(off, off + E + 1, target) - off);
         e1 = std::max(e1, q.e0 + 1);                   // at least one event
         q.e1 = std::min(e1, E - (uint64_t)(K - 1 - k));  // and one for every later chunk
