@@ -33,10 +33,13 @@
 namespace {
 
 constexpr uint32_t kMaxChunks = 64;
-// automatic chunking: about this many pixel words per chunk, at most kAutoMaxChunks chunks (on 10k
-// pile-up-5.5 events, 125M words, 10 chunks measured best: 28.1 ms against 29.6 at 8 and 29.1 at 16)
+// automatic chunking: about this many pixel words per chunk, at most kAutoMaxChunks chunks.  On 10k
+// pile-up-5.5 events (125M words, half-size first and last chunks) tracks-only results measured best
+// at 10 chunks (18.7 ms against 19.0 at 6, 8 and 12, 21.2 at 16), full results (three times the
+// bytes out) at 12 (25.1 ms against 25.6 at 10, 26.1 at 8 and 26.6 at 20)
 constexpr uint32_t kAutoMaxChunks = 12;
-constexpr uint64_t kAutoChunkWords = 12ull << 20;
+constexpr uint64_t kAutoChunkWords = 12ull << 20;          // tracks only
+constexpr uint64_t kAutoChunkWordsClusters = 10ull << 20;  // with cluster coordinates
 // chunk k's kernels start once chunk k-1's clustering is done (stage mark 1):
 // chunk k's clustering then fills the SMs that chunk k-1's tracking tail
 // leaves idle, but never competes with chunk k-1's clustering, so chunks
@@ -188,9 +191,10 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
   // ---- chunks of whole events (the middle ones of about equal word counts), their workspace regions
   const bool valid = offsets_valid(off, E, P);
   uint32_t K = c->max_chunks;
-  if (K == 0)
-    K = (uint32_t)std::min<uint64_t>(kAutoMaxChunks,
-                                     std::max<uint64_t>(1, (P + kAutoChunkWords - 1) / kAutoChunkWords));
+  if (K == 0) {
+    const uint64_t per = ho->cluster_x || ho->cluster_y || ho->cluster_z ? kAutoChunkWordsClusters : kAutoChunkWords;
+    K = (uint32_t)std::min<uint64_t>(kAutoMaxChunks, std::max<uint64_t>(1, (P + per - 1) / per));
+  }
   if (!valid) K = 1;
   K = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(K, E));
   Chunk ch[kMaxChunks];
