@@ -663,6 +663,16 @@ def run_ours(args):
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None if traffic is None else traffic * n_ev,
             "peak_source": f"{peak_kind} hbm_gbs (copy)", "stage_ms": stage_ms}
+    # DRAM bytes per second measured by ncu (bytes per event of the committed
+    # summaries, current sources only) over the live times: of the dominant
+    # stage (the tracking stage holds k_track and k_fit) and of the whole step
+    dram = {k: profiled_traffic(k) for k in ("k_cluster", "k_track", "k_fit", "k_output")}
+    stage_kernels = {"k_track": ("k_track", "k_fit")}.get(dom, (dom,))
+    if all(dram.get(k) is not None for k in stage_kernels):
+        roof["dram_gbs"] = sum(dram[k] for k in stage_kernels) * n_ev / (stage_ms[dom] / 1000.0) / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / peaks["hbm_gbs"]
+    if all(v is not None for v in dram.values()):
+        roof["step_dram_gbs"] = sum(dram.values()) * n_ev / (ms / 1000.0) / 1e9
     # second ceiling: the plain FP32 pipe (measured on this GPU), with the busy
     # fractions of the dominant kernel's FMA and ALU pipes from its ncu summary
     fma = profiled_metric(dom, "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active")
