@@ -16,6 +16,7 @@ result being on the host (p50 / p99).
 """
 from __future__ import annotations
 
+import gc
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -116,9 +117,24 @@ class Server:
         slot.done_evt = evt
         slot.phase = 2
 
-    def run(self, requests: list, poll_sleep: float = 0.0) -> dict:
+    def run(self, requests: list, poll_sleep: float = 0.0, freeze_gc: bool = True) -> dict:
         """Serve `requests` (arrival times in seconds from now).  Returns statistics;
-        every request's result dict (host tensors) is left in request.result."""
+        every request's result dict (host tensors) is left in request.result.
+
+        With `freeze_gc` the objects that exist when serving starts are moved out
+        of the interpreter's cyclic collector (gc.freeze) until it ends: a full
+        collection over a large heap stalls the loop for tens of milliseconds,
+        which lands on the latency of every request in flight."""
+        if freeze_gc:
+            gc.collect()
+            gc.freeze()
+        try:
+            return self._serve(requests, poll_sleep)
+        finally:
+            if freeze_gc:
+                gc.unfreeze()
+
+    def _serve(self, requests: list, poll_sleep: float) -> dict:
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         t0 = time.perf_counter()
         waiting = deque()
