@@ -50,7 +50,8 @@ enum {
   VELO_EINVAL = 1,     /* bad argument: NULL where a pointer is required, bad geometry or params */
   VELO_ECAPACITY = 2,  /* a caller buffer or workspace is smaller than velo_query_sizes asked for */
   VELO_ECUDA = 3,      /* a CUDA runtime call failed (the CUDA error is not cleared) */
-  VELO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+  /* 4 is not used: a bounded device-side loop that gives up fails its event
+     (VELO_EVT_TIMEOUT), not the call */
   VELO_ENOMEM = 5      /* a library allocation failed (only the allocating entry points) */
 };
 
@@ -58,7 +59,9 @@ enum {
 enum {
   VELO_EVT_OK = 0,
   VELO_EVT_BADWORD = 1,  /* a pixel word has bit 31 set, q = 0, or module/row/col outside the geometry */
-  VELO_EVT_OVERFLOW = 2  /* a module has more than VELO_MAX_MODULE_CLUSTERS clusters */
+  VELO_EVT_OVERFLOW = 2, /* a module has more than VELO_MAX_MODULE_CLUSTERS clusters */
+  VELO_EVT_TIMEOUT = 3   /* the clustering's lock-free union-find gave up after its bounded link
+                            attempts (velo_tuning_t.union_link_attempts; not expected at the default) */
 };
 /* A failed event contributes no cluster and no track; the other events are unaffected. */
 
@@ -154,13 +157,21 @@ typedef struct velo_sizes {
 } velo_sizes_t;
 
 /* Fill *p with the standard parameters (win 0.04, slope 0.3, scatter 0.01 /
- * 0.02 mm^2, 1 skipped module, sigma 0.0159 mm, 0.5 mrad, cuts 10 and 2). */
+ * 0.02 mm^2, 1 skipped module, sigma 0.0159 mm, 0.5 mrad, cuts 10 and 2).
+ * Passage: Sec. "HLT1 details and results" names the pattern recognition,
+ * the parameterised Kalman filter and the track-quality cut these values
+ * steer; the paper prints none of the values (they are this library's,
+ * tuned on simulated events).  VELO_EINVAL for a NULL p. */
 int velo_params_default(velo_params_t* p);
 
 /* Sizes for a batch (host arithmetic only; no device call). */
 int velo_query_sizes(uint64_t n_events, uint64_t n_pixels, velo_sizes_t* out);
 
 /* Reconstruct a device-resident batch into caller-owned device buffers.
+ * Passage: Sec. "HLT1 details and results" (simplified pattern recognition
+ * and a parameterised Kalman filter on the pixel-tracker segment of each
+ * track) for what is computed; Sec. "Data flow overview" (every event
+ * reconstructed, events independent) for the batching.
  * events->event_offsets/pixels and every output pointer are device pointers;
  * geometry->module_z is a host pointer (copied into the launch arguments).
  * workspace: device, >= sizes.workspace_bytes, 256-byte aligned, contents
@@ -184,7 +195,8 @@ int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometr
 /* Block shapes of the persistent kernels (events of any size are spread over
  * the SMs by work queues; these choose how).  Any valid setting gives the same
  * results bit for bit; speed depends on the workload (autotuned by the Python
- * layer).  velo_tuning_default: 1024 / largest tier / 256 / all resident / 0. */
+ * layer).  velo_tuning_default: 1024 / largest tier / 256 / all resident / 0 /
+ * 2^20; start from it (a zeroed struct is rejected with VELO_EINVAL). */
 typedef struct velo_tuning {
   uint32_t cluster_threads;      /* 512 (two CTAs per SM) or 1024 (one) */
   uint32_t cluster_smem_pixels;  /* words per event sorted in shared memory, 0 = the most that fits;
@@ -197,6 +209,12 @@ typedef struct velo_tuning {
   uint32_t wide_cluster;         /* CTAs (a thread-block cluster of 1024-thread CTAs) tracking each event of
                                     20000 clusters or more: 0 = the largest the device can place (16, else
                                     8), or 8 or 16 (VELO_EINVAL if the device cannot place it) */
+  uint32_t union_link_attempts;  /* most link attempts of one union in the clustering's lock-free
+                                    union-find before it gives up and its event fails with
+                                    VELO_EVT_TIMEOUT (an attempt retries only after losing a race to
+                                    another union, so the default 2^20 is never reached); 0 = a
+                                    union that still has to link two trees gives up at once (a test
+                                    setting: it fails exactly the events that need such a union) */
 } velo_tuning_t;
 #define VELO_CTAS_PER_EVENT 0xFFFFFFFFu
 int velo_tuning_default(velo_tuning_t* t);
@@ -207,7 +225,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
                                 const velo_tuning_t* tuning);
 
 /* The same with library-owned results (the form of the call that returns
- * "tracks"): allocates the output buffers and the workspace on `stream`
+ * "tracks"; passage as velo_reconstruct_into): allocates the output buffers and the workspace on `stream`
  * with cudaMallocAsync and returns an opaque handle in *result.  The handle
  * is valid immediately; its contents once `stream` reaches this point. */
 typedef struct velo_result velo_result_t;
@@ -218,8 +236,12 @@ typedef struct velo_result_view {
 } velo_result_view_t;
 int velo_reconstruct(const velo_events_t* events, const velo_geometry_t* geometry,
                      const velo_params_t* params, velo_result_t** result, void* stream);
+/* The device pointers and capacities of a result (the tracks and clusters of
+ * Sec. "HLT1 details and results" in the velo_output_t layout above), owned
+ * by the result: valid until velo_result_free.  VELO_EINVAL for NULL. */
 int velo_result_view(const velo_result_t* result, velo_result_view_t* view);
-/* Frees the result's buffers on its stream (stream-ordered; no host wait). */
+/* Frees the result's buffers on its stream (stream-ordered; no host wait).
+ * NULL is ignored.  No counterpart in the paper (memory ownership only). */
 void velo_result_free(velo_result_t* result);
 
 /* Host-buffer form, for callers whose events sit in host memory: a context
@@ -240,10 +262,16 @@ void velo_result_free(velo_result_t* result);
  * cluster_y and cluster_z may be NULL (the clusters are still found and
  * tracked, their coordinates are not copied back: tracks-only results).  Offsets
  * that the device form rejects are passed to it unchanged, in one chunk, so
- * every event then fails as there.  velo_context_set_pipeline sets the most
- * chunks per call: 0 = automatic (about 12.6M pixel words per chunk, at most
- * 12), 1 = one chunk (copy in, compute, copy out, no overlap), at most 64;
- * VELO_EINVAL otherwise. */
+ * every event then fails as there.  The capacities in host_out behave as in
+ * velo_reconstruct_into: a batch whose totals exceed one copies no cluster
+ * and no track (status, per-event offsets, pixel labels and totals are
+ * still written), so nothing is written past a capacity; capacities below
+ * velo_query_sizes' bounds make the call wait for every chunk's totals
+ * before it copies results out (less overlap).  velo_context_set_pipeline
+ * sets the most chunks per call: 0 = automatic (about 10.5M pixel words per
+ * chunk when cluster coordinates are copied back, about 12.6M for
+ * tracks-only results, at most 12 chunks), 1 = one chunk (copy in, compute,
+ * copy out, no overlap), at most 64; VELO_EINVAL otherwise. */
 typedef struct velo_context velo_context_t;
 int velo_context_create(uint64_t max_events, uint64_t max_pixels, velo_context_t** ctx);
 void velo_context_destroy(velo_context_t* ctx);
@@ -394,7 +422,8 @@ int velo_forward(const velo_downstream_hits_t* hits, const velo_output_t* tracks
  * if a CUDA call fails. */
 int velo_measure_fp32_peak(double* flops_per_s, void* stream);
 
-/* Name of a VELO_* return code. */
+/* Name of a VELO_* return code (a static string; unknown codes get a generic
+ * name, never NULL).  No counterpart in the paper (error reporting only). */
 const char* velo_strerror(int code);
 
 /* Library version (major * 10000 + minor * 100 + patch). */

@@ -9,8 +9,12 @@ order).  It shares no code with the CUDA library: its C++ source is
 ``-ffp-contract=off``), and this wrapper marshals numpy arrays only.
 
 Pins (the checks that tie the oracle to something other than itself) live in
-``tests/test_oracle_*.py``; the functions that have none are listed in the
-module docstring of ``tests/test_oracle_pins.py``.
+``tests/test_oracle_*.py``: clustering, fits, tracking (hand-built events and
+brute-force enumeration), learned-rejection features and network, forward
+tracking, and the Monte-Carlo truth matching of ``mc.py``; planted mistakes in
+``tests/test_oracle_mutations.py`` check that the pins catch them.  Parity
+unpinned: the absolute efficiency and ghost rate against the paper, which
+prints none for this stage, and the tuned parameter values themselves.
 """
 from __future__ import annotations
 

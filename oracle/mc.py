@@ -6,12 +6,16 @@ figure for the first trigger stage, Sec. "HLT1 details and results"):
 * pixel truth: the particle with the largest deposit on the pixel (noise = -1),
   written by the generator;
 * cluster truth: the particle (or -1) with the largest summed charge over the
-  cluster's pixels, ties to the smaller id;
+  cluster's pixels, ties to the smaller id -- noise counts as id -1, so a tie
+  between noise and a particle leaves the cluster as noise;
 * reconstructible particle: >= 3 clusters with its truth, on distinct modules;
 * a track matches particle P if >= 70 % of its hits carry truth P (P >= 0);
 * efficiency = reconstructible particles matched by >= 1 track / reconstructible;
 * ghost rate = tracks matching no particle / tracks;
 * clone rate = (matching tracks beyond the first of each particle) / matched particles.
+
+Pinned by hand-counted events in tests/test_oracle_mc.py (every rule above
+changes a hand-counted figure when misread).
 """
 from __future__ import annotations
 

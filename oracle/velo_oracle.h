@@ -11,8 +11,7 @@
  * simplified pattern recognition and a parameterised Kalman filter applied
  * to the pixel-tracker segment of a track only (Sec. "HLT1 details and
  * results").  It gives no algorithm, so the steps below are this project's
- * reading of that statement; every reading is listed with the algorithm
- * definition in the design notes.
+ * reading of that statement.
  *
  * Arithmetic contract: IEEE-754 binary32 for every floating-point quantity
  * that decides anything, one rounding per + - * / in the written order, no

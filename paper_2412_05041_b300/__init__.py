@@ -24,8 +24,8 @@ MLP_WEIGHTS = 1505
 MLP_FLOATS = 1529
 FEATURE_NAMES = ("n_hits", "chi2ndf", "tx", "ty", "z_first", "z_last", "n_skipped", "mean_rx", "rms_rx", "mean_ry",
                  "rms_ry", "max_abs_r")
-EVT_OK, EVT_BADWORD, EVT_OVERFLOW = 0, 1, 2
-OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENOMEM = range(6)
+EVT_OK, EVT_BADWORD, EVT_OVERFLOW, EVT_TIMEOUT = 0, 1, 2, 3
+OK, EINVAL, ECAPACITY, ECUDA, ENOMEM = 0, 1, 2, 3, 5
 STATE_FIELDS = ("x", "y", "tx", "ty", "z_first", "z_beam", "chi2_lsq", "chi2_kf", "kf_x", "kf_y", "kf_tx",
                 "kf_ty", "kf_cxx", "kf_cxtx", "kf_ctxtx", "kf_cyy", "kf_cyty", "kf_ctyty", "ndf", "reserved")
 
@@ -61,7 +61,7 @@ class Output(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("cluster_threads", ctypes.c_uint32), ("cluster_smem_pixels", ctypes.c_uint32),
                 ("track_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("wide_cluster", ctypes.c_uint32)]
+                ("wide_cluster", ctypes.c_uint32), ("union_link_attempts", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

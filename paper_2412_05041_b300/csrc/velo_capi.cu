@@ -235,7 +235,6 @@ const char* velo_strerror(int code) {
     case VELO_EINVAL: return "invalid argument";
     case VELO_ECAPACITY: return "buffer or workspace too small";
     case VELO_ECUDA: return "CUDA runtime error";
-    case VELO_ETIMEOUT: return "bounded device wait timed out";
     case VELO_ENOMEM: return "allocation failed";
     default: return "unknown error";
   }
@@ -287,6 +286,7 @@ int velo_tuning_default(velo_tuning_t* t) {
   t->track_threads = 256;
   t->ctas_per_sm = 0;
   t->wide_cluster = 0;
+  t->union_link_attempts = 1u << 20;
   return VELO_OK;
 }
 
@@ -318,6 +318,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   L.par = make_par(params);
   L.out = *out;
   L.cluster_tier = tier;
+  L.union_link_attempts = tu.union_link_attempts;
   if (!carve_workspace(workspace, workspace_bytes_, L.n_events, L.n_pixels, &L.ws)) return VELO_ECAPACITY;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const uint64_t E = L.n_events;

@@ -70,13 +70,18 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t a) {
   }
 }
 
-// Link the larger root under the smaller.  Returns false if the retry bound
-// was hit (never expected; the event is then failed instead of looping).
-__device__ __forceinline__ bool uf_unite(uint32_t* parent, uint32_t a, uint32_t b) {
-  for (int it = 0; it < (1 << 20); ++it) {
+// Link the larger root under the smaller.  A link attempt that loses a race
+// (another union lowered the root first) retries from the new root; after
+// `attempts` attempts the union gives up and returns false (never expected
+// with the default bound of 2^20; the event then fails with
+// VELO_EVT_TIMEOUT instead of looping).  With attempts = 0 every union that
+// still has to link two trees gives up.
+__device__ __forceinline__ bool uf_unite(uint32_t* parent, uint32_t a, uint32_t b, uint32_t attempts) {
+  for (uint32_t it = 0;; ++it) {
     a = uf_find(parent, a);
     b = uf_find(parent, b);
     if (a == b) return true;
+    if (it >= attempts) return false;
     if (a < b) {
       const uint32_t t = a;
       a = b;
@@ -86,7 +91,6 @@ __device__ __forceinline__ bool uf_unite(uint32_t* parent, uint32_t a, uint32_t 
     if (old == a) return true;
     a = old;
   }
-  return false;
 }
 
 // 19-bit fixed-point value of a pseudo-angle key in [0, 4] (a key can round
@@ -331,13 +335,13 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
       for (int64_t j = (int64_t)i - 1; j >= 0; --j) {
         const uint32_t kj = A[j] & kKeyMask;
         if (kj != k && !(c > 0u && kj == k - 1u)) break;
-        ok &= uf_unite(B, i, (uint32_t)j);
+        ok &= uf_unite(B, i, (uint32_t)j, L.union_link_attempts);
       }
       if (r > 0u) {
         const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u), hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
         const uint32_t mr = k >> 11;
         uint32_t j = lower_bound_by(rt[mr - 1u], rt[mr], [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
-        for (; j < rt[mr] && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j);
+        for (; j < rt[mr] && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j, L.union_link_attempts);
       }
     }
   } else {
@@ -392,26 +396,26 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
           break;
         }
         if (kj == k || (c > 0u && kj == k - 1u) || (r > 0u && kj >= lo_k && kj <= hi_k))
-          ok &= uf_unite(B, i, (uint32_t)j);
+          ok &= uf_unite(B, i, (uint32_t)j, L.union_link_attempts);
       }
       if (!done) {  // past 16 steps (unions are idempotent: a neighbour seen twice is harmless)
         // duplicates of k and the left neighbour (k - 1) are the words just before i
         for (int64_t jj = (int64_t)i - 1; jj >= 0; --jj) {
           const uint32_t kj = A[jj] & kKeyMask;
-          if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)jj);
+          if (kj == k || (c > 0u && kj == k - 1u)) ok &= uf_unite(B, i, (uint32_t)jj, L.union_link_attempts);
           else break;
         }
         if (r > 0u) {  // previous row, columns c-1 .. c+1 of the same module
           uint32_t jj = lower_bound_by(0u, i, [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
-          for (; jj < i && (A[jj] & kKeyMask) <= hi_k; ++jj) ok &= uf_unite(B, i, jj);
+          for (; jj < i && (A[jj] & kKeyMask) <= hi_k; ++jj) ok &= uf_unite(B, i, jj, L.union_link_attempts);
         }
       }
     }
   }
   if (!ok) S.flag = 2u;
   __syncthreads();
-  if (S.flag) {
-    fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
+  if (S.flag) {  // a union gave up after its bounded link attempts
+    fail_event(L, e, VELO_EVT_TIMEOUT, true, p0, n);
     return kNone;
   }
   // every word to its root (the walks halve their paths with atomicMin, so a

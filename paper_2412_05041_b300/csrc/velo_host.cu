@@ -285,7 +285,26 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
     ok &= cudaEventRecord(c->ev_tot[k], s) == cudaSuccess;
   }
 
-  // ---- the host takes the chunks' totals in order and copies their results out
+  // ---- the host takes the chunks' totals in order and copies their results out.
+  // Capacities below the bounds of velo_query_sizes may not hold the batch:
+  // then every chunk's totals are awaited first, and a batch that does not fit
+  // copies no cluster and no track (as the device form writes none), only its
+  // status, per-event offsets, labels and totals.
+  const bool may_overflow = (ho->cap_clusters && ho->cap_clusters < P) ||
+                            (ho->cap_tracks && ho->cap_tracks < P / 3) ||
+                            (ho->cap_track_hits && ho->cap_track_hits < P);
+  bool copy = true;
+  if (may_overflow && rc == VELO_OK && ok) {
+    uint64_t nc = 0, nt = 0, nh = 0;
+    for (uint32_t k = 0; k < K && ok; ++k) {
+      if (cudaEventSynchronize(c->ev_tot[k]) != cudaSuccess) ok = false;
+      nc += c->h_tot[4 * k];
+      nt += c->h_tot[4 * k + 1];
+      nh += c->h_tot[4 * k + 2];
+    }
+    copy = (!ho->cap_clusters || nc <= ho->cap_clusters) && (!ho->cap_tracks || nt <= ho->cap_tracks) &&
+           (!ho->cap_track_hits || nh <= ho->cap_track_hits);
+  }
   uint64_t run_c = 0, run_t = 0, run_h = 0, run_f = 0;
   auto fixup = [&](const Chunk& q, uint32_t k) {
     if (cudaEventSynchronize(c->ev_done[k]) != cudaSuccess) {
@@ -297,7 +316,7 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
         ho->cluster_offsets[e] += q.bc;
         ho->track_offsets[e] += q.bt;
       }
-    if (q.bh)
+    if (q.bh && copy)
       for (uint64_t t = q.bt + 1; t <= q.bt + q.nt; ++t) ho->track_hit_offsets[t] += q.bh;
   };
   ho->cluster_offsets[0] = 0;
@@ -324,6 +343,11 @@ int velo_reconstruct_host(velo_context_t* c, const velo_events_t* ev, const velo
       run_f += q.nf;
       const velo_output_t d = region(k);
       cudaStream_t s = c->s_out;
+      if (!copy) {
+        ok &= cudaEventRecord(c->ev_done[k], s) == cudaSuccess;
+        if (k) fixup(ch[k - 1], k - 1);
+        continue;
+      }
       if (ho->cluster_x) d2h(ho->cluster_x + q.bc, d.cluster_x, 4 * q.nc, s);
       if (ho->cluster_y) d2h(ho->cluster_y + q.bc, d.cluster_y, 4 * q.nc, s);
       if (ho->cluster_z) d2h(ho->cluster_z + q.bc, d.cluster_z, 4 * q.nc, s);

@@ -89,6 +89,7 @@ struct Par {
 struct Launch {
   uint64_t n_events, n_pixels;
   uint32_t cluster_tier;  // words per event kept in shared memory by the clustering kernel
+  uint32_t union_link_attempts;  // bound of each union's link attempts (velo_tuning_t)
   const uint64_t* off;
   const uint32_t* pix;
   Geo geo;

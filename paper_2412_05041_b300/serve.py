@@ -124,14 +124,19 @@ class Server:
         With `freeze_gc` the objects that exist when serving starts are moved out
         of the interpreter's cyclic collector (gc.freeze) until it ends: a full
         collection over a large heap stalls the loop for tens of milliseconds,
-        which lands on the latency of every request in flight."""
-        if freeze_gc:
+        which lands on the latency of every request in flight.  The freeze is
+        process-wide, so it is taken only when nothing is frozen yet (not when
+        an enclosing caller or another Server froze objects), and undone only
+        by the call that took it.  Taking it runs one full collection first,
+        before the serving clock starts."""
+        own_freeze = freeze_gc and gc.get_freeze_count() == 0
+        if own_freeze:
             gc.collect()
             gc.freeze()
         try:
             return self._serve(requests, poll_sleep)
         finally:
-            if freeze_gc:
+            if own_freeze:
                 gc.unfreeze()
 
     def _serve(self, requests: list, poll_sleep: float) -> dict:

@@ -16,6 +16,7 @@ import oracle
 import paper_2412_05041_b300 as velo
 import velogen
 from _compare import to_numpy
+from oracle import mc
 from oracle import mlp as omlp
 from paper_2412_05041_b300 import mlp
 
@@ -147,5 +148,14 @@ def test_trained_network_beats_plain_cut_and_matches_oracle():
     learned = mlp.event_metrics_at(te, z >= thr)
     assert learned["efficiency"] >= plain["efficiency"] - 0.005, (plain, learned)
     assert learned["ghost_rate"] < plain["ghost_rate"], (plain, learned)
+    # the same comparison on the tracks the two in-kernel reconstructions return,
+    # matched by the oracle's truth code
+    lp = velo.default_params(use_mlp=1, mlp_logit_min=thr)
+    blob_dev = torch.from_numpy(blob).cuda()
+    lp.mlp = blob_dev.data_ptr()
+    out_plain = mc.evaluate_batch(test_b, gpu(test_b, velo.default_params(), pixel_labels=True))
+    out_learned = mc.evaluate_batch(test_b, gpu(test_b, lp, pixel_labels=True))
+    assert out_learned["efficiency"] >= out_plain["efficiency"] - 0.005, (out_plain, out_learned)
+    assert out_learned["ghost_rate"] < out_plain["ghost_rate"], (out_plain, out_learned)
     n_common, n_diff = _learned_vs_oracle(velogen.generate(velogen.Config(seed=5, n_events=60)), blob, thr)
     assert n_common > 10_000 and n_diff <= 5

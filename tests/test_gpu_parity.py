@@ -262,6 +262,39 @@ def test_host_form_chunks_agree_with_oracle():
     assert ge["n_failed"] == 2
 
 
+def test_host_form_respects_capacities():
+    """Capacities in the host output behave as in the device form: exact
+    capacities give the full result; one entry short copies no cluster and no
+    track (nothing written past a capacity), and the totals report the sizes
+    needed, while status and per-event offsets are still written."""
+    b = velogen.generate(velogen.C2, n_events=40, first_event=900)
+    vp, op = params(5e-4)
+    r = oracle.reconstruct(b.offsets, b.pixels, b.geometry, op)
+    H = velo.HostReconstructor(b.geometry, vp, max_events=40, max_pixels=len(b.pixels), chunks=3)
+    off, pix = _host(b.offsets, np.int64), _host(b.pixels, np.int32)
+    assert_same(H.run(off, pix), r)
+    need = [int(v) for v in H.totals[:3]]
+    H._out.cap_clusters, H._out.cap_tracks, H._out.cap_track_hits = need
+    assert_same(H.run(off, pix), r)  # capacities below the bounds, but enough
+    sentinel = -7
+    for which in range(3):
+        caps = list(need)
+        caps[which] -= 1
+        H._out.cap_clusters, H._out.cap_tracks, H._out.cap_track_hits = caps
+        for t in (H.cluster_x, H.cluster_y, H.cluster_z, H.track_hits, H.track_states, H.track_hit_offsets):
+            t.fill_(sentinel)
+        g = to_numpy(H.run(off, pix))
+        assert [int(v) for v in H.totals[:3]] == need
+        np.testing.assert_array_equal(g["status"], r["status"])
+        np.testing.assert_array_equal(g["cluster_offsets"].astype(np.uint64), r["cluster_offsets"])
+        np.testing.assert_array_equal(g["track_offsets"].astype(np.uint64), r["track_offsets"])
+        for t in (H.cluster_x, H.cluster_y, H.cluster_z, H.track_hits, H.track_states):
+            assert (t == sentinel).all()
+        assert int(H.track_hit_offsets[0]) == 0 and (H.track_hit_offsets[1:] == sentinel).all()
+    H._out.cap_clusters = H._out.cap_tracks = H._out.cap_track_hits = 0
+    assert_same(H.run(off, pix), r)
+
+
 def test_host_form_bad_offsets_and_empty_batch():
     b = velogen.generate(velogen.C2, n_events=6)
     off = b.offsets.copy()
@@ -355,3 +388,56 @@ def test_fp32_peak_measurement():
     assert velo.lib().velo_measure_fp32_peak(ctypes.byref(v), None) == velo.OK
     assert 10e12 < v.value < 200e12
     assert velo.lib().velo_measure_fp32_peak(None, None) == velo.EINVAL
+
+
+def _sub_batch(offsets, pixels, events):
+    """The listed events of a CSR batch, as a batch of their own."""
+    evs = [pixels[int(offsets[e]):int(offsets[e + 1])] for e in events]
+    off = np.zeros(len(evs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in evs])
+    return off, (np.concatenate(evs) if evs else np.zeros(0)).astype(np.uint32)
+
+
+def test_union_find_bound_fails_its_event_only():
+    """The clustering's lock-free union-find retries a link only after losing a
+    race, at most union_link_attempts times.  With no attempt allowed, exactly
+    the events that need a linking union (a V-shaped neighbourhood: a word
+    whose left and up-right neighbours are not otherwise connected) fail with
+    VELO_EVT_TIMEOUT -- no cluster, no track, labels 0xFFFFFFFF -- while every
+    other event stays identical to the oracle; at the default bound every
+    event is identical to the oracle."""
+    evs = []
+    # isolated pixels, a horizontal pair and a 2x2 block: linked without the union pass
+    evs.append(np.array([_word(9, 2, 300, 300), _word(4, 5, 700, 900), _word(6, 5, 700, 901),
+                         _word(3, 9, 1000, 500), _word(5, 9, 1000, 501), _word(7, 9, 1001, 500),
+                         _word(8, 9, 1001, 501)], np.uint32))
+    # the V: (r, c-1), (r-1, c+1), (r, c)
+    evs.append(np.array([_word(5, 3, 400, 599), _word(6, 3, 399, 601), _word(7, 3, 400, 600),
+                         _word(9, 7, 200, 200)], np.uint32))
+    c2 = velogen.generate(velogen.C2, n_events=6, first_event=1234)
+    evs += [c2.event(i) for i in range(6)]
+    offsets = np.zeros(len(evs) + 1, np.uint64)
+    offsets[1:] = np.cumsum([len(e) for e in evs])
+    pixels = np.concatenate(evs).astype(np.uint32)
+    vp, op = params(5e-4)
+    geo = velogen.Geometry()
+    r = oracle.reconstruct(offsets, pixels, geo, op)
+    assert (r["status"] == 0).all()
+    g = to_numpy(gpu_run(offsets, pixels, geo, vp))
+    assert_same(g, r)
+    t = to_numpy(velo.reconstruct(torch.from_numpy(offsets.view(np.int64)).cuda(),
+                                  torch.from_numpy(pixels.view(np.int32)).cuda(), geo, vp, pixel_labels=True,
+                                  tuning=velo.default_tuning(union_link_attempts=0)))
+    st = t["status"]
+    assert st[0] == velo.EVT_OK and st[1] == velo.EVT_TIMEOUT
+    assert set(st.tolist()) <= {velo.EVT_OK, velo.EVT_TIMEOUT}
+    assert t["n_failed"] == int((st == velo.EVT_TIMEOUT).sum())
+    for e in np.flatnonzero(st == velo.EVT_TIMEOUT):
+        assert t["cluster_offsets"][e + 1] == t["cluster_offsets"][e]
+        assert t["track_offsets"][e + 1] == t["track_offsets"][e]
+        assert (t["pixel_cluster"][int(offsets[e]):int(offsets[e + 1])].astype(np.uint32) == 0xFFFFFFFF).all()
+    good = np.flatnonzero(st == velo.EVT_OK)
+    so, sp = _sub_batch(offsets, pixels, good)
+    rs = oracle.reconstruct(so, sp, geo, op)
+    assert_same(t, rs, events=good)
+    assert_labels(t["pixel_cluster"], rs["pixel_cluster"], offsets, so, events=good)

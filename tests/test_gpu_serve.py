@@ -1,13 +1,16 @@
 """Streaming serving: requests arriving while others run are admitted as slots
 and device memory free up, run concurrently on their own streams, and every
-request's result is identical to the result of running it alone."""
+request's result is identical to the result of running it alone and to the
+CPU oracle's reconstruction of the same events (every request, the
+heavy-ion-like ones included)."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2412_05041_b300 as velo
 import velogen
-from _compare import to_numpy
+from _compare import assert_same, to_numpy
 from paper_2412_05041_b300 import serve
 
 pytestmark = pytest.mark.gpu
@@ -40,11 +43,15 @@ def alone(req, geo):
 
 
 def check_same(req, geo):
+    """The served result equals the request run alone (bit for bit) and the
+    oracle's result on the request's events (hit lists and cluster positions
+    exact, states within the 1e-5 contract)."""
     ref = alone(req, geo)
     got = to_numpy(req.result)
     for k in ("status", "cluster_offsets", "cluster_x", "cluster_y", "cluster_z", "track_offsets", "track_hit_offsets",
               "track_hits", "track_states"):
         np.testing.assert_array_equal(got[k], ref[k], err_msg=f"request {req.rid} {k}")
+    assert_same(got, oracle.reconstruct(req.offsets, req.pixels, geo, oracle.Params()))
 
 
 def test_results_identical_alone_and_in_the_mix():
@@ -53,9 +60,12 @@ def test_results_identical_alone_and_in_the_mix():
     stats = S.run(reqs)
     assert stats["requests"] == len(reqs) and stats["max_in_flight"] > 1
     assert stats["peak_memory_bytes"] <= stats["budget_bytes"]
+    n_heavy = 0
     for r in reqs:
         assert r.done >= r.admitted >= r.arrival
         check_same(r, geo)
+        n_heavy += int((np.diff(r.offsets.astype(np.int64)) > 60000).sum())
+    assert n_heavy > 0  # the mix holds heavy-ion-like events, and they were checked
 
 
 def test_memory_budget_limits_admission():

@@ -8,7 +8,7 @@ the product library is not involved.  Each case names the step of the method
 it breaks (centroid, connectivity, pseudo-angle window, straight-line and
 Kalman fits, chi2/ndf and the 3-hit rule, extension, seeding and its
 conflicts, termination, learned-rejection features and bfloat16 rounding,
-forward tracking).
+forward tracking, Monte-Carlo truth matching).
 """
 import concurrent.futures
 import os
@@ -20,10 +20,11 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PIN_TESTS = ("test_oracle_cluster.py", "test_oracle_fit.py", "test_oracle_track.py", "test_oracle_mlp.py",
+PIN_TESTS = ("test_oracle_mc.py", "test_oracle_cluster.py", "test_oracle_fit.py", "test_oracle_track.py", "test_oracle_mlp.py",
              "test_oracle_forward.py", "test_oracle_bruteforce.py")
 
-# (name, exact source text, replacement): each text occurs once in velo_oracle.cpp
+# (name, exact source text, replacement[, file]): each text occurs once in its
+# file of oracle/ (velo_oracle.cpp unless named)
 MUTATIONS = [
     ("centroid without the half-pixel offset",
      "snx[id] += q * (int64_t)(2 * w_col(w) + 1);", "snx[id] += q * (int64_t)(2 * w_col(w));"),
@@ -96,11 +97,31 @@ MUTATIONS = [
     ("forward: line from the two most upstream hits",
      "const uint32_t ha = track_hits[track_hit_offsets[t + 1] - 1], hb = track_hits[track_hit_offsets[t + 1] - 2];",
      "const uint32_t ha = track_hits[track_hit_offsets[t] + 1], hb = track_hits[track_hit_offsets[t]];"),
+    # Monte-Carlo truth matching (efficiency, ghost and clone rates)
+    ("truth: a track matches above 70 % instead of at 70 %",
+     "if cnt[j] >= min_frac * len(hits):", "if cnt[j] > min_frac * len(hits):", "mc.py"),
+    ("truth: 70 % of the truth-carrying hits instead of all hits",
+     "if cnt[j] >= min_frac * len(hits):", "if cnt[j] >= min_frac * int((t >= 0).sum()):", "mc.py"),
+    ("truth: reconstructible with 2 modules",
+     "recon[p] = len(mods) >= 3", "recon[p] = len(mods) >= 2", "mc.py"),
+    ("truth: reconstructible by clusters instead of distinct modules",
+     "mods = np.unique(cluster_module[ct == p])", "mods = cluster_module[ct == p]", "mc.py"),
+    ("truth: charge ties go to the larger id",
+     "if s > bestq[c]:", "if s >= bestq[c]:", "mc.py"),
+    ("truth: a particle beats noise in a charge tie",
+     "if s > bestq[c]:", "if s > bestq[c] or (s == bestq[c] and best[c] < 0 <= p):", "mc.py"),
+    ("truth: cluster truth by pixel count instead of summed charge",
+     "q = ((words >> 27) & 15).astype(np.int64)", "q = np.ones(len(words), np.int64)", "mc.py"),
+    ("truth: clone rate over tracks",
+     "clone_rate=n_clone / max(n_matched_p, 1),", "clone_rate=n_clone / max(n_tracks, 1),", "mc.py"),
+    ("truth: efficiency counts matched particles that are not reconstructible",
+     "n_eff += int(rec[uniq].sum()) if len(uniq) else 0", "n_eff += len(uniq)", "mc.py"),
 ]
 
 
 def _run_case(case, scratch):
-    name, old, new = case
+    name, old, new = case[:3]
+    fname = case[3] if len(case) > 3 else "velo_oracle.cpp"
     work = os.path.join(scratch, "case%02d" % MUTATIONS.index(case))
     os.makedirs(os.path.join(work, "tests"))
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(work, "oracle"),
@@ -110,7 +131,7 @@ def _run_case(case, scratch):
     for f in ("conftest.py", "_compare.py") + PIN_TESTS:
         shutil.copy2(os.path.join(ROOT, "tests", f), os.path.join(work, "tests", f))
     shutil.copy2(os.path.join(ROOT, "pytest.ini"), os.path.join(work, "pytest.ini"))
-    src = os.path.join(work, "oracle", "velo_oracle.cpp")
+    src = os.path.join(work, "oracle", fname)
     text = open(src).read()
     assert text.count(old) == 1, f"{name}: the source text is not unique"
     open(src, "w").write(text.replace(old, new))
