@@ -42,12 +42,8 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   ws->sc = c.take<uint32_t>(P);
   ws->sd = c.take<uint32_t>(P);
   ws->acc = c.take<unsigned long long>(3 * P);
-  ws->cl_x = c.take<float>(P);
-  ws->cl_y = c.take<float>(P);
-  ws->h_x = c.take<float>(P);
-  ws->h_y = c.take<float>(P);
-  ws->h_key = c.take<float>(P);
-  ws->h_id = c.take<uint32_t>(P);
+  ws->cl_xy = c.take<float2>(P);
+  ws->hit = c.take<float4>(P);
   ws->h_pos = c.take<uint32_t>(P);
   ws->used = c.take<uint8_t>(P);
   ws->trk_meta = c.take<uint32_t>(T);

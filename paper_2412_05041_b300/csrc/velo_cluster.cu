@@ -537,15 +537,15 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   // sort keeps its keys (32-bit) and cluster ids (16-bit: fewer than 2^16
   // clusters here) with their ping-pong copies, 12 bytes per cluster; the
   // cluster x, y and pseudo-angle key, read once at the end, go to global
-  // scratch (cl_x, cl_y, and sc, unused by the shared tier).
+  // scratch (cl_xy, and sc, unused by the shared tier; in the global tier
+  // h_pos, written only at the end).
   using V = typename std::conditional<HS, uint16_t, uint32_t>::type;
   uint32_t* KA = HS ? region : W.sa + p0;
   uint32_t* KB = HS ? region + n_clusters : W.sb + p0;
   V* VA = HS ? reinterpret_cast<V*>(region + 2 * n_clusters) : reinterpret_cast<V*>(W.sc + p0);
   V* VB = HS ? reinterpret_cast<V*>(region + 2 * n_clusters) + n_clusters : reinterpret_cast<V*>(W.sd + p0);
-  float* cx = W.cl_x + p0;
-  float* cy = W.cl_y + p0;
-  float* ck = HS ? reinterpret_cast<float*>(W.sc + p0) : W.h_key + p0;
+  float2* cxy = W.cl_xy + p0;
+  float* ck = reinterpret_cast<float*>(HS ? W.sc + p0 : W.h_pos + p0);
   const Geo& g = L.geo;
   const uint32_t* mo = S.mod_off;
   // In shared memory, when 16-bit counters of 2^kHitBucketBits key buckets
@@ -580,8 +580,7 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
     const float x = __fadd_rn(g.x0, __fmul_rn(g.pitch, u));
     const float y = __fadd_rn(g.y0, __fmul_rn(g.pitch, v));
     const float key = pseudo_angle(x, y);
-    cx[id] = x;
-    cy[id] = y;
+    cxy[id] = make_float2(x, y);
     if (counted) {  // key bits and bucket (< 2^16) of every cluster
       const uint32_t b = module_of(mo, M, id) << kHitBucketBits | hit_key_fixed(key) >> (19 - kHitBucketBits);
       KA[id] = __float_as_uint(key);
@@ -664,18 +663,15 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
       }
     }
     __syncthreads();
-    // the keys in sorted order through KA (dead after the last pass): in the
-    // global tier ck is h_key itself, read by id
+    // the keys in sorted order through KA (dead after the last pass)
     for (uint32_t pos = tid; pos < n_clusters; pos += NT) KA[pos] = __float_as_uint(ck[VB[pos]]);
     __syncthreads();
   }
   const uint32_t* KS = counted ? KB : KA;  // the keys (bits) in sorted order
   for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
     const uint32_t id = VB[pos];
-    W.h_x[p0 + pos] = cx[id];
-    W.h_y[p0 + pos] = cy[id];
-    W.h_key[p0 + pos] = __uint_as_float(KS[pos]);
-    W.h_id[p0 + pos] = id;
+    const float2 c = cxy[id];
+    W.hit[p0 + pos] = make_float4(c.x, c.y, __uint_as_float(KS[pos]), __uint_as_float(id));
     W.h_pos[p0 + id] = pos;
   }
   if (tid <= M) W.ev_modoff[e * kModOffStride + tid] = S.mod_off[tid];

@@ -181,54 +181,33 @@ __device__ __forceinline__ float dmod4(float a, float b) {
   return d;
 }
 
-// Candidate index ranges of a sorted key array (positions [lo, hi)) that
-// contain every key within half-width w of k on the circle [0, 4).  The
-// ranges are a superset (margin 1e-5 >> rounding of k +- w); callers apply
-// the exact dmod4 test to every candidate.
+// Candidate index ranges of a module's sorted keys that contain every key
+// within half-width w of k on the circle [0, 4).  The ranges are a superset
+// (margin 1e-5 >> rounding of k +- w); callers apply the exact dmod4 test to
+// every candidate.
 struct Ranges {
   uint32_t a0, a1, b0, b1;  // [a0, a1) and [b0, b1)
 };
 
-__device__ __forceinline__ Ranges window_ranges(const float* keys, uint32_t lo, uint32_t hi, float k, float w) {
-  const float eps = 1e-5f;
-  const float a = k - w - eps, b = k + w + eps;
-  auto lb = [&](float v) { return lower_bound_by(lo, hi, [&](uint32_t i) { return keys[i] < v; }); };
-  auto ub = [&](float v) { return lower_bound_by(lo, hi, [&](uint32_t i) { return keys[i] <= v; }); };
-  Ranges r;
-  if (a < 0.0f) {
-    r.a0 = lo;
-    r.a1 = ub(b);
-    r.b0 = max(lb(a + 4.0f), r.a1);
-    r.b1 = hi;
-  } else if (b >= 4.0f) {
-    r.a0 = lo;
-    r.a1 = ub(b - 4.0f);
-    r.b0 = max(lb(a), r.a1);
-    r.b1 = hi;
-  } else {
-    r.a0 = lb(a);
-    r.a1 = ub(b);
-    r.b0 = r.b1 = r.a1;
-  }
-  return r;
-}
-
-// Bucketed index of one module's sorted keys, so that a search bisects one
-// bucket of a few hits instead of the module: bucket b holds the keys in
+// Bucketed index of one module's sorted keys: bucket b holds the keys in
 // [b/S, (b+1)/S), S = kKeyBuckets / 4 (the last one also a key rounded up to
 // 4), tab[b] is the first module-local index of a key in bucket b or later,
-// tab[kKeyBuckets] the count.  Keys below v sit in v's bucket or earlier and
-// keys of later buckets are above v, so the first key >= v (or > v) lies in
-// [tab[b], tab[b+1]] and the answer is the one the bisection of the whole
-// module gives.
-constexpr uint32_t kKeyBuckets = 128;
+// tab[kKeyBuckets] the count.  The buckets are fine (about half a hit each in
+// a pile-up-5.5 module), so a window is searched as the whole buckets it
+// touches, from the table alone: a key >= v lies in v's bucket or later, so
+// at or after tab[bucket(v)], and a key <= v before tab[bucket(v) + 1].  The
+// ranges are therefore supersets of the window (callers test every candidate
+// exactly), and finding them reads no key.
+#ifndef VELO_KEY_BUCKETS
+#define VELO_KEY_BUCKETS 512
+#endif
+constexpr uint32_t kKeyBuckets = VELO_KEY_BUCKETS;
 __device__ __forceinline__ uint32_t key_bucket(float v) {
   const float t = v * (float)(kKeyBuckets / 4);  // exact: a power of two
   return t <= 0.0f ? 0u : (t >= (float)(kKeyBuckets - 1) ? kKeyBuckets - 1 : (uint32_t)t);
 }
 
 struct KeyIndex {
-  const float* keys;    // the event's sorted keys (positions index them)
   uint32_t lo;          // first position of the module
   const uint16_t* tab;  // kKeyBuckets + 1 module-local indices
 };
@@ -237,28 +216,22 @@ __device__ __forceinline__ Ranges window_ranges(const KeyIndex& I, float k, floa
   const float eps = 1e-5f;
   const float a = k - w - eps, b = k + w + eps;
   const uint32_t lo = I.lo, hi = I.lo + I.tab[kKeyBuckets];
-  auto lb = [&](float v) {
-    const uint32_t q = key_bucket(v);
-    return lo + lower_bound_by(I.tab[q], I.tab[q + 1], [&](uint32_t x) { return I.keys[lo + x] < v; });
-  };
-  auto ub = [&](float v) {
-    const uint32_t q = key_bucket(v);
-    return lo + lower_bound_by(I.tab[q], I.tab[q + 1], [&](uint32_t x) { return I.keys[lo + x] <= v; });
-  };
+  auto first = [&](float v) { return lo + I.tab[key_bucket(v)]; };     // every key >= v is at or after it
+  auto past = [&](float v) { return lo + I.tab[key_bucket(v) + 1]; };  // every key <= v is before it
   Ranges r;
   if (a < 0.0f) {
     r.a0 = lo;
-    r.a1 = ub(b);
-    r.b0 = max(lb(a + 4.0f), r.a1);
+    r.a1 = past(b);
+    r.b0 = max(first(a + 4.0f), r.a1);
     r.b1 = hi;
   } else if (b >= 4.0f) {
     r.a0 = lo;
-    r.a1 = ub(b - 4.0f);
-    r.b0 = max(lb(a), r.a1);
+    r.a1 = past(b - 4.0f);
+    r.b0 = max(first(a), r.a1);
     r.b1 = hi;
   } else {
-    r.a0 = lb(a);
-    r.a1 = ub(b);
+    r.a0 = first(a);
+    r.a1 = past(b);
     r.b0 = r.b1 = r.a1;
   }
   return r;

@@ -51,13 +51,10 @@ struct Workspace {
   uint32_t* sb;              // pixel-indexed u32: sort ping-pong / seed h2
   uint32_t* sc;              // pixel-indexed u32: hit-sort values / prev link
   uint32_t* sd;              // pixel-indexed u32: hit-sort values / first_of
-  unsigned long long* acc;   // pixel-indexed x3: centroid sums / claims + seed keys
-  float* cl_x;               // pixel-indexed: cluster x in id order (events whose hits overflow shared memory)
-  float* cl_y;               // pixel-indexed: cluster y in id order
-  float* h_x;                // pixel-indexed: hits sorted by (module, key, id)
-  float* h_y;
-  float* h_key;
-  uint32_t* h_id;
+  unsigned long long* acc;   // pixel-indexed x3: centroid sums / claims, seed keys, seeding u terms
+  float2* cl_xy;             // pixel-indexed: cluster (x, y) in id order (clustering -> output)
+  float4* hit;               // pixel-indexed: hits sorted by (module, key, id), one 16-byte record
+                             // each: x, y, pseudo-angle key, cluster id (its bits)
   uint32_t* h_pos;           // pixel-indexed: sorted position of each cluster id
   uint8_t* used;             // pixel-indexed
   uint32_t* trk_meta;        // track-indexed

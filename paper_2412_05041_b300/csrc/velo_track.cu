@@ -126,11 +126,12 @@ __device__ __forceinline__ uint32_t gather_track(const Workspace& W, uint64_t p0
   uint32_t p = W.trk_a[tb + t];
   for (uint32_t j = 0; j < n; ++j) {
     const uint32_t m = module_of_pos(mod_off, M, p);
-    xs[j] = W.h_x[p0 + p];
-    ys[j] = W.h_y[p0 + p];
+    const float4 h = W.hit[p0 + p];
+    xs[j] = h.x;
+    ys[j] = h.y;
     zs[j] = mz[m];
     mods[j] = m;
-    if (ids) ids[j] = W.h_id[p0 + p];
+    if (ids) ids[j] = __float_as_uint(h.w);
     p = W.sc[p0 + p];  // link to the next hit downstream
   }
   return n;
@@ -155,6 +156,16 @@ __device__ __forceinline__ Ranges narrowed_ranges(const KeyIndex& I, float win, 
   const float half = 1.5708f * reach / r * 1.01f + 1e-4f;
   if (!(half < win)) return wide;
   return window_ranges(I, pseudo_angle(xc, yc), half);
+}
+
+// A claim on a hit at module step m: the step in the top five bits, then the
+// claim's value (the bits of a non-negative binary32, which order as the
+// values) and a 28-bit index (a track index or cluster id: below 2^21, as an
+// event holds at most 32 x 65535 clusters).  Steps run downwards, so a claim of
+// step m is smaller than any left by an earlier step and the claims need no
+// reset between steps; within a step the order is the method's (value, index).
+__device__ __forceinline__ unsigned long long step_key(uint32_t m, uint32_t value_bits, uint32_t index) {
+  return (unsigned long long)m << 59 | (unsigned long long)value_bits << 28 | index;
 }
 
 // chi2/ndf of the cut: straight-line chi2 without scattering, Kalman chi2 with it
@@ -216,10 +227,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   if (tid < kModOffStride) S.mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
   if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
 
-  const float* hx = W.h_x + p0;
-  const float* hy = W.h_y + p0;
-  const float* hk = W.h_key + p0;
-  const uint32_t* hid = W.h_id + p0;
+  const float4* hit = W.hit + p0;  // x, y, key, id bits
   uint8_t* used = W.used + p0;
   uint32_t* prev = W.sc + p0;
   uint32_t* first_of = W.sd + p0;
@@ -236,32 +244,34 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   for (uint32_t i = gt; i < H; i += GT) {
     used[i] = 0;
     first_of[i] = kNone;
+    claim[i] = ~0ull;  // claims carry their step (step_key): no reset between steps
   }
   bar();  // mod_off
-  // bucketed key index of module j into slot j % 3: entries past the last
-  // bucket hold the count, every hit fills the buckets from its predecessor's
-  // (exclusive) to its own
+  // bucketed key index of module j into slot j % 3, without a barrier: every
+  // entry is written once -- each hit fills the buckets from its predecessor's
+  // (exclusive) to its own, the last hit the ones after its own with the count
   auto index_module = [&](uint32_t j) {
     const uint32_t lo = S.mod_off[j], n = S.mod_off[j + 1] - lo;
     uint16_t* tab = S.ktab[j % 3u];
-    for (uint32_t q = tid; q <= kKeyBuckets; q += NT) tab[q] = (uint16_t)n;
-    __syncthreads();
+    if (n == 0u) {
+      for (uint32_t q = tid; q <= kKeyBuckets; q += NT) tab[q] = 0;
+      return;
+    }
     for (uint32_t i = tid; i < n; i += NT) {
-      const uint32_t b = key_bucket(hk[lo + i]), b0 = i ? key_bucket(hk[lo + i - 1]) + 1u : 0u;
+      const uint32_t b = key_bucket(hit[lo + i].z), b0 = i ? key_bucket(hit[lo + i - 1].z) + 1u : 0u;
       for (uint32_t q = b0; q <= b; ++q) tab[q] = (uint16_t)i;
+      if (i + 1u == n)
+        for (uint32_t q = b + 1u; q <= kKeyBuckets; ++q) tab[q] = (uint16_t)n;
     }
   };
   index_module(M - 1);
-  __syncthreads();
   index_module(M - 2);
   __syncthreads();
 
   uint32_t n_tr = 0;
   for (int m = (int)M - 2; m >= 0; --m) {
     if (m >= 1) index_module((uint32_t)m - 1u);  // its slot held module m + 2, done with at step m + 1
-    const uint32_t clo = S.mod_off[m > 0 ? m - 1 : 0], chi = S.mod_off[min((uint32_t)m + 2u, M)];
-    for (uint32_t pos = clo + gt; pos < chi; pos += GT) claim[pos] = ~0ull;
-    bar();
+    if constexpr (WIDE) __syncthreads();  // the radial order below reads the index
     // (heavy events) the hits of module m - 1 inside each key bucket by r^2,
     // so that a dense h2 window visits only the hits of the radial band a seed
     // can reach (read by the seeding of this step, after the extension's
@@ -278,12 +288,12 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           const uint32_t n2 = S.mod_off[m] - lo;
           float* rkey = reinterpret_cast<float*>(rord + kRadialCap);
           for (uint32_t i = tid; i < n2; i += NT) {
-            const float x = hx[lo + i], y = hy[lo + i];
-            rkey[i] = fa(fm(x, x), fm(y, y));
+            const float4 h = hit[lo + i];
+            rkey[i] = fa(fm(h.x, h.x), fm(h.y, h.y));
           }
           __syncthreads();
           for (uint32_t i = tid; i < n2; i += NT) {
-            const uint32_t b = key_bucket(hk[lo + i]), s0 = tab[b], s1 = tab[b + 1];
+            const uint32_t b = key_bucket(hit[lo + i].z), s0 = tab[b], s1 = tab[b + 1];
             const float r2 = rkey[i];
             uint32_t c = 0;
             for (uint32_t j = s0; j < s1; ++j) {
@@ -311,25 +321,27 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           meta[t] = mt & ~kTrkActive;
         } else if (la > m) {
           const uint32_t a = ldx<WIDE>(ta + t), b = ldx<WIDE>(tbk + t);
-          const float xa = hx[a], ya = hy[a], ka = hk[a], xb = hx[b], yb = hy[b];
+          const float4 A = hit[a], B = hit[b];
+          const float xa = A.x, ya = A.y, ka = A.z, xb = B.x, yb = B.y;
           const float za = S.z[la], zb = S.z[lb];
           const float dzab = fs(za, zb);
           const float tx = fd(fs(xa, xb), dzab), ty = fd(fs(ya, yb), dzab);
           const float dzm = fs(zm, za);
           const float xp = fa(xa, fm(tx, dzm)), yp = fa(ya, fm(ty, dzm));
-          const KeyIndex Im{hk, mlo, S.ktab[m % 3]};
+          const KeyIndex Im{mlo, S.ktab[m % 3]};
           Ranges R = window_ranges(Im, ka, P.win_fwd);
           if ((R.a1 - R.a0) + (R.b1 - R.b0) > kNarrowAbove) R = narrowed_ranges(Im, P.win_fwd, R, xp, yp, fwd_reach);
           unsigned long long best = ~0ull;
           for (int part = 0; part < 2; ++part) {
             const uint32_t s = part ? R.b0 : R.a0, en = part ? R.b1 : R.a1;
             for (uint32_t pos = s; pos < en; ++pos) {  // the cut first: few candidates pass it
-              const float dx = fs(xp, hx[pos]), dy = fs(yp, hy[pos]);
+              const float4 h = hit[pos];
+              const float dx = fs(xp, h.x), dy = fs(yp, h.y);
               const float d2 = fa(fm(dx, dx), fm(dy, dy));
               if (d2 > P.max_scatter_fwd) continue;
               if (ldx<WIDE>(used + pos)) continue;
-              if (dmod4(hk[pos], ka) > P.win_fwd) continue;
-              const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | hid[pos];
+              if (dmod4(h.z, ka) > P.win_fwd) continue;
+              const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | fbits(h.w);
               if (cand < best) {
                 best = cand;
                 pk = pos;
@@ -337,7 +349,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
             }
           }
           if (pk != kNone) {
-            const unsigned long long key = (best >> 32) << 32 | t;
+            const unsigned long long key = step_key((uint32_t)m, (uint32_t)(best >> 32), t);
             pick_key[t] = key;
             atomicMin(claim + pk, key);
           }
@@ -396,23 +408,24 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const float pre_r = sqrtf(P.max_scatter_seed) * (1.0f + 1e-6f) + 1.5f * pre_err;
     const float pre_sc = pre_r * pre_r * (1.0f + 1e-5f);
     const float ap = fm(rcp_dz02, dz12), oma = fs(1.0f, ap);
-    float* ux = W.cl_x + p0;  // (1 - a') x2, (1 - a') y2 of the hits of module m - 1 (the
-    float* uy = W.cl_y + p0;  // clustering's centroid scratch, free during tracking)
+    // (1 - a') x2, (1 - a') y2 of the hits of module m - 1, in the third slice of
+    // the clustering's charge-sum scratch (dead after the clustering; the
+    // first two hold the claims and the seed keys)
+    float2* uxy = reinterpret_cast<float2*>(W.acc + 2 * L.n_pixels) + p0;
     // (WIDE, modules of up to kRadialCap hits) every CTA keeps its own copy of
     // the u terms of module m - 1 and of the used flags of module m + 1
     bool local = false;
-    float *sux = nullptr, *suy = nullptr;
+    float2* su = nullptr;
     uint32_t* sused = nullptr;
     if constexpr (WIDE) {
       local = radial && hi0 - lo0 <= kRadialCap;
-      sux = reinterpret_cast<float*>(rord + kRadialCap) + kRadialCap;
-      suy = sux + kRadialCap;
-      sused = reinterpret_cast<uint32_t*>(suy + kRadialCap);
+      su = reinterpret_cast<float2*>(reinterpret_cast<float*>(rord + kRadialCap) + kRadialCap);
+      sused = reinterpret_cast<uint32_t*>(su + kRadialCap);
     }
     if (local) {
       for (uint32_t q = tid; q < hi2 - lo2; q += NT) {
-        sux[q] = fm(oma, hx[lo2 + q]);
-        suy[q] = fm(oma, hy[lo2 + q]);
+        const float4 h = hit[lo2 + q];
+        su[q] = make_float2(fm(oma, h.x), fm(oma, h.y));
       }
       for (uint32_t base = 0; base < hi0 - lo0; base += NT) {
         const uint32_t q = base + tid;
@@ -421,8 +434,8 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       }
     } else {
       for (uint32_t q = lo2 + gt; q < hi2; q += GT) {
-        ux[q] = fm(oma, hx[q]);
-        uy[q] = fm(oma, hy[q]);
+        const float4 h = hit[q];
+        uxy[q] = make_float2(fm(oma, h.x), fm(oma, h.y));
       }
     }
     constexpr uint32_t kChunk = seed_chunk<NT>();
@@ -442,10 +455,10 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
             S.sd.best[i] = ~0ull;
           }
           if (!ldx<WIDE>(used + p1)) {
-            const float k1 = hk[p1];
-            const Ranges R0 = window_ranges(KeyIndex{hk, lo0, S.ktab[(m + 1) % 3]}, k1, P.win_seed);
+            const float k1 = hit[p1].z;
+            const Ranges R0 = window_ranges(KeyIndex{lo0, S.ktab[(m + 1) % 3]}, k1, P.win_seed);
             S.sd.r0[i] = pack_ranges(R0, lo0);
-            S.sd.r2[i] = pack_ranges(window_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, k1, P.win_seed), lo2);
+            S.sd.r2[i] = pack_ranges(window_ranges(KeyIndex{lo2, S.ktab[(m - 1) % 3]}, k1, P.win_seed), lo2);
             c = (R0.a1 - R0.a0) + (R0.b1 - R0.b0);
           }
         }
@@ -470,19 +483,21 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const uint32_t kk = j - S.sd.ioff[i], na = R0.a1 - R0.a0;
         const uint32_t q0 = kk < na ? R0.a0 + kk : R0.b0 + (kk - na);
         if (local ? (sused[(q0 - lo0) >> 5] >> ((q0 - lo0) & 31u)) & 1u : ldx<WIDE>(used + q0)) continue;
-        const float k1 = hk[p1];
-        if (dmod4(hk[q0], k1) > P.win_seed) continue;
-        const float x1 = hx[p1], y1 = hy[p1], x0 = hx[q0], y0 = hy[q0];
-        const unsigned long long lid0 = hid[q0] - lo0;
+        const float4 H0 = hit[q0], H1 = hit[p1];
+        const float k1 = H1.z;
+        if (dmod4(H0.z, k1) > P.win_seed) continue;
+        const float x1 = H1.x, y1 = H1.y, x0 = H0.x, y0 = H0.y;
+        const unsigned long long lid0 = fbits(H0.w) - lo0;
         Ranges R2 = unpack_ranges(S.sd.r2[i], lo2);
         const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
         unsigned long long best = ~0ull;
         auto try_h2 = [&](uint32_t q2) {
-          const float ex = fa(local ? sux[q2 - lo2] : ldx<WIDE>(ux + q2), c0x),
-                      ey = fa(local ? suy[q2 - lo2] : ldx<WIDE>(uy + q2), c0y);
+          const float2 u = local ? su[q2 - lo2] : ldx<WIDE>(uxy + q2);
+          const float ex = fa(u.x, c0x), ey = fa(u.y, c0y);
           if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) return;
-          if (dmod4(hk[q2], k1) > P.win_seed) return;
-          const float x2 = hx[q2], y2 = hy[q2];
+          const float4 H2 = hit[q2];
+          if (dmod4(H2.z, k1) > P.win_seed) return;
+          const float x2 = H2.x, y2 = H2.y;
           const float dx02 = fs(x0, x2), dy02 = fs(y0, y2);
           const float tx = fd(dx02, dz02), ty = fd(dy02, dz02);
           if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) return;
@@ -491,7 +506,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           const float sc = fa(fm(dx, dx), fm(dy, dy));
           if (sc > P.max_scatter_seed) return;
           const unsigned long long cand =
-              (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(hid[q2] - lo2);
+              (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(fbits(H2.w) - lo2);
           best = cand < best ? cand : best;
         };
         bool searched = false;
@@ -540,7 +555,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         }
         if (!searched) {
           if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
-            R2 = narrowed_ranges(KeyIndex{hk, lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2,
+            R2 = narrowed_ranges(KeyIndex{lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2,
                                  (x1 - alpha * x0) / one_m_alpha, (y1 - alpha * y0) / one_m_alpha, seed_reach);
           for (int part2 = 0; part2 < 2; ++part2) {
             const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
@@ -557,7 +572,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         if (key != ~0ull) {
           const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
           const uint32_t b2 = W.h_pos[p0 + lo2 + (uint32_t)(key & 0xFFFFu)];
-          skey = (key >> 32) << 32 | hid[p1];
+          skey = step_key((uint32_t)m, (uint32_t)(key >> 32), fbits(hit[p1].w));
           seed_h0[p1] = b0;
           seed_h2[p1] = b2;
           atomicMin(claim + b0, skey);
@@ -675,7 +690,7 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
   if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
   if (tid == 0) S.hit_fill = 0;
   __syncthreads();
-  const uint32_t* hid = W.h_id + p0;
+  const float4* hit = W.hit + p0;
   uint32_t* first_of = W.sd + p0;
   // for k_output: every track's state and its hit ids (in z order) at a slot of
   // the event's word slice of sa (dead after the module loop; the tracks hold
@@ -716,7 +731,7 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
     if (valid) {
       rank[t] = kNone;
       if (keep) {
-        first_of[hid[ta[t]]] = t;
+        first_of[fbits(hit[ta[t]].w)] = t;
         if (P.use_mlp) st[19] = W.trk_logit[tb + t];
         float4* so = reinterpret_cast<float4*>(W.trk_state + (tb + t) * VELO_STATE_STRIDE);  // 16-byte aligned
 #pragma unroll
@@ -792,20 +807,19 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   __syncthreads();
   const uint32_t H = W.ev_nclusters[e];
   const uint64_t co = L.out.cluster_offsets[e];
-  // clusters in id order (coalesced stores), each read from its sorted
-  // position (h_pos: id -> position; the reads stay within the module's few
-  // cache lines); the loads of U ids are issued before their stores.  The
-  // module offsets hold for ids as for positions (the hit sort keeps every
-  // module's clusters together).
+  // clusters in id order (coalesced loads and stores): the clustering's
+  // (x, y) by id, untouched by the tracking; the loads of U ids are issued
+  // before their stores.  The module offsets hold for ids as for positions
+  // (the hit sort keeps every module's clusters together).
   for (uint32_t id0 = tid; id0 < H; id0 += U * NT) {
     float x[U], y[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t id = id0 + u * NT;
       if (id < H) {
-        const uint32_t pos = W.h_pos[p0 + id];
-        x[u] = W.h_x[p0 + pos];
-        y[u] = W.h_y[p0 + pos];
+        const float2 c = W.cl_xy[p0 + id];
+        x[u] = c.x;
+        y[u] = c.y;
       }
     }
 #pragma unroll
