@@ -45,10 +45,10 @@ struct ClusterSmem {
 };
 
 constexpr uint32_t kRootFlag = 0x80000000u;
-constexpr uint32_t kRowSortMax = 32;
+constexpr uint32_t kRowSortMax = 32;  // longest row sorted by insertion (else the full radix sort)
 // key buckets per module of the counting hit sort: 2^8 (about one hit each
 // at pile-up 5.5)
-constexpr uint32_t kHitBucketBits = 8;  // longest row sorted by insertion (else the full radix sort)
+constexpr uint32_t kHitBucketBits = 8;
 // Events of at least this many words (kept in the workspace) index the first
 // sorted position of every (module, row): 32 modules x 2048 rows.
 constexpr uint32_t kRowTable = 1u << 16;
@@ -143,35 +143,48 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   uint32_t* A = PS ? region : W.sa + p0;
   uint32_t* B = PS ? region + n : W.sb + p0;
 
-  // 2. sort by (module, row, col).  First by (module, row): in shared memory,
-  // when a 16-bit counter per (module, row) fits after the two word arrays,
-  // by one counting pass (counts, their exclusive scan, and a scatter whose
-  // atomics give the words of a row their places in arbitrary order); else by
-  // two stable LSD passes (A->B->A).  Then the words of every row -- a few in
-  // a pile-up event -- go in column order by an insertion sort, run by the
-  // thread that owns the row's first word.  If a row has more than
-  // kRowSortMax words, the whole array is sorted again by the full key (4
-  // passes).  (Events of kRowTable words or more -- dense modules, long rows
-  // -- take the full sort at once.)  Words with equal keys (duplicates) may
-  // end in any order among themselves, and nothing that follows depends on
-  // it: they share one cluster, their charges add without order, and every
-  // label is found by key.
+  // 2. sort by (module, row, col).  In shared memory, when 16-bit counters
+  // per group fit after the two word arrays -- a group is a (module, row), or
+  // a (module, row pair) for larger events -- by one counting pass: counts,
+  // their exclusive scan, and a scatter whose atomics give the words of a
+  // group their places in arbitrary order (A -> B) and leave every group's
+  // end in its counter; then every word takes its place in (row, column)
+  // order inside its group by counting the group's words that precede it
+  // (a smaller key, or an equal key at an earlier place: B -> A).  Groups
+  // hold a few words in a pile-up event.  Otherwise by two stable LSD passes
+  // by (module, row) and an insertion sort of every row by the thread that
+  // owns its first word; a row of more than kRowSortMax words sends the whole
+  // array to the full sort by the key (4 passes).  (Events of kRowTable
+  // words or more -- dense modules, long rows -- take the full sort at once.)
+  // Words with equal keys (duplicates) may end in any order among
+  // themselves, and nothing that follows depends on it: they share one
+  // cluster, their charges add without order, and every label is found by
+  // key.
   bool long_row = !PS && n >= kRowTable;
   bool counted = false;
   if constexpr (PS) {
     const uint32_t nrow = L.geo.n_rows;
-    const uint32_t cw = (M * nrow + 1u) / 2u;  // u32 words of 16-bit counter pairs
-    if (n < 65536u && 2u * n + cw <= 2u * tier) {
+    bool fits = false;
+    uint32_t gshift = 11, ngrp = nrow, cw = 0;  // group = key >> gshift: (module, row), else (module, row pair)
+    for (int pass = 0; pass < 2 && !fits; ++pass) {
+      gshift = 11u + (uint32_t)pass;
+      ngrp = (nrow + (uint32_t)pass) >> pass;
+      cw = (M * ngrp + 1u) / 2u;  // u32 words of 16-bit counter pairs
+      fits = n < 65536u && 2u * n + cw <= 2u * tier;
+    }
+    if (fits) {
       counted = true;
       uint32_t* C = region + 2 * n;
+      const uint32_t rmask = 2047u >> (gshift - 11u);
+      auto group = [&](uint32_t w) { return ((w >> 22) & 31u) * ngrp + ((w >> gshift) & rmask); };
       for (uint32_t q = tid; q < cw; q += NT) C[q] = 0u;
       __syncthreads();
       for (uint32_t i = tid; i < n; i += NT) {
-        const uint32_t w = A[i], b = ((w >> 22) & 31u) * nrow + ((w >> 11) & 2047u);
+        const uint32_t b = group(A[i]);
         atomicAdd(C + (b >> 1), 1u << ((b & 1u) << 4));
       }
       __syncthreads();
-      // exclusive scan of the counts in (module, row) order: a chunk of an odd
+      // exclusive scan of the counts in group order: a chunk of an odd
       // number of words per thread (no bank conflicts), one block scan
       const uint32_t per = ((cw + NT - 1) / NT) | 1u;
       const uint32_t q0 = min(cw, tid * per), q1 = min(cw, q0 + per);
@@ -189,13 +202,23 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
       }
       __syncthreads();
       for (uint32_t i = tid; i < n; i += NT) {
-        const uint32_t w = A[i], b = ((w >> 22) & 31u) * nrow + ((w >> 11) & 2047u), sh = (b & 1u) << 4;
+        const uint32_t w = A[i], b = group(w), sh = (b & 1u) << 4;
         B[(atomicAdd(C + (b >> 1), 1u << sh) >> sh) & 0xFFFFu] = w;
       }
       __syncthreads();
-      uint32_t* t = A;  // the sorted words are in B: swap the roles
-      A = B;
-      B = t;
+      // every counter now holds its group's end (start + count, < n < 2^16)
+      auto group_end = [&](uint32_t b) { return (C[b >> 1] >> ((b & 1u) << 4)) & 0xFFFFu; };
+      for (uint32_t p = tid; p < n; p += NT) {
+        const uint32_t w = B[p], k = w & kKeyMask, b = group(w);
+        const uint32_t s0 = b ? group_end(b - 1u) : 0u, s1 = group_end(b);
+        uint32_t r = s0;
+        for (uint32_t q = s0; q < s1; ++q) {
+          const uint32_t kq = B[q] & kKeyMask;
+          r += kq < k || (kq == k && q < p);
+        }
+        A[r] = w;
+      }
+      __syncthreads();
     }
   }
   if (!long_row && !counted) {
@@ -204,49 +227,28 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     radix_pass<NT, false>(B, A, (const uint32_t*)nullptr, (uint32_t*)nullptr, n,
                           [](uint32_t k, uint32_t) { return (k & kKeyMask) >> 19; }, S.cnt, S.tmp);
   }
-  // Every warp takes 32 consecutive words at a time.  A row that starts and
-  // ends among them is ordered by the warp at once: each word's place is the
-  // row's first lane plus the number of the row's words with a smaller key,
-  // or an equal key in a lower lane (the row's lanes are contiguous).  A row
-  // that goes on past the 32 words is sorted by insertion, by the thread that
-  // owns its first word.  Rows only permute inside themselves, so the rows
-  // read next to a window never change while others sort theirs.
-  for (uint32_t pos0 = tid & ~31u; pos0 < n && !(!PS && n >= kRowTable); pos0 += NT) {
-    const uint32_t lane = lane_id(), pos = pos0 + lane;
-    const bool valid = pos < n;
-    const uint32_t w = valid ? A[pos] : 0u, k = w & kKeyMask;
-    const uint32_t mr = valid ? k >> 11 : 0x80000000u | lane;  // invalid lanes match nothing
-    // the row's lanes are contiguous: a ballot of the lanes that start a
-    // group (a row other than the lane below's) bounds every lane's row
-    const uint32_t below = __shfl_up_sync(kFull, mr, 1);
-    const uint32_t heads = __ballot_sync(kFull, lane == 0u || below != mr);
-    const uint32_t upto = lane == 31u ? kFull : (2u << lane) - 1u;
-    const uint32_t first = 31u - __clz(heads & upto), above = heads & ~upto;
-    const uint32_t cnt = (above ? (uint32_t)__ffs(above) - 1u : 32u) - first;
-    const bool starts = first > 0u || pos0 == 0u || ((A[pos0 - 1] & kKeyMask) >> 11) != mr;
-    const bool ends = first + cnt < 32u || pos0 + 32u >= n || ((A[pos0 + 32] & kKeyMask) >> 11) != mr;
-    const bool inside = valid && starts && ends;
-    const uint32_t rounds = __reduce_max_sync(kFull, inside ? cnt : 0u);
-    uint32_t at = first;
-    for (uint32_t t = 0; t < rounds; ++t) {
-      const uint32_t j = t < cnt ? first + t : lane;
-      const uint32_t kj = __shfl_sync(kFull, k, j);
-      at += t < cnt && (kj < k || (kj == k && j < lane));
-    }
-    __syncwarp();
-    if (inside && cnt > 1u) A[pos0 + at] = w;
-    if (valid && starts && !ends && lane == first) {  // the row goes on past the window
-      uint32_t end = pos + 1;
+  // After the LSD passes every row's words are contiguous, in any column
+  // order.  The thread that holds a row's first word (the word before it lies
+  // in another row) puts the row in column order by insertion when it has
+  // more than one word.  Rows only permute inside themselves, and a word's
+  // row never changes, so the row tests of the other threads read the same
+  // rows while a row is being sorted.
+  if (!counted && (PS || n < kRowTable)) {
+    for (uint32_t pos = tid; pos < n; pos += NT) {
+      const uint32_t mr = (A[pos] & kKeyMask) >> 11;
+      if (pos > 0 && ((A[pos - 1] & kKeyMask) >> 11) == mr) continue;   // not the row's first word
+      if (pos + 1 >= n || ((A[pos + 1] & kKeyMask) >> 11) != mr) continue;  // a row of one word
+      uint32_t end = pos + 2;
       while (end < n && end - pos <= kRowSortMax && ((A[end] & kKeyMask) >> 11) == mr) ++end;
       if (end - pos > kRowSortMax) {
         long_row = true;
-      } else {
-        for (uint32_t a = pos + 1; a < end; ++a) {
-          const uint32_t wa = A[a], ka = wa & kKeyMask;
-          uint32_t b = a;
-          for (; b > pos && (A[b - 1] & kKeyMask) > ka; --b) A[b] = A[b - 1];
-          A[b] = wa;
-        }
+        continue;
+      }
+      for (uint32_t a = pos + 1; a < end; ++a) {
+        const uint32_t wa = A[a], ka = wa & kKeyMask;
+        uint32_t b = a;
+        for (; b > pos && (A[b - 1] & kKeyMask) > ka; --b) A[b] = A[b - 1];
+        A[b] = wa;
       }
     }
   }
@@ -441,12 +443,33 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   uint32_t n_clusters;
   uint32_t rank = block_exclusive_scan<NT, uint32_t>(lane == 0 ? wroots : 0u, &n_clusters, S.tmp);
   rank = __shfl_sync(kFull, rank, 0);
+  // where the charge sums of phase 5 go (known now that n_clusters is): with
+  // at most kNarrowPixels words, sum q(2c+1) <= 15 * 4095 * 23552 < 2^32, so
+  // 32-bit sums (and a 32-bit division) are exact; larger events use 64 bits.
+  // The 32-bit sums go to shared memory after the two pixel arrays (free
+  // since the row sort) when they fit there and clear of the hit sort's keys
+  // and first ids ([0, 2.5 n_c) words), which the centroid pass writes while
+  // it reads the sums.  Every root starts its cluster's 32-bit sums: the
+  // charge sum (< 15 * 23552 < 2^19) with the cluster's module in bits
+  // 27-31, so the centroid pass reads the module with the sums.
+  const bool narrow = n <= kNarrowPixels;
+  unsigned long long* acc = W.acc + 3 * p0;
+  const bool sums_smem = PS && narrow && 2u * n + 3u * n_clusters <= 2u * tier && 5u * n_clusters <= 4u * n;
+  uint32_t* acc32 = sums_smem ? region + 2 * n : reinterpret_cast<uint32_t*>(acc);  // global: in this event's slice
   const uint32_t lt = (1u << lane) - 1u;
   for (uint32_t base = wlo; base < whi; base += 32) {
     const uint32_t i = base + lane;
     const bool root = i < whi && B[i] == i;
     const uint32_t bal = __ballot_sync(kFull, root);
-    if (root) B[i] = (rank + __popc(bal & lt)) | kRootFlag;
+    if (root) {
+      const uint32_t id = rank + __popc(bal & lt);
+      B[i] = id | kRootFlag;
+      if (narrow) {
+        acc32[3 * id] = ((A[i] >> 22) & 31u) << 27;
+        acc32[3 * id + 1] = 0u;
+        acc32[3 * id + 2] = 0u;
+      }
+    }
     rank += __popc(bal);
   }
   __syncthreads();
@@ -485,23 +508,13 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     }
   }
 
-  // 5. integer charge sums per cluster, then the binary32 centroid.  With at
-  // most kNarrowPixels words, sum q(2c+1) <= 15 * 4095 * 23552 < 2^32, so
-  // 32-bit sums (and a 32-bit division) are exact; larger events use 64 bits.
-  // The 32-bit sums go to shared memory after the two pixel arrays when they
-  // fit there and clear of the hit sort's keys and first ids ([0, 2.5 n_c)
-  // words), which the centroid pass writes while it reads the sums.
-  const bool narrow = n <= kNarrowPixels;
-  unsigned long long* acc = W.acc + 3 * p0;
-  const bool sums_smem = PS && narrow && 2u * n + 3u * n_clusters <= 2u * tier && 5u * n_clusters <= 4u * n;
-  uint32_t* acc32 = sums_smem ? region + 2 * n : reinterpret_cast<uint32_t*>(acc);  // global: in this event's slice
+  // 5. integer charge sums per cluster (32-bit ones started by the roots in
+  // phase 4), then the binary32 centroid.
   *sums = acc32;
-  if (narrow) {
-    for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc32[i] = 0u;
-  } else {
+  if (!narrow) {
     for (uint32_t i = tid; i < 3 * n_clusters; i += NT) acc[i] = 0ull;
+    __syncthreads();
   }
-  __syncthreads();
   for (uint32_t i = tid; i < n; i += NT) {
     const uint32_t w = A[i];
     const uint32_t q = (w >> 27) & 15u, c = w & 2047u, r = (w >> 11) & 2047u;
@@ -564,14 +577,18 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   }
   for (uint32_t id = tid; id < n_clusters; id += NT) {
     float u, v;
+    uint32_t mod;
     if (narrow) {
-      const uint32_t sq = acc32[3 * id], snx = acc32[3 * id + 1], sny = acc32[3 * id + 2];
+      const uint32_t s0 = acc32[3 * id], snx = acc32[3 * id + 1], sny = acc32[3 * id + 2];
+      const uint32_t sq = s0 & 0x7FFFFFFu;
+      mod = s0 >> 27;
       const uint32_t D = 2u * sq;
       const float Df = __uint2float_rn(D);
       u = __fadd_rn(__uint2float_rn(snx / D), __fdiv_rn(__uint2float_rn(snx % D), Df));
       v = __fadd_rn(__uint2float_rn(sny / D), __fdiv_rn(__uint2float_rn(sny % D), Df));
     } else {
       const unsigned long long sq = acc[3 * id], snx = acc[3 * id + 1], sny = acc[3 * id + 2];
+      mod = module_of(mo, M, id);
       const unsigned long long D = 2ull * sq;
       const float Df = __ull2float_rn(D);
       u = __fadd_rn(__ull2float_rn(snx / D), __fdiv_rn(__ull2float_rn(snx % D), Df));
@@ -582,13 +599,13 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
     const float key = pseudo_angle(x, y);
     cxy[id] = make_float2(x, y);
     if (counted) {  // key bits and bucket (< 2^16) of every cluster
-      const uint32_t b = module_of(mo, M, id) << kHitBucketBits | hit_key_fixed(key) >> (19 - kHitBucketBits);
+      const uint32_t b = mod << kHitBucketBits | hit_key_fixed(key) >> (19 - kHitBucketBits);
       KA[id] = __float_as_uint(key);
       VA[id] = (V)b;
       atomicAdd(C + (b >> 1), 1u << ((b & 1u) << 4));
     } else {
       ck[id] = key;
-      KA[id] = module_of(mo, M, id) << 19 | hit_key_fixed(key);
+      KA[id] = mod << 19 | hit_key_fixed(key);
       VA[id] = (V)id;
     }
   }
