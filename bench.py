@@ -33,7 +33,11 @@ sys.path.insert(0, ROOT)
 METRIC = "events/s (1 B300) for VELO-like tracking at pileup 5.5; p99 batch latency"
 UNIT = "events/s"
 WORKLOAD = "C2: 10k events, pileup 5.5 (n_PV~Poisson(5.5), 40 tracks/PV), 26 modules, MS 0.5 mrad, eff 0.99, noise 1e-4"
-STAGES = ("k_cluster", "k_track", "k_scan", "k_output")
+# the intervals between the library's five stage marks: clustering, pattern
+# recognition (k_track and k_track_wide), the fit (k_fit_out: in the fused
+# form it also writes the offsets and the compact output), and the separate
+# scan and output kernels (empty in the fused form)
+STAGES = ("k_cluster", "k_track", "k_fit_out", "k_scan_output")
 
 
 def parse():
@@ -672,8 +676,8 @@ def run_ours(args):
     alg = {
         "k_cluster": 4 * P + 8 * (n_ev + 1) + 12 * n_cl + 4 * n_cl,
         "k_track": 16 * n_cl,
-        "k_scan": 24 * n_ev,
-        "k_output": 8 * n_cl + 12 * n_cl + n_tr * (4 * 20 + 8) + 4 * n_hits,
+        "k_fit_out": 8 * n_hits + 8 * n_cl + 12 * n_cl + n_tr * (4 * 20 + 8) + 4 * n_hits + 24 * n_ev,
+        "k_scan_output": 0,
     }
     achieved = alg[dom] / (stage_ms[dom] / 1000.0) / 1e9
     traffic = profiled_traffic(dom)
@@ -682,9 +686,9 @@ def run_ours(args):
             "peak_source": f"{peak_kind} hbm_gbs (copy)", "stage_ms": stage_ms}
     # DRAM bytes per second measured by ncu (bytes per event of the committed
     # summaries, current sources only) over the live times: of the dominant
-    # stage (the tracking stage holds k_track and k_fit) and of the whole step
-    dram = {k: profiled_traffic(k) for k in ("k_cluster", "k_track", "k_fit", "k_output")}
-    stage_kernels = {"k_track": ("k_track", "k_fit")}.get(dom, (dom,))
+    # stage and of the whole step
+    dram = {k: profiled_traffic(k) for k in ("k_cluster", "k_track", "k_fit_out")}
+    stage_kernels = (dom,)
     if all(dram.get(k) is not None for k in stage_kernels):
         roof["dram_gbs"] = sum(dram[k] for k in stage_kernels) * n_ev / (stage_ms[dom] / 1000.0) / 1e9
         roof["dram_frac"] = roof["dram_gbs"] / peaks["hbm_gbs"]
@@ -708,7 +712,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (event sharding)"},
         "p50_batch_latency_ms": float(np.percentile(lat, 50)), "p99_batch_latency_ms": float(np.percentile(lat, 99)),
         "latency_batch_events": nb,
-        "gpu_launches": 7 * K,  # validate, cluster, track, track (heavy events), fit, scan, output per step
+        "gpu_launches": 5 * K,  # validate, cluster, track, track (heavy events), fit + offsets + output per step
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": e2e,

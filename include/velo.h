@@ -185,9 +185,11 @@ int velo_reconstruct_into(const velo_events_t* events, const velo_geometry_t* ge
 
 /* velo_reconstruct_into plus timing marks: stage_events holds 5 cudaEvent_t
  * handles created by the caller (cast to void*), recorded on `stream` before
- * the clustering kernel, after it, after the tracking kernel, after the
- * offsets scan and after the output kernel.  NULL records nothing.  The
- * marks add no work and no synchronisation. */
+ * the clustering kernel, after it, after the pattern-recognition kernels,
+ * after the fit kernel (which in the fused form, velo_tuning_t.fused_output,
+ * also writes the offsets and the output) and after the offsets-scan and
+ * output kernels (none in the fused form).  NULL records nothing.  The marks
+ * add no work and no synchronisation. */
 int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometry_t* geometry,
                                  const velo_params_t* params, const velo_output_t* out, void* workspace,
                                  uint64_t workspace_bytes, void* stream, void* const* stage_events);
@@ -196,7 +198,7 @@ int velo_reconstruct_into_marked(const velo_events_t* events, const velo_geometr
  * the SMs by work queues; these choose how).  Any valid setting gives the same
  * results bit for bit; speed depends on the workload (autotuned by the Python
  * layer).  velo_tuning_default: 1024 / largest tier / 256 / all resident / 0 /
- * 2^20; start from it (a zeroed struct is rejected with VELO_EINVAL). */
+ * 0 / 2^20; start from it (a zeroed struct is rejected with VELO_EINVAL). */
 typedef struct velo_tuning {
   uint32_t cluster_threads;      /* 512 (two CTAs per SM) or 1024 (one) */
   uint32_t cluster_smem_pixels;  /* words per event sorted in shared memory, 0 = the most that fits;
@@ -209,6 +211,11 @@ typedef struct velo_tuning {
   uint32_t wide_cluster;         /* CTAs (a thread-block cluster of 1024-thread CTAs) tracking each event of
                                     20000 clusters or more: 0 = the largest the device can place (16, else
                                     8), or 8 or 16 (VELO_EINVAL if the device cannot place it) */
+  uint32_t fused_output;         /* 1 = the fit kernel also writes the event offsets (decoupled
+                                    look-back) and the compact output, one launch instead of three,
+                                    when no capacity can be exceeded and no features are asked for;
+                                    0 = separate fit, offsets-scan and output kernels (faster on
+                                    pile-up-5.5 batches) */
   uint32_t union_link_attempts;  /* most link attempts of one union in the clustering's lock-free
                                     union-find before it gives up and its event fails with
                                     VELO_EVT_TIMEOUT (an attempt retries only after losing a race to

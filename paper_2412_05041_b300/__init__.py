@@ -61,7 +61,8 @@ class Output(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("cluster_threads", ctypes.c_uint32), ("cluster_smem_pixels", ctypes.c_uint32),
                 ("track_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("wide_cluster", ctypes.c_uint32), ("union_link_attempts", ctypes.c_uint32)]
+                ("wide_cluster", ctypes.c_uint32), ("fused_output", ctypes.c_uint32),
+                ("union_link_attempts", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -21,10 +21,25 @@ CTAS_PER_EVENT = 0xFFFFFFFF  # one CTA per event (VELO_CTAS_PER_EVENT)
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "velo_b300", "tuning.json")
 
 
+# shared-memory tiers of the clustering kernel: 0 = the most that fits (about
+# 25k words at 1024 threads, one CTA per SM; about 12k at 512 threads, two),
+# or a smaller one (valid for both) that sends larger events to the
+# global-memory path and leaves more of the SM's memory to L1
+TIERS = (0, 8192)
+
+
 def candidates():
+    """Block shapes searched: clustering threads (one 1024-thread or two
+    512-thread CTAs per SM), its shared-memory tier, tracking threads per
+    event, the persistent grid (every resident CTA, at most two per SM, or
+    one CTA per event scheduled by the hardware), and the fit fused with the
+    offsets and the output."""
     out = []
-    for ct, tt, cps in itertools.product((1024, 512), (128, 256), (0, 2, CTAS_PER_EVENT)):
-        out.append(default_tuning(cluster_threads=ct, cluster_smem_pixels=0, track_threads=tt, ctas_per_sm=cps))
+    for ct, tier, tt, cps in itertools.product((1024, 512), TIERS, (128, 256), (0, 2, CTAS_PER_EVENT)):
+        out.append(default_tuning(cluster_threads=ct, cluster_smem_pixels=tier, track_threads=tt, ctas_per_sm=cps))
+    # the fit with the offsets and the output in one kernel (fewer launches)
+    out.append(default_tuning(fused_output=1))
+    out.append(default_tuning(track_threads=128, fused_output=1))
     return out
 
 

@@ -55,6 +55,8 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   ws->trk_hoff = c.take<uint32_t>(T);
   ws->trk_logit = c.take<float>(T);
   ws->trk_state = c.take<float>(T * VELO_STATE_STRIDE);
+  ws->lb_flag = c.take<uint32_t>(E);
+  ws->lb_val = c.take<unsigned long long>(8 * E);
 }
 
 bool geometry_ok(const velo_geometry_t* g) {
@@ -282,6 +284,7 @@ int velo_tuning_default(velo_tuning_t* t) {
   t->track_threads = 256;
   t->ctas_per_sm = 0;
   t->wide_cluster = 0;
+  t->fused_output = 0;
   t->union_link_attempts = 1u << 20;
   return VELO_OK;
 }
@@ -299,7 +302,7 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   if (tuning) tu = *tuning;
   if ((tu.cluster_threads != 512 && tu.cluster_threads != 1024) ||
       (tu.track_threads != 128 && tu.track_threads != 256) ||
-      (tu.wide_cluster != 0 && tu.wide_cluster != 8 && tu.wide_cluster != 16))
+      (tu.wide_cluster != 0 && tu.wide_cluster != 8 && tu.wide_cluster != 16) || tu.fused_output > 1u)
     return VELO_EINVAL;
   const uint32_t max_tier = cluster_max_tier((int)tu.cluster_threads);
   const uint32_t tier = tu.cluster_smem_pixels ? tu.cluster_smem_pixels : max_tier;
@@ -338,10 +341,24 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   if (E) rc = launch_track(L, (int)tu.track_threads, (uint32_t)E, tu.wide_cluster, s);  // one CTA per event
   if (rc != VELO_OK) return rc;
   mark(2);
-  k_scan<<<1, kScanThreads, 0, s>>>(L);
-  mark(3);
-  if (E) rc = launch_output(L, grid(output_blocks_per_sm(L.out.track_features != nullptr)), s);
+  // In the fused form the fit writes the compact output itself (offsets by
+  // a decoupled look-back), unless the candidate features are asked for or
+  // the output could exceed a capacity the caller set (then nothing may be
+  // written, so the totals must be known first: the separate scan and output
+  // kernels).
+  const uint64_t P = L.n_pixels;
+  const bool fits_always = (!out->cap_clusters || out->cap_clusters >= P) &&
+                           (!out->cap_tracks || out->cap_tracks >= P / 3) &&
+                           (!out->cap_track_hits || out->cap_track_hits >= P);
+  const bool fused = tu.fused_output && E && !out->track_features && fits_always;
+  if (E) rc = launch_fit(L, fused, s);
   if (rc != VELO_OK) return rc;
+  mark(3);
+  if (!fused) {
+    k_scan<<<1, kScanThreads, 0, s>>>(L);
+    if (E) rc = launch_output(L, grid(output_blocks_per_sm(L.out.track_features != nullptr)), s);
+    if (rc != VELO_OK) return rc;
+  }
   mark(4);
   return cudaGetLastError() == cudaSuccess ? VELO_OK : VELO_ECUDA;
 }

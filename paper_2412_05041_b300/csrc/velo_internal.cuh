@@ -66,6 +66,9 @@ struct Workspace {
   uint32_t* trk_hoff;        // first hit of the track among the event's kept hits
   float* trk_logit;          // the network's logit (learned rejection)
   float* trk_state;          // VELO_STATE_STRIDE floats per track: the fit's state, written by k_fit
+  uint32_t* lb_flag;         // [E] look-back record state of the fused fit: 0 none, 1 aggregate, 2 prefix
+  unsigned long long* lb_val;// [E * 8] the event's counts (clusters, kept tracks, hits, failed), then
+                             // the inclusive prefix of those counts over the events up to it
 };
 
 struct Geo {
@@ -105,6 +108,7 @@ __global__ void k_validate_offsets(Launch L);
 __global__ void k_scan(Launch L);
 int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s);
 int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, cudaStream_t s);
+int launch_fit(const Launch& L, bool fused, cudaStream_t s);  // k_fit_out, or k_fit (k_scan and k_output follow)
 int launch_output(const Launch& L, uint32_t grid, cudaStream_t s);
 uint32_t cluster_smem_bytes(int nt, uint32_t tier);
 uint32_t cluster_max_tier(int nt);

@@ -667,11 +667,9 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
 // chi2/ndf (or scored by the ghost-rejection network on tensor cores), and
 // the kept ones are ranked by their smallest cluster id.  A kernel of its
 // own, so that the module loop runs with fewer registers and more CTAs.
-__global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
-  __shared__ FitSmem S;
+__device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, FitSmem& S) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
-  const uint64_t e = blockIdx.x;
   const Par P = L.par;
   const uint32_t M = L.geo.n_modules;
   if (P.use_mlp) mlp_load(P.mlp, S.mlp, tid, kFitThreads);  // network constants
@@ -786,6 +784,12 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
     W.ev_ntracks[e] = (uint32_t)(tot >> 32);
     W.ev_nhits[e] = (uint32_t)tot;
   }
+}
+
+// The fit of the separate form (one CTA per event; k_scan and k_output follow).
+__global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
+  __shared__ FitSmem S;
+  fit_event(L, blockIdx.x, S);
 }
 
 // Compaction: clusters and kept tracks of event e into the caller's CSR
@@ -904,6 +908,112 @@ __global__ void __launch_bounds__(kOutputThreads, FEAT ? 1 : 6) k_output(Launch 
   }
 }
 
+// Fit, offsets and output in one kernel (the fused form, for batches whose
+// output cannot exceed the caller's capacities).  Every CTA takes the next
+// event from a ticket counter, so the events before it have all started;
+// it fits the event's tracks (as k_fit), publishes the event's counts
+// (clusters, kept tracks, their hits, failed) and finds the counts of all
+// the events before it by a decoupled look-back: one warp reads the records
+// of the 32 events before its window at once, adding aggregates until it
+// meets an event that already published its inclusive prefix.  It then
+// publishes its own inclusive prefix, writes its event's offsets and its
+// clusters and tracks straight into the caller's CSR arrays (as k_output),
+// and the last event writes the closing offsets and the totals.  Every wait
+// on another event's record is bounded; a wait that gives up (not expected:
+// the events waited for are running) fails this event with
+// VELO_EVT_TIMEOUT instead of hanging, and its record never holds a prefix.
+__global__ void __launch_bounds__(kFitThreads, 4) k_fit_out(Launch L) {
+  __shared__ FitSmem S;
+  __shared__ uint32_t ticket;
+  __shared__ unsigned long long prefix[4];
+  __shared__ bool gave_up;
+  const Workspace& W = L.ws;
+  const uint32_t tid = threadIdx.x, lane = lane_id();
+  if (tid == 0) {
+    ticket = atomicAdd(W.queue + 6, 1u);
+    gave_up = false;
+  }
+  __syncthreads();
+  const uint64_t e = ticket;
+  fit_event(L, e, S);
+  __syncthreads();
+  unsigned long long* rec = W.lb_val + 8 * e;  // aggregate [0, 4), inclusive prefix [4, 8)
+  if (tid == 0) {
+    const bool failed = *(const volatile uint32_t*)W.flag != 0u || L.out.status[e] != VELO_EVT_OK;
+    rec[0] = failed ? 0ull : W.ev_nclusters[e];
+    rec[1] = W.ev_ntracks[e];
+    rec[2] = W.ev_nhits[e];
+    rec[3] = failed ? 1ull : 0ull;
+    __threadfence();
+    atomicExch(W.lb_flag + e, 1u);
+  }
+  if (tid < 32) {
+    constexpr uint32_t kSpinLimit = 1u << 22;  // x 64 ns: a wait gives up after about a quarter second
+    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+    int64_t j = (int64_t)e - 1;  // the window of events j, j - 1, ..., j - 31 (lane l reads j - l)
+    bool done = j < 0, bad = false;
+    while (!done) {
+      const int64_t q = j - (int64_t)lane;
+      uint32_t fl = 2u;  // before event 0: an empty inclusive prefix
+      if (q >= 0) {
+        uint32_t it = 0;
+        while ((fl = *(const volatile uint32_t*)(W.lb_flag + q)) == 0u && ++it < kSpinLimit) __nanosleep(64);
+      }
+      if (__any_sync(kFull, fl == 0u)) {
+        bad = true;
+        break;
+      }
+      __threadfence();  // the records' values after their flags
+      const uint32_t incl = __ballot_sync(kFull, fl == 2u);
+      const uint32_t stop = incl ? (uint32_t)__ffs(incl) - 1u : 31u;  // the lanes up to it contribute
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        unsigned long long v = 0ull;
+        if (q >= 0 && lane <= stop) v = *(const volatile unsigned long long*)(W.lb_val + 8 * q + (fl == 2u ? 4 : 0) + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        acc[k] += v;
+      }
+      done = incl != 0u;
+      j -= 32;
+    }
+    if (lane == 0) {
+      if (bad) {
+        gave_up = true;
+      } else {
+        for (int k = 0; k < 4; ++k) {
+          prefix[k] = acc[k];
+          rec[4 + k] = acc[k] + rec[k];
+        }
+        __threadfence();
+        atomicExch(W.lb_flag + e, 2u);
+      }
+    }
+  }
+  __syncthreads();
+  if (gave_up) {
+    if (tid == 0) L.out.status[e] = VELO_EVT_TIMEOUT;
+    return;
+  }
+  if (tid == 0) {
+    L.out.cluster_offsets[e] = prefix[0];
+    L.out.track_offsets[e] = prefix[1];
+    W.ev_hitbase[e] = prefix[2];
+    if (e + 1 == L.n_events) {  // the closing offsets and the totals
+      const unsigned long long tc = rec[4], tt = rec[5], th = rec[6], tf = rec[7];
+      L.out.cluster_offsets[e + 1] = tc;
+      L.out.track_offsets[e + 1] = tt;
+      L.out.track_hit_offsets[tt] = th;
+      L.out.totals[0] = tc;
+      L.out.totals[1] = tt;
+      L.out.totals[2] = th;
+      L.out.totals[3] = tf;
+    }
+  }
+  __syncthreads();
+  output_one<false>(L, e, S.mod_off, S.z);
+}
+
 // One CTA: event offsets into the output CSR arrays and the batch totals.
 __global__ void __launch_bounds__(kScanThreads) k_scan(Launch L) {
   constexpr int NT = kScanThreads;
@@ -959,8 +1069,9 @@ __global__ void __launch_bounds__(kScanThreads) k_validate_offsets(Launch L) {
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     *L.ws.flag = bad ? 1u : 0u;
-    for (int q = 0; q < 8; ++q) L.ws.queue[q] = 0u;  // the persistent kernels' work queues
+    for (int q = 0; q < 8; ++q) L.ws.queue[q] = 0u;  // the persistent kernels' work queues, the fit tickets
   }
+  for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.ws.lb_flag[e] = 0u;  // the fused fit's look-back
   if (bad) {
     for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.out.status[e] = VELO_EVT_BADWORD;
     if (L.out.pixel_cluster)
@@ -1025,7 +1136,13 @@ int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (cudaLaunchKernelEx(&cfg, k_track_wide, L) != cudaSuccess) return VELO_ECUDA;
-  k_fit<<<grid, kFitThreads, 0, s>>>(L);
+  return VELO_OK;
+}
+
+int launch_fit(const Launch& L, bool fused, cudaStream_t s) {
+  const uint32_t grid = (uint32_t)L.n_events;  // one CTA per event
+  if (fused) k_fit_out<<<grid, kFitThreads, 0, s>>>(L);
+  else k_fit<<<grid, kFitThreads, 0, s>>>(L);
   return VELO_OK;
 }
 

@@ -441,3 +441,23 @@ def test_union_find_bound_fails_its_event_only():
     rs = oracle.reconstruct(so, sp, geo, op)
     assert_same(t, rs, events=good)
     assert_labels(t["pixel_cluster"], rs["pixel_cluster"], offsets, so, events=good)
+
+
+def test_fused_fit_and_output_equal_the_separate_kernels():
+    """The fit that also writes the offsets (decoupled look-back over the
+    events) and the compact output gives the bytes of the separate fit, scan
+    and output kernels -- on ragged events with empty, failed and heavy ones,
+    and on a batch of normal events -- and the oracle's results."""
+    vp, op = params(5e-4)
+    geo = velogen.Geometry()
+    offsets, pixels = edge_batch()
+    c2 = velogen.generate(velogen.C2, n_events=200, first_event=5000)
+    for off, pix in ((offsets, pixels), (c2.offsets, c2.pixels)):
+        o = torch.from_numpy(np.ascontiguousarray(off, np.uint64).view(np.int64)).cuda()
+        p = torch.from_numpy(np.ascontiguousarray(pix, np.uint32).view(np.int32)).cuda()
+        sep = to_numpy(velo.reconstruct(o, p, geo, vp, pixel_labels=True))
+        fus = to_numpy(velo.reconstruct(o, p, geo, vp, pixel_labels=True,
+                                        tuning=velo.default_tuning(fused_output=1)))
+        for k in sep:
+            np.testing.assert_array_equal(fus[k], sep[k], err_msg=k)
+        assert_same(fus, oracle.reconstruct(off, pix, geo, op))
