@@ -30,6 +30,7 @@ void carve(Carver& c, uint64_t E, uint64_t P, Workspace* ws) {
   ws->flag = c.take<uint32_t>(4);
   ws->queue = c.take<uint32_t>(8);
   ws->wide_list = c.take<uint32_t>(E);
+  ws->heavy_list = c.take<uint32_t>(E);
   ws->order = c.take<uint32_t>(E);
   ws->ev_nclusters = c.take<uint32_t>(E);
   ws->ev_modoff = c.take<uint32_t>(E * kModOffStride);

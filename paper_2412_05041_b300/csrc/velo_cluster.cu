@@ -26,6 +26,11 @@
 // slice of the global workspace (generic pointers).
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "velo_device.cuh"
 #include "velo_internal.cuh"
 
@@ -52,6 +57,9 @@ constexpr uint32_t kHitBucketBits = 8;
 // Events of at least this many words (kept in the workspace) index the first
 // sorted position of every (module, row): 32 modules x 2048 rows.
 constexpr uint32_t kRowTable = 1u << 16;
+// Sub-events (modules of heavy events) of at least this many words use a row
+// table of their one module (2048 entries in their own word range).
+constexpr uint32_t kSubRowTable = 4096;
 
 __device__ __forceinline__ uint32_t vload(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 
@@ -116,6 +124,23 @@ __device__ __forceinline__ uint32_t module_of(const uint32_t* mod_off, uint32_t 
   return lo;
 }
 
+// A sub-event: one module of a heavy event, clustered by one CTA of the
+// heavy-event kernel (k_cluster_wide) in shared memory.  Its words come from
+// the module-grouped copy of the event, with their positions in the event's
+// input; its clusters take the event-wide ids id_base + local id and its hits
+// the event-wide positions id_base + local position.  The event's own records
+// (status, module offsets, counts, lists) are left to the heavy kernel, and a
+// failure only raises *fail (the heavy kernel then fails the event).
+struct Sub {
+  bool on = false;
+  bool count_only = false;          // first pass: stop once the clusters are counted
+  const uint32_t* words = nullptr;  // the module's words
+  const uint32_t* index = nullptr;  // their positions in the event's input
+  uint64_t ev_p0 = 0;               // the event's first word
+  uint32_t id_base = 0;             // event-wide id of the module's first cluster
+  uint32_t* fail = nullptr;         // VELO_EVT_* code of a failure, 0 if none
+};
+
 __device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offsets_ok, uint64_t p0, uint32_t n) {
   if (threadIdx.x == 0) {
     L.out.status[e] = code;
@@ -136,7 +161,7 @@ __device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offse
 template <int NT, bool PS>
 __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S,
                                                  uint32_t* region, const uint32_t tier, const uint64_t p0,
-                                                 const uint32_t n, uint32_t** sums) {
+                                                 const uint32_t n, uint32_t** sums, const Sub& sub) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
@@ -164,19 +189,20 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   bool counted = false;
   if constexpr (PS) {
     const uint32_t nrow = L.geo.n_rows;
+    const uint32_t Mg = sub.on ? 1u : M;  // a sub-event's words all lie on one module
     bool fits = false;
     uint32_t gshift = 11, ngrp = nrow, cw = 0;  // group = key >> gshift: (module, row), else (module, row pair)
     for (int pass = 0; pass < 2 && !fits; ++pass) {
       gshift = 11u + (uint32_t)pass;
       ngrp = (nrow + (uint32_t)pass) >> pass;
-      cw = (M * ngrp + 1u) / 2u;  // u32 words of 16-bit counter pairs
+      cw = (Mg * ngrp + 1u) / 2u;  // u32 words of 16-bit counter pairs
       fits = n < 65536u && 2u * n + cw <= 2u * tier;
     }
     if (fits) {
       counted = true;
       uint32_t* C = region + 2 * n;
       const uint32_t rmask = 2047u >> (gshift - 11u);
-      auto group = [&](uint32_t w) { return ((w >> 22) & 31u) * ngrp + ((w >> gshift) & rmask); };
+      auto group = [&](uint32_t w) { return (sub.on ? 0u : (w >> 22) & 31u) * ngrp + ((w >> gshift) & rmask); };
       for (uint32_t q = tid; q < cw; q += NT) C[q] = 0u;
       __syncthreads();
       for (uint32_t i = tid; i < n; i += NT) {
@@ -286,19 +312,24 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   // root, so every component ends with its smallest sorted position, i.e. its
   // smallest (module, row, col), as root -- whatever the thread order.
   bool ok = true;
-  if (!PS && n >= kRowTable) {
-    // Large events (words in the workspace): a table of the first sorted
-    // position of every (module, row) -- in the hit-sort scratch, free until
-    // then -- gives the previous row's words directly, so every word finds
-    // all its earlier neighbours (duplicates and the left neighbour just
-    // before it, the previous row by bisection of that row) and only the
-    // V-shaped ones are united in pass b.
-    uint32_t* rt = W.sc + p0;
-    for (uint32_t q = tid; q < kRowTable; q += NT) rt[q] = n;
+  if ((!PS && n >= kRowTable) || (sub.on && n >= kSubRowTable)) {
+    // Large events (words in the workspace) and large sub-events (the dense
+    // modules of heavy events): a table of the first sorted position of every
+    // (module, row) -- in the hit-sort scratch, free until then; a sub-event's
+    // rows of its one module, module * 2048 + row at rt[row] -- gives the
+    // previous row's words directly, so every word finds all its earlier
+    // neighbours (duplicates and the left neighbour just before it, the
+    // previous row by bisection of that row) and only the V-shaped ones are
+    // united in pass b.
+    const uint32_t rbase = sub.on ? ((A[0] & kKeyMask) >> 22) << 11 : 0u;
+    const uint32_t rsize = sub.on ? 2048u : kRowTable;
+    uint32_t* rt = W.sc + p0;  // rt[mr - rbase] for mr = module * 2048 + row
+    auto row_start = [&](uint32_t mr) { return rt[mr - rbase]; };
+    for (uint32_t q = tid; q < rsize; q += NT) rt[q] = n;
     __syncthreads();
     for (uint32_t pos = tid; pos < n; pos += NT) {
-      const uint32_t mr = (A[pos] & kKeyMask) >> 11, mp = pos ? ((A[pos - 1] & kKeyMask) >> 11) + 1u : 0u;
-      for (uint32_t q = mp; q <= mr; ++q) rt[q] = pos;
+      const uint32_t mr = (A[pos] & kKeyMask) >> 11, mp = pos ? ((A[pos - 1] & kKeyMask) >> 11) + 1u : rbase;
+      for (uint32_t q = mp; q <= mr; ++q) rt[q - rbase] = pos;
     }
     __syncthreads();
     for (uint32_t i = tid; i < n; i += NT) {
@@ -316,9 +347,9 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
       if (r > 0u) {
         const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u), hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
         const uint32_t mr = k >> 11;
-        uint32_t j = lower_bound_by(rt[mr - 1u], rt[mr], [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
-        if (j < rt[mr] && (A[j] & kKeyMask) <= hi_k) nb_min = j;  // the smallest earlier neighbour
-        for (; j < rt[mr]; ++j) {
+        uint32_t j = lower_bound_by(row_start(mr - 1u), row_start(mr), [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+        if (j < row_start(mr) && (A[j] & kKeyMask) <= hi_k) nb_min = j;  // the smallest earlier neighbour
+        for (; j < row_start(mr); ++j) {
           const uint32_t pc = A[j] & 2047u;  // previous-row column c-1, c or c+1
           if ((A[j] & kKeyMask) > hi_k) break;
           up_left |= pc + 1u == c;
@@ -342,8 +373,8 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
       if (r > 0u) {
         const uint32_t lo_k = k - 2048u - (c > 0u ? 1u : 0u), hi_k = k - 2048u + (c + 1u < L.geo.n_cols ? 1u : 0u);
         const uint32_t mr = k >> 11;
-        uint32_t j = lower_bound_by(rt[mr - 1u], rt[mr], [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
-        for (; j < rt[mr] && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j, L.union_link_attempts);
+        uint32_t j = lower_bound_by(row_start(mr - 1u), row_start(mr), [&](uint32_t x) { return (A[x] & kKeyMask) < lo_k; });
+        for (; j < row_start(mr) && (A[j] & kKeyMask) <= hi_k; ++j) ok &= uf_unite(B, i, j, L.union_link_attempts);
       }
     }
   } else {
@@ -417,6 +448,10 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   if (!ok) S.flag = 2u;
   __syncthreads();
   if (S.flag) {  // a union gave up after its bounded link attempts
+    if (sub.on) {
+      if (tid == 0) atomicMax(sub.fail, (uint32_t)VELO_EVT_TIMEOUT);
+      return kNone;
+    }
     fail_event(L, e, VELO_EVT_TIMEOUT, true, p0, n);
     return kNone;
   }
@@ -495,16 +530,22 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   }
   __syncthreads();
   if (S.flag) {
+    if (sub.on) {
+      if (tid == 0) atomicMax(sub.fail, (uint32_t)VELO_EVT_OVERFLOW);
+      return kNone;
+    }
     fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
     return kNone;
   }
+  if (sub.count_only) return n_clusters;
 
-  // optional per-word labels in input order
+  // optional per-word labels in input order (a sub-event's at its words' event positions)
   if (L.out.pixel_cluster) {
     for (uint32_t i = tid; i < n; i += NT) {
-      const uint32_t k = __ldg(L.pix + p0 + i) & kKeyMask;
+      const uint32_t k = (sub.on ? sub.words[i] : __ldg(L.pix + p0 + i)) & kKeyMask;
       const uint32_t j = lower_bound_by(0u, n, [&](uint32_t x) { return (A[x] & kKeyMask) < k; });
-      L.out.pixel_cluster[p0 + i] = j < n ? B[j] : kNone;  // j < n always: the word is in A
+      const uint32_t label = j < n ? sub.id_base + B[j] : kNone;  // j < n always: the word is in A
+      L.out.pixel_cluster[sub.on ? sub.ev_p0 + sub.index[i] : p0 + i] = label;
     }
   }
 
@@ -540,7 +581,7 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
 template <int NT, bool HS>
 __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
                                            const uint32_t tier, const uint64_t p0, const uint32_t n,
-                                           const uint32_t n_clusters, const uint32_t* acc32) {
+                                           const uint32_t n_clusters, const uint32_t* acc32, const Sub& sub) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const uint32_t M = L.geo.n_modules;
@@ -557,7 +598,7 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   uint32_t* KB = HS ? region + n_clusters : W.sb + p0;
   V* VA = HS ? reinterpret_cast<V*>(region + 2 * n_clusters) : reinterpret_cast<V*>(W.sc + p0);
   V* VB = HS ? reinterpret_cast<V*>(region + 2 * n_clusters) + n_clusters : reinterpret_cast<V*>(W.sd + p0);
-  float2* cxy = W.cl_xy + p0;
+  float2* cxy = sub.on ? W.cl_xy + sub.ev_p0 + sub.id_base : W.cl_xy + p0;  // by (local) id
   float* ck = reinterpret_cast<float*>(HS ? W.sc + p0 : W.h_pos + p0);
   const Geo& g = L.geo;
   const uint32_t* mo = S.mod_off;
@@ -688,9 +729,11 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   for (uint32_t pos = tid; pos < n_clusters; pos += NT) {
     const uint32_t id = VB[pos];
     const float2 c = cxy[id];
-    W.hit[p0 + pos] = make_float4(c.x, c.y, __uint_as_float(KS[pos]), __uint_as_float(id));
-    W.h_pos[p0 + id] = pos;
+    const uint64_t base = sub.on ? sub.ev_p0 + sub.id_base : p0;  // a sub-event's hits at their event-wide places
+    W.hit[base + pos] = make_float4(c.x, c.y, __uint_as_float(KS[pos]), __uint_as_float(sub.id_base + id));
+    W.h_pos[base + id] = sub.id_base + pos;
   }
+  if (sub.on) return;  // the heavy kernel writes the event's records
   if (tid <= M) W.ev_modoff[e * kModOffStride + tid] = S.mod_off[tid];
   if (tid == 0) {
     W.ev_nclusters[e] = n_clusters;
@@ -701,15 +744,21 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
 
 // The clustering of event e by one CTA of NT threads; `tier` = most words
 // kept in shared memory (the region holds 2 * tier words).
+// (With sub.on: module m of a heavy event, whose words lie at [p0, p0 + n) of
+// the event's word slices: the sub-event's scratch.)
 template <int NT>
-__device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
-                                            const uint32_t tier) {
+__device__ __forceinline__ uint32_t cluster_one(const Launch& L, const uint64_t e, ClusterSmem<NT>& S, uint32_t* region,
+                                            const uint32_t tier, const Sub& sub = Sub(), uint64_t sub_p0 = 0,
+                                            uint32_t sub_n = 0) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
 
-  const bool offsets_ok = *(const volatile uint32_t*)W.flag == 0u;
+  const bool offsets_ok = sub.on || *(const volatile uint32_t*)W.flag == 0u;
   uint64_t p0 = 0, p1 = 0;
-  if (offsets_ok) {
+  if (sub.on) {
+    p0 = sub_p0;
+    p1 = sub_p0 + sub_n;
+  } else if (offsets_ok) {
     p0 = L.off[e];
     p1 = L.off[e + 1];
   }
@@ -719,7 +768,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   // the words of event e + gridDim.x (taken, most likely, in the next round
   // by some CTA) into L2 meanwhile, one 128-byte line per thread at a time
   // (the offsets are valid: every range lies inside the pixel array)
-  if (offsets_ok && e + gridDim.x < L.n_events) {
+  if (!sub.on && offsets_ok && e + gridDim.x < L.n_events) {
     const uint64_t q0 = L.off[e + gridDim.x], q1 = L.off[e + gridDim.x + 1];
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(L.pix + q0) & ~uintptr_t(127);
     const uintptr_t a1 = reinterpret_cast<uintptr_t>(L.pix + q1);
@@ -734,7 +783,7 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
     bool bad = false;
 #pragma unroll 4
     for (uint32_t i = tid; i < n; i += NT) {
-      const uint32_t w = __ldg(L.pix + p0 + i);
+      const uint32_t w = sub.on ? sub.words[i] : __ldg(L.pix + p0 + i);
       bad |= !word_valid(w, L.geo);
       A[i] = w;
     }
@@ -742,15 +791,20 @@ __device__ __forceinline__ void cluster_one(const Launch& L, const uint64_t e, C
   }
   __syncthreads();
   if (S.flag) {
+    if (sub.on) {  // the heavy kernel validated the words (not expected)
+      if (tid == 0) atomicMax(sub.fail, (uint32_t)VELO_EVT_BADWORD);
+      return kNone;
+    }
     fail_event(L, e, VELO_EVT_BADWORD, offsets_ok, p0, n);
-    return;
+    return kNone;
   }
   uint32_t* sums = nullptr;
-  const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n, &sums)
-                                        : pixel_phases<NT, false>(L, e, S, region, tier, p0, n, &sums);
-  if (n_clusters == kNone) return;
-  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, tier, p0, n, n_clusters, sums);
-  else hit_phases<NT, false>(L, e, S, region, tier, p0, n, n_clusters, sums);
+  const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n, &sums, sub)
+                                        : pixel_phases<NT, false>(L, e, S, region, tier, p0, n, &sums, sub);
+  if (n_clusters == kNone || sub.count_only) return n_clusters;
+  if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, tier, p0, n, n_clusters, sums, sub);
+  else hit_phases<NT, false>(L, e, S, region, tier, p0, n, n_clusters, sums, sub);
+  return n_clusters;
 }
 
 // Persistent: every CTA takes events from the work queue until it is empty,
@@ -766,6 +820,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cluster(Launch L) {
     const uint32_t e = S.next;
     __syncthreads();
     if (e >= L.n_events) break;
+    // heavy-ion-like events are left to k_cluster_wide (listed when the offsets are valid)
+    if (*(const volatile uint32_t*)L.ws.flag == 0u && L.off[e + 1] - L.off[e] >= kHeavyWords) continue;
     cluster_one<NT>(L, e, S, region, L.cluster_tier);
     if (threadIdx.x == 0) {  // the event's place in the tracking order (its count was written by this thread)
       const bool large = L.ws.ev_nclusters[e] >= kLargeEvent;
@@ -775,6 +831,234 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cluster(Launch L) {
     }
     __syncthreads();
   }
+}
+
+// Cross-CTA records of k_cluster_wide: every CTA's own, read by the others
+// through distributed shared memory; the event-wide ones live in rank 0's.
+struct WideShared {
+  uint32_t cnt[VELO_MAX_MODULES];    // words of each module in this CTA's slice of the event
+  uint32_t base[VELO_MAX_MODULES];   // where this CTA's words of each module go in the grouped copy
+  uint32_t mo[kModOffStride];        // module word offsets of the grouped copy
+  uint32_t cb[kModOffStride];        // module cluster offsets (first event-wide id of each module)
+  uint32_t order[VELO_MAX_MODULES];  // the non-empty modules, most words first
+  uint32_t n_jobs;                   // how many
+  uint32_t next;                     // this CTA's current module job
+  // rank 0 only:
+  uint32_t nclu[VELO_MAX_MODULES];   // clusters of each module (first pass)
+  uint32_t job[2];                   // the next module job of each pass
+  uint32_t bad;                      // a word of the event is invalid
+  uint32_t fail;                     // a module's failure (VELO_EVT_*), 0 if none
+};
+
+// Heavy-ion-like events (kHeavyWords words or more), one thread-block
+// cluster of CTAs of 1024 threads per event.  Clusters never span modules,
+// so every module is a sub-event of about a C2 event's size that one CTA
+// clusters in shared memory with the ordinary code:
+//  1. every CTA counts (and validates) the words of its slice of the event
+//     by module; the module offsets follow, and every CTA scatters its words
+//     into a module-grouped copy of the event (words in sa, their input
+//     positions in sb);
+//  2. first pass: the CTAs take modules from a cluster-wide counter (most
+//     words first) and count each module's clusters;
+//  3. the module cluster offsets give every module its first event-wide
+//     id; second pass: every module is clustered again and writes its
+//     labels, centroids and hit records at their event-wide places;
+//  4. rank 0 writes the event's records (status, module offsets, counts,
+//     lists).
+// A module larger than the shared-memory tier, or with too many clusters
+// for the shared-memory hit sort, sends the whole event to rank 0 alone
+// (the ordinary one-CTA path from the input words).
+constexpr uint32_t kClusterWideMax = 16, kClusterWidePortable = 8;
+
+__global__ void __launch_bounds__(1024, 1) k_cluster_wide(Launch L, uint32_t tier) {
+  constexpr int NT = 1024;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  ClusterSmem<NT>& S = *reinterpret_cast<ClusterSmem<NT>*>(smem_raw);
+  uint32_t* region = reinterpret_cast<uint32_t*>(smem_raw + sizeof(ClusterSmem<NT>));
+  __shared__ WideShared X;
+  const Workspace& W = L.ws;
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t CS = cl.num_blocks(), rank = cl.block_rank(), tid = threadIdx.x;
+  WideShared* X0 = cl.map_shared_rank(&X, 0);
+  const uint32_t M = L.geo.n_modules;
+  const uint32_t count = *(const volatile uint32_t*)(W.queue + 7);
+  const uint32_t wid = warp_id();
+  for (uint32_t q = blockIdx.x / CS; q < count; q += gridDim.x / CS) {
+    const uint64_t e = W.heavy_list[q];
+    const uint64_t p0 = L.off[e];
+    const uint32_t n = (uint32_t)(L.off[e + 1] - p0);
+    // ---- 1. per-module word counts of this CTA's slice (per-warp counters), validation
+    const uint32_t s0 = (uint32_t)((uint64_t)n * rank / CS), s1 = (uint32_t)((uint64_t)n * (rank + 1) / CS);
+    S.cnt[tid] = 0u;  // 32 warps x 32 modules
+    if (rank == 0 && tid == 0) {
+      X.job[0] = X.job[1] = 0u;
+      X.bad = X.fail = 0u;
+    }
+    __syncthreads();
+    bool bad = false;
+    for (uint32_t i = s0 + tid; i < s1; i += NT) {
+      const uint32_t w = __ldg(L.pix + p0 + i);
+      if (word_valid(w, L.geo)) atomicAdd(&S.cnt[wid * 32u + ((w >> 22) & 31u)], 1u);
+      else bad = true;
+    }
+    if (bad) atomicOr(&X0->bad, 1u);
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t c = 0;
+      for (uint32_t w = 0; w < NT / 32; ++w) c += S.cnt[w * 32u + tid];
+      X.cnt[tid] = c;
+    }
+    cl.sync();  // every CTA's counts, the bad-word flag
+    const bool ev_bad = *(volatile uint32_t*)&X0->bad != 0u;
+    if (!ev_bad) {
+      if (tid < 32) {  // module totals and this CTA's share before it
+        uint32_t tot = 0, mine = 0;
+        for (uint32_t r = 0; r < CS; ++r) {
+          const uint32_t c = cl.map_shared_rank(&X, r)->cnt[tid];
+          tot += c;
+          if (r < rank) mine += c;
+        }
+        X.base[tid] = mine;
+        X.cb[tid] = tot;  // (module word totals until the offsets are taken)
+      }
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t o = 0;
+        for (uint32_t m = 0; m < VELO_MAX_MODULES; ++m) {
+          X.mo[m] = o;
+          X.base[m] += o;
+          o += X.cb[m];
+        }
+        X.mo[VELO_MAX_MODULES] = o;
+        // the non-empty modules, most words first (a selection over at most 32)
+        uint32_t k = 0;
+        for (uint32_t m = 0; m < M; ++m)
+          if (X.cb[m]) X.order[k++] = m;
+        for (uint32_t a = 0; a < k; ++a)
+          for (uint32_t b = a + 1; b < k; ++b)
+            if (X.cb[X.order[b]] > X.cb[X.order[a]]) {
+              const uint32_t t = X.order[a];
+              X.order[a] = X.order[b];
+              X.order[b] = t;
+            }
+        X.n_jobs = k;
+      }
+      __syncthreads();
+      for (uint32_t i = s0 + tid; i < s1; i += NT) {  // the module-grouped copy
+        const uint32_t w = __ldg(L.pix + p0 + i);
+        const uint32_t pos = atomicAdd(&X.base[(w >> 22) & 31u], 1u);
+        W.sa[p0 + pos] = w;
+        W.sb[p0 + pos] = i;
+      }
+    }
+    cl.sync();  // the grouped copy is complete
+    uint32_t big = 0;  // a module too large for the shared-memory tier
+    if (!ev_bad)
+      for (uint32_t m = 0; m < M; ++m) big |= X.mo[m + 1] - X.mo[m] > tier;
+    if (!ev_bad && !big) {
+      // ---- 2, 3. the two passes over the modules
+      for (int pass = 0; pass < 2; ++pass) {
+        for (;;) {
+          if (tid == 0) X.next = atomicAdd(&X0->job[pass], 1u);
+          __syncthreads();
+          const uint32_t j = X.next;
+          __syncthreads();
+          if (j >= X.n_jobs) break;
+          const uint32_t m = X.order[j];
+          Sub sub;
+          sub.on = true;
+          sub.count_only = pass == 0;
+          sub.words = W.sa + p0 + X.mo[m];
+          sub.index = W.sb + p0 + X.mo[m];
+          sub.ev_p0 = p0;
+          sub.id_base = pass == 0 ? 0u : X.cb[m];
+          sub.fail = &X0->fail;
+          const uint32_t nc = cluster_one<NT>(L, e, S, region, tier, sub, p0 + X.mo[m], X.mo[m + 1] - X.mo[m]);
+          if (pass == 0 && tid == 0) X0->nclu[m] = nc;
+          __syncthreads();
+        }
+        cl.sync();  // every module's count (pass 0), every module's results (pass 1)
+        if (pass == 0) {
+          if (tid == 0) {  // module cluster offsets; too many clusters for the hit sort -> one CTA
+            uint32_t o = 0;
+            for (uint32_t m = 0; m < VELO_MAX_MODULES; ++m) {
+              const uint32_t c = m < M && X.mo[m + 1] > X.mo[m] ? X0->nclu[m] : 0u;
+              X.cb[m] = o;
+              if (c != kNone) {
+                o += c;
+                if (3u * c > 2u * tier) big = 1u;
+              }
+            }
+            X.cb[VELO_MAX_MODULES] = o;
+            X.next = big;
+          }
+          __syncthreads();
+          big = X.next;
+          if (big || *(volatile uint32_t*)&X0->fail) break;  // (every CTA sees the same)
+        }
+      }
+    }
+    // ---- 4. the event's records (rank 0)
+    if (rank == 0) {
+      const uint32_t fail = ev_bad ? (uint32_t)VELO_EVT_BADWORD : *(volatile uint32_t*)&X0->fail;
+      if (fail) {
+        fail_event(L, e, (int32_t)fail, true, p0, n);
+      } else if (big) {
+        cluster_one<NT>(L, e, S, region, tier);  // the whole event here, from its input words
+      } else {
+        const uint32_t nc = X.cb[VELO_MAX_MODULES];
+        if (tid <= M) W.ev_modoff[e * kModOffStride + tid] = X.cb[tid];
+        if (tid == 0) {
+          W.ev_nclusters[e] = nc;
+          L.out.status[e] = VELO_EVT_OK;
+          if (nc >= kWideClusters) W.wide_list[atomicAdd(W.queue + 3, 1u)] = (uint32_t)e;
+        }
+      }
+      if (tid == 0) W.order[atomicAdd(W.queue + 4, 1u)] = (uint32_t)e;  // tracked first
+    }
+    cl.sync();  // the shared records are reused by the next event
+  }
+}
+
+// CTAs per heavy event for k_cluster_wide on the current device (once per
+// device): the largest of 16, 8, 4, 2 for which such a cluster of
+// 1024-thread CTAs with their shared memory can be placed, else 1; 0 if the
+// kernel's attributes cannot be set.
+uint32_t cluster_wide_size(uint32_t smem) {
+  static std::mutex mu;
+  static uint32_t size[64] = {};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (size[d]) return size[d];
+  const void* f = reinterpret_cast<const void*>(k_cluster_wide);
+  if (!set_max_smem_once(f, 6, smem)) return 0;
+  const bool large = allow_large_clusters_once(f, 1);
+  uint32_t cs = 1;  // the largest cluster (16, 8, 4, 2) the device can place, else single CTAs
+  for (uint32_t c = kClusterWideMax; c > 1; c /= 2) {
+    if (c > kClusterWidePortable && !large) continue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, k_cluster_wide, &cfg) == cudaSuccess && n >= 1;
+    cudaGetLastError();
+    if (ok) {
+      cs = c;
+      break;
+    }
+  }
+  size[d] = cs;
+  return cs;
 }
 
 uint32_t cluster_smem_bytes(int nt, uint32_t tier) {
@@ -797,7 +1081,33 @@ int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s) {
     if (!set_max_smem_once(reinterpret_cast<const void*>(k_cluster<1024>), 1)) return VELO_ECUDA;
     k_cluster<1024><<<grid, 1024, smem, s>>>(L);
   }
+  // the heavy-ion-like events: one wave of thread-block clusters (one
+  // 1024-thread CTA per SM), each taking events from the list
+  const uint32_t wtier = cluster_wide_tier();
+  const uint32_t wsmem = cluster_smem_bytes(1024, wtier);
+  const uint32_t cs = cluster_wide_size(wsmem);
+  if (!cs) return VELO_ECUDA;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(std::max<uint32_t>(1u, (uint32_t)device_sm_count() / cs) * cs);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = wsmem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_cluster_wide, L, wtier) != cudaSuccess) return VELO_ECUDA;
   return VELO_OK;
+}
+
+// The shared-memory tier of k_cluster_wide: the largest at 1024 threads that
+// leaves room for its static cross-CTA records.
+uint32_t cluster_wide_tier() {
+  const uint32_t head = cluster_smem_bytes(1024, 0) + (uint32_t)sizeof(WideShared);
+  return ((kSmemPerBlock - head) / 8u) & ~255u;
 }
 
 int cluster_blocks_per_sm(int nt, uint32_t tier) {

@@ -22,6 +22,10 @@ constexpr uint32_t kModOffStride = 33;  // per-event module offsets, n_modules +
 // and more) are tracked by clusters of CTAs (k_track_wide), listed by the
 // clustering kernel in wide_list (count in queue[3]).
 constexpr uint32_t kWideClusters = 20000;
+// Events of at least this many pixel words (heavy-ion-like) are clustered
+// module by module, one thread-block cluster of CTAs per event
+// (k_cluster_wide), listed by k_validate_offsets in heavy_list.
+constexpr uint32_t kHeavyWords = 1u << 16;
 // The tracking kernel takes the events of at least this many clusters first
 // (listed at the front of `order` by the clustering kernel, the others from
 // the back), so that the last CTAs to start are small events.
@@ -40,6 +44,7 @@ struct Workspace {
   uint32_t* queue;           // [8] work-queue counters of the persistent kernels; [3] wide_list count,
                              // [4] / [5] events listed at the front / back of order
   uint32_t* wide_list;       // [E] events of kWideClusters clusters or more (any order)
+  uint32_t* heavy_list;      // [E] events of kHeavyWords words or more (queue[7] of them, any order)
   uint32_t* order;           // [E] events in the tracking kernel's order: kLargeEvent clusters or more first
   uint32_t* ev_nclusters;    // [E]
   uint32_t* ev_modoff;       // [E * 33] cluster-id (= sorted position) offsets per module
@@ -106,12 +111,13 @@ bool carve_workspace(void* base, uint64_t bytes, uint64_t E, uint64_t P, Workspa
 // kernels and their launchers (persistent grids; velo_capi.cu sizes them)
 __global__ void k_validate_offsets(Launch L);
 __global__ void k_scan(Launch L);
-int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s);
+int launch_cluster(const Launch& L, int nt, uint32_t grid, cudaStream_t s);  // k_cluster, then k_cluster_wide
 int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, cudaStream_t s);
 int launch_fit(const Launch& L, bool fused, cudaStream_t s);  // k_fit_out, or k_fit (k_scan and k_output follow)
 int launch_output(const Launch& L, uint32_t grid, cudaStream_t s);
 uint32_t cluster_smem_bytes(int nt, uint32_t tier);
 uint32_t cluster_max_tier(int nt);
+uint32_t cluster_wide_tier();  // the shared-memory tier of the heavy-event clustering
 int cluster_blocks_per_sm(int nt, uint32_t tier);
 int track_blocks_per_sm(int nt);
 int output_blocks_per_sm(bool features);

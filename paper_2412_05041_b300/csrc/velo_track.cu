@@ -1072,6 +1072,10 @@ __global__ void __launch_bounds__(kScanThreads) k_validate_offsets(Launch L) {
     for (int q = 0; q < 8; ++q) L.ws.queue[q] = 0u;  // the persistent kernels' work queues, the fit tickets
   }
   for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.ws.lb_flag[e] = 0u;  // the fused fit's look-back
+  __syncthreads();
+  if (!bad)  // the heavy-ion-like events, for the module-by-module clustering
+    for (uint64_t e = threadIdx.x; e < E; e += blockDim.x)
+      if (L.off[e + 1] - L.off[e] >= kHeavyWords) L.ws.heavy_list[atomicAdd(L.ws.queue + 7, 1u)] = (uint32_t)e;
   if (bad) {
     for (uint64_t e = threadIdx.x; e < E; e += blockDim.x) L.out.status[e] = VELO_EVT_BADWORD;
     if (L.out.pixel_cluster)
