@@ -88,15 +88,17 @@ struct TrackSmem {
 };
 
 constexpr int kFitThreads = 256;
+constexpr int kFitWideThreads = 1024;  // the fit of the heavy-ion-like events (thousands of tracks)
 static_assert(VELO_STATE_STRIDE % 4 == 0, "states move in 16-byte pieces");
 
+template <int NT>
 struct FitSmem {
   uint32_t hit_fill;  // hit ids of the event's tracks staged so far
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   unsigned long long tmp64[64];
   MlpWeights mlp;
-  MlpTiles tiles[kFitThreads / 32];
+  MlpTiles tiles[NT / 32];
 };
 
 // the caller's output buffers hold the batch (capacity 0 = as velo_query_sizes)
@@ -667,7 +669,9 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
 // chi2/ndf (or scored by the ghost-rejection network on tensor cores), and
 // the kept ones are ranked by their smallest cluster id.  A kernel of its
 // own, so that the module loop runs with fewer registers and more CTAs.
-__device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, FitSmem& S) {
+template <int NT>
+__device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, FitSmem<NT>& S) {
+  constexpr int kFitThreads = NT;
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const Par P = L.par;
@@ -786,10 +790,28 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
   }
 }
 
-// The fit of the separate form (one CTA per event; k_scan and k_output follow).
+// The fit of the separate form (one CTA per event; k_scan and k_output
+// follow); the heavy-ion-like events (those k_track_wide tracked) are left
+// to k_fit_wide.
 __global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
-  __shared__ FitSmem S;
-  fit_event(L, blockIdx.x, S);
+  __shared__ FitSmem<kFitThreads> S;
+  const uint64_t e = blockIdx.x;
+  if (*(const volatile uint32_t*)L.ws.flag == 0u && L.out.status[e] == VELO_EVT_OK &&
+      L.ws.ev_nclusters[e] >= kWideClusters)
+    return;
+  fit_event<kFitThreads>(L, e, S);
+}
+
+// The fit of the heavy-ion-like events: one 1024-thread CTA per listed event
+// (the CTAs take the events of the list in turn).
+__global__ void __launch_bounds__(kFitWideThreads, 1) k_fit_wide(Launch L) {
+  extern __shared__ __align__(16) uint8_t fit_raw[];
+  FitSmem<kFitWideThreads>& S = *reinterpret_cast<FitSmem<kFitWideThreads>*>(fit_raw);
+  const uint32_t count = *(const volatile uint32_t*)(L.ws.queue + 3);
+  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    fit_event<kFitWideThreads>(L, L.ws.wide_list[i], S);
+    __syncthreads();  // the shared records are reused by the next event
+  }
 }
 
 // Compaction: clusters and kept tracks of event e into the caller's CSR
@@ -923,7 +945,7 @@ __global__ void __launch_bounds__(kOutputThreads, FEAT ? 1 : 6) k_output(Launch 
 // the events waited for are running) fails this event with
 // VELO_EVT_TIMEOUT instead of hanging, and its record never holds a prefix.
 __global__ void __launch_bounds__(kFitThreads, 4) k_fit_out(Launch L) {
-  __shared__ FitSmem S;
+  __shared__ FitSmem<kFitThreads> S;
   __shared__ uint32_t ticket;
   __shared__ unsigned long long prefix[4];
   __shared__ bool gave_up;
@@ -935,7 +957,7 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit_out(Launch L) {
   }
   __syncthreads();
   const uint64_t e = ticket;
-  fit_event(L, e, S);
+  fit_event<kFitThreads>(L, e, S);
   __syncthreads();
   unsigned long long* rec = W.lb_val + 8 * e;  // aggregate [0, 4), inclusive prefix [4, 8)
   if (tid == 0) {
@@ -1145,8 +1167,14 @@ int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, 
 
 int launch_fit(const Launch& L, bool fused, cudaStream_t s) {
   const uint32_t grid = (uint32_t)L.n_events;  // one CTA per event
-  if (fused) k_fit_out<<<grid, kFitThreads, 0, s>>>(L);
-  else k_fit<<<grid, kFitThreads, 0, s>>>(L);
+  if (fused) {
+    k_fit_out<<<grid, kFitThreads, 0, s>>>(L);
+    return VELO_OK;
+  }
+  k_fit<<<grid, kFitThreads, 0, s>>>(L);
+  const uint32_t smem = (uint32_t)sizeof(FitSmem<kFitWideThreads>);
+  if (!set_max_smem_once(reinterpret_cast<const void*>(k_fit_wide), 7, smem)) return VELO_ECUDA;
+  k_fit_wide<<<(uint32_t)device_sm_count(), kFitWideThreads, smem, s>>>(L);
   return VELO_OK;
 }
 
