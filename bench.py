@@ -687,8 +687,11 @@ def run_ours(args):
     # DRAM bytes per second measured by ncu (bytes per event of the committed
     # summaries, current sources only) over the live times: of the dominant
     # stage and of the whole step
-    dram = {k: profiled_traffic(k) for k in ("k_cluster", "k_track", "k_fit_out")}
-    stage_kernels = (dom,)
+    # the kernels of each stage (the default, separate form)
+    stage_of = {"k_cluster": ("k_cluster",), "k_track": ("k_track",), "k_fit_out": ("k_fit",),
+                "k_scan_output": ("k_output",)}
+    dram = {k: profiled_traffic(k) for k in ("k_cluster", "k_track", "k_fit", "k_output")}
+    stage_kernels = stage_of.get(dom, (dom,))
     if all(dram.get(k) is not None for k in stage_kernels):
         roof["dram_gbs"] = sum(dram[k] for k in stage_kernels) * n_ev / (stage_ms[dom] / 1000.0) / 1e9
         roof["dram_frac"] = roof["dram_gbs"] / peaks["hbm_gbs"]

@@ -30,6 +30,7 @@
 #include "velo_mlp.cuh"
 
 #include <cooperative_groups.h>
+#include <cstddef>
 #include <mutex>
 
 namespace velo {
@@ -83,9 +84,11 @@ struct TrackSmem {
   uint16_t ktab[3][kKeyBuckets + 1];  // bucketed key index of the modules a step reads, module j in j % 3
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
-  uint32_t tmp[64];
+  alignas(16) uint32_t tmp[64];  // (also read as 64-bit scan words)
   SeedArrays<seed_chunk<NT>()> sd;
 };
+static_assert(offsetof(TrackSmem<256>, tmp) % 8 == 0 && offsetof(TrackSmem<128>, tmp) % 8 == 0,
+              "the scan buffer holds 64-bit words");
 
 constexpr int kFitThreads = 256;
 constexpr int kFitWideThreads = 1024;  // the fit of the heavy-ion-like events (thousands of tracks)
@@ -441,9 +444,15 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       }
     }
     constexpr uint32_t kChunk = seed_chunk<NT>();
+    constexpr int PER = kChunk / NT;
+    // a module of one chunk (nearly always): every thread keeps the seeds of
+    // its middle hits (tid + k NT) in registers from the claims to the
+    // survivors, instead of the seed arrays in global memory
+    const bool one_chunk = !WIDE && mhi - mlo <= kChunk;
+    unsigned long long rkey[PER];
+    uint32_t rb0[PER], rb2[PER];
     for (uint32_t cbase = mlo; cbase < mhi; cbase += kChunk) {
       const uint32_t cn = min(kChunk, mhi - cbase);
-      constexpr int PER = kChunk / NT;
       uint32_t cnt[PER], sum = 0;
 #pragma unroll
       for (int k = 0; k < PER; ++k) {  // thread tid owns middle hits PER*tid .. PER*tid+PER-1
@@ -567,22 +576,75 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         if (best != ~0ull) atomicMin(WIDE ? &seedkey[p1] : &S.sd.best[i], best);
       }
       bar();
-      for (uint32_t i = gt; i < cn; i += GT) {  // seeds claim their h0 and h2
-        const uint32_t p1 = cbase + i;
-        const unsigned long long key = WIDE ? ldx<WIDE>(seedkey + p1) : S.sd.best[i];
-        unsigned long long skey = ~0ull;
-        if (key != ~0ull) {
-          const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
-          const uint32_t b2 = W.h_pos[p0 + lo2 + (uint32_t)(key & 0xFFFFu)];
-          skey = step_key((uint32_t)m, (uint32_t)(key >> 32), fbits(hit[p1].w));
-          seed_h0[p1] = b0;
-          seed_h2[p1] = b2;
-          atomicMin(claim + b0, skey);
-          atomicMin(claim + b2, skey);
+      if (one_chunk) {  // seeds claim their h0 and h2
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const uint32_t i = tid + (uint32_t)k * NT;
+          rkey[k] = ~0ull;
+          rb0[k] = rb2[k] = 0;
+          const unsigned long long key = i < cn ? S.sd.best[i] : ~0ull;
+          if (key != ~0ull) {
+            rb0[k] = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
+            rb2[k] = W.h_pos[p0 + lo2 + (uint32_t)(key & 0xFFFFu)];
+            rkey[k] = step_key((uint32_t)m, (uint32_t)(key >> 32), fbits(hit[cbase + i].w));
+            atomicMin(claim + rb0[k], rkey[k]);
+            atomicMin(claim + rb2[k], rkey[k]);
+          }
         }
-        seedkey[p1] = skey;
+      } else {
+        for (uint32_t i = gt; i < cn; i += GT) {  // seeds claim their h0 and h2
+          const uint32_t p1 = cbase + i;
+          const unsigned long long key = WIDE ? ldx<WIDE>(seedkey + p1) : S.sd.best[i];
+          unsigned long long skey = ~0ull;
+          if (key != ~0ull) {
+            const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((key >> 16) & 0xFFFFu)];
+            const uint32_t b2 = W.h_pos[p0 + lo2 + (uint32_t)(key & 0xFFFFu)];
+            skey = step_key((uint32_t)m, (uint32_t)(key >> 32), fbits(hit[p1].w));
+            seed_h0[p1] = b0;
+            seed_h2[p1] = b2;
+            atomicMin(claim + b0, skey);
+            atomicMin(claim + b2, skey);
+          }
+          seedkey[p1] = skey;
+        }
       }
       bar();
+    }
+    if (one_chunk) {
+      // surviving seeds become tracks in the order of h1: middle hit tid + k NT
+      // is ranked by the survivors of the blocks before k and of the lower
+      // threads in block k (one scan of the counts, 16 bits per block)
+      bool surv[PER];
+      unsigned long long v = 0;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        surv[k] = rkey[k] != ~0ull && claim[rb0[k]] == rkey[k] && claim[rb2[k]] == rkey[k];
+        v |= (unsigned long long)(surv[k] ? 1u : 0u) << (16 * k);
+      }
+      unsigned long long tot;
+      const unsigned long long ex =
+          block_exclusive_scan<NT, unsigned long long>(v, &tot, reinterpret_cast<unsigned long long*>(S.tmp));
+      uint32_t before = 0;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const uint32_t r = before + (uint32_t)((ex >> (16 * k)) & 0xFFFFu);
+        if (surv[k] && n_tr + r < track_cap) {  // (the slice bound, as below)
+          const uint32_t t = n_tr + r, p1 = mlo + tid + (uint32_t)k * NT;
+          ta[t] = rb2[k];
+          tbk[t] = p1;
+          meta[t] = 3u | kTrkActive | ((uint32_t)(m - 1) << 16) | ((uint32_t)m << 24);
+          prev[rb2[k]] = p1;
+          prev[p1] = rb0[k];
+          prev[rb0[k]] = kNone;
+          used[rb0[k]] = 1;
+          used[p1] = 1;
+          used[rb2[k]] = 1;
+        }
+        before += (uint32_t)((tot >> (16 * k)) & 0xFFFFu);
+      }
+      n_tr = min(n_tr + before, track_cap);
+      bar();
+      continue;
     }
     // surviving seeds become tracks in the order of h1: two consecutive
     // middle hits per thread, one block scan per 2 NT of them
