@@ -484,13 +484,22 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
   // The 32-bit sums go to shared memory after the two pixel arrays (free
   // since the row sort) when they fit there and clear of the hit sort's keys
   // and first ids ([0, 2.5 n_c) words), which the centroid pass writes while
-  // it reads the sums.  Every root starts its cluster's 32-bit sums: the
-  // charge sum (< 15 * 23552 < 2^19) with the cluster's module in bits
-  // 27-31, so the centroid pass reads the module with the sums.
+  // it reads the sums.  Their layout: a 64-bit word per cluster holding the
+  // charge sum (< 15 * 23552 < 2^27, above it the cluster's module in bits
+  // 27-31) in its high half and the row sum sum q(2r+1) (< 2^32, so no carry
+  // ever reaches the high half) in its low half -- one atomic adds both --
+  // then a 32-bit column sum per cluster: 3 n_c words from an 8-byte aligned
+  // start.  Every root starts its cluster's sums with its module.
   const bool narrow = n <= kNarrowPixels;
   unsigned long long* acc = W.acc + 3 * p0;
-  const bool sums_smem = PS && narrow && 2u * n + 3u * n_clusters <= 2u * tier && 5u * n_clusters <= 4u * n;
-  uint32_t* acc32 = sums_smem ? region + 2 * n : reinterpret_cast<uint32_t*>(acc);  // global: in this event's slice
+  const bool sums_smem = PS && narrow && 2u * n + 3u * n_clusters + 1u <= 2u * tier && 5u * n_clusters <= 4u * n;
+  uint32_t* acc32 = reinterpret_cast<uint32_t*>(acc);  // global: in this event's slice (8-byte aligned)
+  if (sums_smem) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(region + 2 * n);
+    acc32 = reinterpret_cast<uint32_t*>(a + (a & 4u));  // the next 8-byte boundary
+  }
+  unsigned long long* qy64 = reinterpret_cast<unsigned long long*>(acc32);  // (charge | module, row sum)
+  uint32_t* qx32 = acc32 + 2 * n_clusters;                                    // column sums
   const uint32_t lt = (1u << lane) - 1u;
   for (uint32_t base = wlo; base < whi; base += 32) {
     const uint32_t i = base + lane;
@@ -500,9 +509,8 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
       const uint32_t id = rank + __popc(bal & lt);
       B[i] = id | kRootFlag;
       if (narrow) {
-        acc32[3 * id] = ((A[i] >> 22) & 31u) << 27;
-        acc32[3 * id + 1] = 0u;
-        acc32[3 * id + 2] = 0u;
+        qy64[id] = (unsigned long long)(((A[i] >> 22) & 31u) << 27) << 32;
+        qx32[id] = 0u;
       }
     }
     rank += __popc(bal);
@@ -560,10 +568,9 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     const uint32_t w = A[i];
     const uint32_t q = (w >> 27) & 15u, c = w & 2047u, r = (w >> 11) & 2047u;
     if (narrow) {
-      uint32_t* a3 = acc32 + 3u * B[i];
-      atomicAdd(a3 + 0, q);
-      atomicAdd(a3 + 1, q * (2u * c + 1u));
-      atomicAdd(a3 + 2, q * (2u * r + 1u));
+      const uint32_t id = B[i];
+      atomicAdd(qy64 + id, (unsigned long long)q << 32 | (unsigned long long)(q * (2u * r + 1u)));
+      atomicAdd(qx32 + id, q * (2u * c + 1u));
     } else {
       unsigned long long* a3 = acc + 3ull * B[i];
       atomicAdd(a3 + 0, (unsigned long long)q);
@@ -610,7 +617,7 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
   const uint32_t cwh = (M << kHitBucketBits) / 2u;  // u32 words of 16-bit counter pairs
   const uint32_t c0 = 2u * tier - cwh;
   const bool counted = HS && n_clusters < 65536u && 2u * tier >= cwh && c0 >= 3u * n_clusters &&
-                       (acc32 != region + 2 * n || c0 >= 2u * n + 3u * n_clusters);
+                       (acc32 < region || acc32 >= region + 2u * tier || c0 >= 2u * n + 3u * n_clusters + 1u);
   uint32_t* C = region + c0;
   if (counted) {
     for (uint32_t q = tid; q < cwh; q += NT) C[q] = 0u;
@@ -620,7 +627,8 @@ __device__ __forceinline__ void hit_phases(const Launch& L, const uint64_t e, Cl
     float u, v;
     uint32_t mod;
     if (narrow) {
-      const uint32_t s0 = acc32[3 * id], snx = acc32[3 * id + 1], sny = acc32[3 * id + 2];
+      const unsigned long long qy = reinterpret_cast<const unsigned long long*>(acc32)[id];
+      const uint32_t s0 = (uint32_t)(qy >> 32), sny = (uint32_t)qy, snx = acc32[2 * n_clusters + id];
       const uint32_t sq = s0 & 0x7FFFFFFu;
       mod = s0 >> 27;
       const uint32_t D = 2u * sq;

@@ -855,7 +855,7 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
 // The fit of the separate form (one CTA per event; k_scan and k_output
 // follow); the heavy-ion-like events (those k_track_wide tracked) are left
 // to k_fit_wide.
-__global__ void __launch_bounds__(kFitThreads, 4) k_fit(Launch L) {
+__global__ void __launch_bounds__(kFitThreads, 6) k_fit(Launch L) {
   __shared__ FitSmem<kFitThreads> S;
   const uint64_t e = blockIdx.x;
   if (*(const volatile uint32_t*)L.ws.flag == 0u && L.out.status[e] == VELO_EVT_OK &&
