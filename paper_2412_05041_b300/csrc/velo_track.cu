@@ -53,15 +53,18 @@ constexpr int kWideThreads = 1024;
 // non-portable size) where the device can place such a cluster, else the
 // portable 8; the kernel reads the size at run time.
 constexpr uint32_t kWideClusterMax = 16, kWideClusterPortable = 8;
-// Modules of up to this many hits get, in heavy events, a second order of
-// their hits for the h2 searches: by (key bucket, r^2) (dynamic shared memory
-// of k_track_wide: r^2 f32 + module-local index u16 per hit).
-constexpr uint32_t kRadialCap = 8192;
-// dynamic shared memory of k_track_wide: the radial order (r^2 f32, index
-// u16, r^2 in key order f32 while it is built), the u terms of the h2 module
-// (2 f32) and the used flags of the h0 module (1 bit) -- per CTA, so that the
-// triplet loop reads none of them from another SM through L2
-constexpr uint32_t kRadialBytes = kRadialCap * 18u + kRadialCap / 8u;
+// Heavy events seed through a grid of the h2 module's hits in the plane of
+// their u terms (the per-hit half of the seeding's pre-test, u = (1 - a')
+// (x2, y2)): kGridSide^2 cells over the sensor, for modules of up to kGridCap
+// hits.  Every CTA of the cluster keeps its own copy in the dynamic shared
+// memory of k_track_wide: the u terms in cell order (2 f32), the cell starts
+// (u32), the hits' module-local indices in cell order (u16) and the used
+// flags of the h0 module (1 bit), so that the triplet loop reads none of them
+// from another SM through L2.
+constexpr uint32_t kGridSide = 64, kGridCells = kGridSide * kGridSide, kGridCap = 8192;
+constexpr uint32_t kGridOffAt = kGridCap * 8u, kGridIdAt = kGridOffAt + (kGridCells + 1u) * 4u,
+                   kGridUsedAt = kGridIdAt + kGridCap * 2u, kGridBytes = kGridUsedAt + kGridCap / 8u;
+static_assert(kGridIdAt % 4 == 0 && kGridUsedAt % 4 == 0, "grid arrays aligned");
 
 template <uint32_t C>
 struct SeedArrays {
@@ -192,8 +195,7 @@ __device__ __forceinline__ T ldx(const T* p) {
 // WIDE: this instance tracks the events of kWideClusters clusters or more
 // (and only those); the other instance every other event.
 template <int NT, bool WIDE>
-__device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, TrackSmem<NT>& S, float* rr2,
-                                          uint16_t* rord) {
+__device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, TrackSmem<NT>& S, uint8_t* gsm) {
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
   const Par P = L.par;  // by value: kept in registers, not re-read through a reference
@@ -276,37 +278,60 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   uint32_t n_tr = 0;
   for (int m = (int)M - 2; m >= 0; --m) {
     if (m >= 1) index_module((uint32_t)m - 1u);  // its slot held module m + 2, done with at step m + 1
-    if constexpr (WIDE) __syncthreads();  // the radial order below reads the index
-    // (heavy events) the hits of module m - 1 inside each key bucket by r^2,
-    // so that a dense h2 window visits only the hits of the radial band a seed
-    // can reach (read by the seeding of this step, after the extension's
-    // barriers)
-    bool radial = false;
+    // (heavy events) the grid of module m - 1's hits by their u terms, built
+    // by every CTA for its own triplet loop (read after the extension's
+    // barriers).  A hit's cell and a query box's cells come from one monotone
+    // function of the coordinate, so every u inside a box lies in its cells.
+    bool grid = false;
+    float g_lo = 0.0f, g_inv = 0.0f;
+    auto gcell = [&](float v) -> uint32_t {
+      const float t = fm(fs(v, g_lo), g_inv);
+      return !(t > 0.0f) ? 0u : (t >= (float)kGridSide ? kGridSide - 1u : (uint32_t)t);
+    };
     if constexpr (WIDE) {
       if (m >= 1) {
-        const uint32_t lo = S.mod_off[m - 1];
-        radial = S.mod_off[m] - lo <= kRadialCap;
-        if (radial) {
-          // r^2 of every hit in key order, then each hit's place in its bucket:
-          // the hits of the bucket before it in (r^2, key-order index) order
-          const uint16_t* tab = S.ktab[(m - 1) % 3];
-          const uint32_t n2 = S.mod_off[m] - lo;
-          float* rkey = reinterpret_cast<float*>(rord + kRadialCap);
-          for (uint32_t i = tid; i < n2; i += NT) {
-            const float4 h = hit[lo + i];
-            rkey[i] = fa(fm(h.x, h.x), fm(h.y, h.y));
+        const uint32_t lo2 = S.mod_off[m - 1], n2 = S.mod_off[m] - lo2;
+        // (1 - a') as the seeding below computes it
+        const float oma = fs(1.0f, fm(__frcp_rn(fs(S.z[m + 1], S.z[m - 1])), fs(S.z[m], S.z[m - 1])));
+        grid = n2 <= kGridCap && S.mod_off[m + 2] - S.mod_off[m + 1] <= kGridCap && fabsf(oma) > 0.05f;
+        if (grid) {
+          static_assert(kGridCells % NT == 0, "the cell scan gives every thread the same number of cells");
+          constexpr uint32_t PG = kGridCells / NT;
+          const float half = fabsf(oma) * coord_max * 1.01f + 1e-3f;
+          g_lo = -half;
+          g_inv = (float)kGridSide / (2.0f * half);
+          float2* gu = reinterpret_cast<float2*>(gsm);
+          uint32_t* goff = reinterpret_cast<uint32_t*>(gsm + kGridOffAt);
+          uint16_t* gid = reinterpret_cast<uint16_t*>(gsm + kGridIdAt);
+          for (uint32_t c = tid; c <= kGridCells; c += NT) goff[c] = 0u;
+          __syncthreads();
+          for (uint32_t i = tid; i < n2; i += NT) {  // counts of cell c at c + 1
+            const float4 h = hit[lo2 + i];
+            atomicAdd(goff + 1u + gcell(fm(oma, h.y)) * kGridSide + gcell(fm(oma, h.x)), 1u);
           }
           __syncthreads();
+          uint32_t cnt[PG], sum = 0;
+#pragma unroll
+          for (uint32_t k = 0; k < PG; ++k) {
+            cnt[k] = goff[tid * PG + k];
+            sum += cnt[k];
+          }
+          uint32_t total;
+          uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &total, S.tmp);
+#pragma unroll
+          for (uint32_t k = 0; k < PG; ++k) {  // goff[c + 1] = the first slot of cell c
+            goff[tid * PG + k] = run;
+            run += cnt[k];
+          }
+          if (tid == 0) goff[kGridCells] = total;
+          __syncthreads();
+          // (afterwards goff[c + 1] is the end of cell c, so cell c is [goff[c], goff[c + 1]))
           for (uint32_t i = tid; i < n2; i += NT) {
-            const uint32_t b = key_bucket(hit[lo + i].z), s0 = tab[b], s1 = tab[b + 1];
-            const float r2 = rkey[i];
-            uint32_t c = 0;
-            for (uint32_t j = s0; j < s1; ++j) {
-              const float r2j = rkey[j];
-              c += (r2j < r2 || (r2j == r2 && j < i)) ? 1u : 0u;
-            }
-            rr2[s0 + c] = r2;
-            rord[s0 + c] = (uint16_t)i;
+            const float4 h = hit[lo2 + i];
+            const float2 u = make_float2(fm(oma, h.x), fm(oma, h.y));
+            const uint32_t at = atomicAdd(goff + 1u + gcell(u.y) * kGridSide + gcell(u.x), 1u);
+            gu[at] = u;
+            gid[at] = (uint16_t)i;
           }
         }
       }
@@ -417,26 +442,86 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     // the clustering's charge-sum scratch (dead after the clustering; the
     // first two hold the claims and the seed keys)
     float2* uxy = reinterpret_cast<float2*>(W.acc + 2 * L.n_pixels) + p0;
-    // (WIDE, modules of up to kRadialCap hits) every CTA keeps its own copy of
-    // the u terms of module m - 1 and of the used flags of module m + 1
-    bool local = false;
-    float2* su = nullptr;
-    uint32_t* sused = nullptr;
-    if constexpr (WIDE) {
-      local = radial && hi0 - lo0 <= kRadialCap;
-      su = reinterpret_cast<float2*>(reinterpret_cast<float*>(rord + kRadialCap) + kRadialCap);
-      sused = reinterpret_cast<uint32_t*>(su + kRadialCap);
-    }
-    if (local) {
-      for (uint32_t q = tid; q < hi2 - lo2; q += NT) {
-        const float4 h = hit[lo2 + q];
-        su[q] = make_float2(fm(oma, h.x), fm(oma, h.y));
-      }
+    if (grid) {
+      // (heavy events) one warp of the cluster per middle hit, its lanes over
+      // the h0 window.  For an h0 the pre-test accepts only u terms within
+      // sqrt(pre_sc) (+ the roundings of u + c0 and of the squares, far below
+      // the margin of `box`) of -c0, so the h2 candidates are the hits of the
+      // grid cells of that box; the exact chain then decides as above.  The
+      // warp's smallest (bits(s), id0, id2) key is the seed of h1 (the same
+      // minimum as a search over the whole window), claimed at once.
+      const float2* gu = reinterpret_cast<const float2*>(gsm);
+      const uint32_t* goff = reinterpret_cast<const uint32_t*>(gsm + kGridOffAt);
+      const uint16_t* gid = reinterpret_cast<const uint16_t*>(gsm + kGridIdAt);
+      uint32_t* sused = reinterpret_cast<uint32_t*>(gsm + kGridUsedAt);  // module m + 1, final since step m + 1
       for (uint32_t base = 0; base < hi0 - lo0; base += NT) {
         const uint32_t q = base + tid;
         const uint32_t bal = __ballot_sync(kFull, q < hi0 - lo0 && ldx<WIDE>(used + lo0 + q));
         if (lane_id() == 0 && base + warp_id() * 32u < hi0 - lo0) sused[(base >> 5) + warp_id()] = bal;
       }
+      __syncthreads();
+      const float box = sqrtf(pre_sc) * 1.001f + 1e-4f;
+      const uint32_t lane = lane_id();
+      const KeyIndex I0{lo0, S.ktab[(m + 1) % 3]};
+      for (uint32_t p1 = mlo + (gt >> 5); p1 < mhi; p1 += GT >> 5) {  // (warp-uniform)
+        unsigned long long best = ~0ull;
+        if (!ldx<WIDE>(used + p1)) {
+          const float4 H1 = hit[p1];
+          const float k1 = H1.z, x1 = H1.x, y1 = H1.y;
+          const Ranges R0 = window_ranges(I0, k1, P.win_seed);
+          const uint32_t na = R0.a1 - R0.a0, nw = na + (R0.b1 - R0.b0);
+          for (uint32_t kk = lane; kk < nw; kk += 32) {
+            const uint32_t q0 = kk < na ? R0.a0 + kk : R0.b0 + (kk - na);
+            if ((sused[(q0 - lo0) >> 5] >> ((q0 - lo0) & 31u)) & 1u) continue;
+            const float4 H0 = hit[q0];
+            if (dmod4(H0.z, k1) > P.win_seed) continue;
+            const float x0 = H0.x, y0 = H0.y;
+            const unsigned long long lid0 = fbits(H0.w) - lo0;
+            const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
+            const uint32_t cx0 = gcell(-c0x - box), cx1 = gcell(box - c0x);
+            for (uint32_t cy = gcell(-c0y - box), cy1 = gcell(box - c0y); cy <= cy1; ++cy) {
+              const uint32_t s1 = goff[cy * kGridSide + cx1 + 1u];  // cells cx0 .. cx1 of the row are adjacent
+              for (uint32_t sl = goff[cy * kGridSide + cx0]; sl < s1; ++sl) {
+                const float2 u = gu[sl];
+                const float ex = fa(u.x, c0x), ey = fa(u.y, c0y);
+                if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) continue;
+                const uint32_t q2 = lo2 + gid[sl];
+                const float4 H2 = hit[q2];
+                if (dmod4(H2.z, k1) > P.win_seed) continue;
+                const float x2 = H2.x, y2 = H2.y;
+                const float tx = fd(fs(x0, x2), dz02), ty = fd(fs(y0, y2), dz02);
+                if (fabsf(tx) > P.max_slope || fabsf(ty) > P.max_slope) continue;
+                const float xp = fa(x2, fm(tx, dz12)), yp = fa(y2, fm(ty, dz12));
+                const float dx = fs(xp, x1), dy = fs(yp, y1);
+                const float sc = fa(fm(dx, dx), fm(dy, dy));
+                if (sc > P.max_scatter_seed) continue;
+                const unsigned long long cand =
+                    (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(fbits(H2.w) - lo2);
+                best = cand < best ? cand : best;
+              }
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(kFull, best, o);
+            best = v < best ? v : best;
+          }
+        }
+        if (lane == 0) {
+          unsigned long long skey = ~0ull;
+          if (best != ~0ull) {
+            const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((best >> 16) & 0xFFFFu)];
+            const uint32_t b2 = W.h_pos[p0 + lo2 + (uint32_t)(best & 0xFFFFu)];
+            skey = step_key((uint32_t)m, (uint32_t)(best >> 32), fbits(hit[p1].w));
+            seed_h0[p1] = b0;
+            seed_h2[p1] = b2;
+            atomicMin(claim + b0, skey);
+            atomicMin(claim + b2, skey);
+          }
+          seedkey[p1] = skey;
+        }
+      }
+      bar();
     } else {
       for (uint32_t q = lo2 + gt; q < hi2; q += GT) {
         const float4 h = hit[q];
@@ -451,7 +536,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     const bool one_chunk = !WIDE && mhi - mlo <= kChunk;
     unsigned long long rkey[PER];
     uint32_t rb0[PER], rb2[PER];
-    for (uint32_t cbase = mlo; cbase < mhi; cbase += kChunk) {
+    for (uint32_t cbase = grid ? mhi : mlo; cbase < mhi; cbase += kChunk) {  // (the grid's seeds are made)
       const uint32_t cn = min(kChunk, mhi - cbase);
       uint32_t cnt[PER], sum = 0;
 #pragma unroll
@@ -493,7 +578,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const Ranges R0 = unpack_ranges(S.sd.r0[i], lo0);
         const uint32_t kk = j - S.sd.ioff[i], na = R0.a1 - R0.a0;
         const uint32_t q0 = kk < na ? R0.a0 + kk : R0.b0 + (kk - na);
-        if (local ? (sused[(q0 - lo0) >> 5] >> ((q0 - lo0) & 31u)) & 1u : ldx<WIDE>(used + q0)) continue;
+        if (ldx<WIDE>(used + q0)) continue;
         const float4 H0 = hit[q0], H1 = hit[p1];
         const float k1 = H1.z;
         if (dmod4(H0.z, k1) > P.win_seed) continue;
@@ -503,7 +588,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const float c0x = fs(fm(ap, x0), x1), c0y = fs(fm(ap, y0), y1);
         unsigned long long best = ~0ull;
         auto try_h2 = [&](uint32_t q2) {
-          const float2 u = local ? su[q2 - lo2] : ldx<WIDE>(uxy + q2);
+          const float2 u = ldx<WIDE>(uxy + q2);
           const float ex = fa(u.x, c0x), ey = fa(u.y, c0y);
           if (fa(fm(ex, ex), fm(ey, ey)) > pre_sc) return;
           const float4 H2 = hit[q2];
@@ -520,58 +605,12 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
               (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(fbits(H2.w) - lo2);
           best = cand < best ? cand : best;
         };
-        bool searched = false;
-        if constexpr (WIDE) {
-          // A dense window in a heavy event: an h2 within the scatter cut lies
-          // within seed_reach of the point (px, py), so its key within `half`
-          // of the point's (as for narrowed_ranges) and its radius within
-          // seed_reach of the point's: the key buckets of that interval,
-          // each bisected by r^2, hold every such h2 (the exact tests decide).
-          if (radial && seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove) {
-            const float px = (x1 - alpha * x0) / one_m_alpha, py = (y1 - alpha * y0) / one_m_alpha;
-            const float rp = sqrtf(px * px + py * py);
-            const float half = 1.5708f * seed_reach / rp * 1.01f + 1e-4f;
-            if (rp > 2.0f * seed_reach && half < P.win_seed) {
-              const float kp = pseudo_angle(px, py), ka = kp - half - 1e-5f, kb = kp + half + 1e-5f;
-              const float rlo = fmaxf(rp - seed_reach, 0.0f), rhi = rp + seed_reach;
-              const float r2lo = rlo * rlo * (1.0f - 1e-5f) - 1e-6f, r2hi = rhi * rhi * (1.0f + 1e-5f) + 1e-6f;
-              const uint16_t* tab = S.ktab[(m - 1) % 3];
-              uint32_t b0[2], b1[2];
-              int nr = 2;
-              if (ka < 0.0f) {
-                b0[0] = 0;
-                b1[0] = key_bucket(kb);
-                b0[1] = key_bucket(ka + 4.0f);
-                b1[1] = kKeyBuckets - 1;
-              } else if (kb >= 4.0f) {
-                b0[0] = 0;
-                b1[0] = key_bucket(kb - 4.0f);
-                b0[1] = key_bucket(ka);
-                b1[1] = kKeyBuckets - 1;
-              } else {
-                nr = 1;
-                b0[0] = key_bucket(ka);
-                b1[0] = key_bucket(kb);
-              }
-              for (int g = 0; g < nr; ++g)
-                for (uint32_t b = b0[g]; b <= b1[g]; ++b) {
-                  const uint32_t s1 = tab[b + 1];
-                  for (uint32_t k = lower_bound_by(tab[b], s1, [&](uint32_t x) { return rr2[x] < r2lo; });
-                       k < s1 && rr2[k] <= r2hi; ++k)
-                    try_h2(lo2 + rord[k]);
-                }
-              searched = true;
-            }
-          }
-        }
-        if (!searched) {
-          if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
-            R2 = narrowed_ranges(KeyIndex{lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2,
-                                 (x1 - alpha * x0) / one_m_alpha, (y1 - alpha * y0) / one_m_alpha, seed_reach);
-          for (int part2 = 0; part2 < 2; ++part2) {
-            const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
-            for (uint32_t q2 = s2; q2 < e2; ++q2) try_h2(q2);
-          }
+        if (seed_narrow && (R2.a1 - R2.a0) + (R2.b1 - R2.b0) > kNarrowAbove)
+          R2 = narrowed_ranges(KeyIndex{lo2, S.ktab[(m - 1) % 3]}, P.win_seed, R2,
+                               (x1 - alpha * x0) / one_m_alpha, (y1 - alpha * y0) / one_m_alpha, seed_reach);
+        for (int part2 = 0; part2 < 2; ++part2) {
+          const uint32_t s2 = part2 ? R2.b0 : R2.a0, e2 = part2 ? R2.b1 : R2.a1;
+          for (uint32_t q2 = s2; q2 < e2; ++q2) try_h2(q2);
         }
         if (best != ~0ull) atomicMin(WIDE ? &seedkey[p1] : &S.sd.best[i], best);
       }
@@ -707,7 +746,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 template <int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
   __shared__ TrackSmem<NT> S;
-  track_one<NT, false>(L, L.ws.order[blockIdx.x], S, nullptr, nullptr);
+  track_one<NT, false>(L, L.ws.order[blockIdx.x], S, nullptr);
 }
 
 // The heavy events: one wave of clusters of CTAs of kWideThreads threads
@@ -715,13 +754,11 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_track(Launch L) {
 // from the list the clustering kernel made, one cluster per event.
 __global__ void __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
   __shared__ TrackSmem<kWideThreads> S;
-  extern __shared__ __align__(16) uint8_t radial_raw[];
-  float* rr2 = reinterpret_cast<float*>(radial_raw);
-  uint16_t* rord = reinterpret_cast<uint16_t*>(radial_raw + 4u * kRadialCap);
+  extern __shared__ __align__(16) uint8_t grid_raw[];
   const uint32_t count = *(const volatile uint32_t*)(L.ws.queue + 3);
   const uint32_t cs = cooperative_groups::this_cluster().num_blocks();
   for (uint32_t i = blockIdx.x / cs; i < count; i += gridDim.x / cs) {
-    track_one<kWideThreads, true>(L, L.ws.wide_list[i], S, rr2, rord);
+    track_one<kWideThreads, true>(L, L.ws.wide_list[i], S, grid_raw);
     cooperative_groups::this_cluster().sync();  // shared memory and the workspace are reused by the next event
   }
 }
@@ -1178,7 +1215,7 @@ uint32_t wide_cluster_size() {
   std::lock_guard<std::mutex> lk(mu);
   if (size[d]) return size[d];
   const void* f = reinterpret_cast<const void*>(k_track_wide);
-  if (!set_max_smem_once(f, 5, kRadialBytes)) return 0;
+  if (!set_max_smem_once(f, 5, kGridBytes)) return 0;
   uint32_t cs = kWideClusterPortable;
   if (allow_large_clusters_once(f, 0)) {
     cudaLaunchConfig_t cfg = {};
@@ -1189,7 +1226,7 @@ uint32_t wide_cluster_size() {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(kWideClusterMax);
     cfg.blockDim = dim3(kWideThreads);
-    cfg.dynamicSmemBytes = kRadialBytes;
+    cfg.dynamicSmemBytes = kGridBytes;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
@@ -1219,7 +1256,7 @@ int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, 
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(std::max<uint32_t>(1u, (uint32_t)device_sm_count() / cs) * cs);
   cfg.blockDim = dim3(kWideThreads);
-  cfg.dynamicSmemBytes = kRadialBytes;
+  cfg.dynamicSmemBytes = kGridBytes;
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
