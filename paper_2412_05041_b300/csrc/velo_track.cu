@@ -56,14 +56,16 @@ constexpr uint32_t kWideClusterMax = 16, kWideClusterPortable = 8;
 // Heavy events seed through a grid of the h2 module's hits in the plane of
 // their u terms (the per-hit half of the seeding's pre-test, u = (1 - a')
 // (x2, y2)): kGridSide^2 cells over the sensor, for modules of up to kGridCap
-// hits.  Every CTA of the cluster keeps its own copy in the dynamic shared
-// memory of k_track_wide: the u terms in cell order (2 f32), the cell starts
-// (u32), the hits' module-local indices in cell order (u16) and the used
-// flags of the h0 module (1 bit), so that the triplet loop reads none of them
+// hits; the next step's extension into that module reads the same grid.
+// Every CTA of the cluster keeps its own copy in the dynamic shared memory of
+// k_track_wide: the u terms in cell order (2 f32), the cell starts (u32), the
+// hits' module-local indices in cell order (u16), and the used flags of the
+// h0 and h1 modules (1 bit each), so that the triplet loop reads none of them
 // from another SM through L2.
 constexpr uint32_t kGridSide = 64, kGridCells = kGridSide * kGridSide, kGridCap = 8192;
 constexpr uint32_t kGridOffAt = kGridCap * 8u, kGridIdAt = kGridOffAt + (kGridCells + 1u) * 4u,
-                   kGridUsedAt = kGridIdAt + kGridCap * 2u, kGridBytes = kGridUsedAt + kGridCap / 8u;
+                   kGridUsedAt = kGridIdAt + kGridCap * 2u, kGridUsed1At = kGridUsedAt + kGridCap / 8u,
+                   kGridBytes = kGridUsed1At + kGridCap / 8u;
 static_assert(kGridIdAt % 4 == 0 && kGridUsedAt % 4 == 0, "grid arrays aligned");
 
 template <uint32_t C>
@@ -275,68 +277,24 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   index_module(M - 2);
   __syncthreads();
 
+  // (heavy events) the grid in the dynamic shared memory, built at step m
+  // for the seeding's h2 module m - 1 and read again by the extension into
+  // that module at step m - 1 (grid_m: the grid holds module m's hits).  A
+  // hit's cell and a query box's cells come from one monotone function of
+  // the coordinate, so every u inside a box lies in the box's cells.
+  float2* gu = WIDE ? reinterpret_cast<float2*>(gsm) : nullptr;
+  uint32_t* goff = WIDE ? reinterpret_cast<uint32_t*>(gsm + kGridOffAt) : nullptr;
+  uint16_t* gid = WIDE ? reinterpret_cast<uint16_t*>(gsm + kGridIdAt) : nullptr;
+  bool grid_m = false;
+  float g_lo = 0.0f, g_inv = 0.0f, g_oma = 0.0f;
+  auto gcell = [&](float v) -> uint32_t {
+    const float t = fm(fs(v, g_lo), g_inv);
+    return !(t > 0.0f) ? 0u : (t >= (float)kGridSide ? kGridSide - 1u : (uint32_t)t);
+  };
+
   uint32_t n_tr = 0;
   for (int m = (int)M - 2; m >= 0; --m) {
     if (m >= 1) index_module((uint32_t)m - 1u);  // its slot held module m + 2, done with at step m + 1
-    // (heavy events) the grid of module m - 1's hits by their u terms, built
-    // by every CTA for its own triplet loop (read after the extension's
-    // barriers).  A hit's cell and a query box's cells come from one monotone
-    // function of the coordinate, so every u inside a box lies in its cells.
-    bool grid = false;
-    float g_lo = 0.0f, g_inv = 0.0f;
-    auto gcell = [&](float v) -> uint32_t {
-      const float t = fm(fs(v, g_lo), g_inv);
-      return !(t > 0.0f) ? 0u : (t >= (float)kGridSide ? kGridSide - 1u : (uint32_t)t);
-    };
-    if constexpr (WIDE) {
-      if (m >= 1) {
-        const uint32_t lo2 = S.mod_off[m - 1], n2 = S.mod_off[m] - lo2;
-        // (1 - a') as the seeding below computes it
-        const float oma = fs(1.0f, fm(__frcp_rn(fs(S.z[m + 1], S.z[m - 1])), fs(S.z[m], S.z[m - 1])));
-        grid = n2 <= kGridCap && S.mod_off[m + 2] - S.mod_off[m + 1] <= kGridCap && fabsf(oma) > 0.05f;
-        if (grid) {
-          static_assert(kGridCells % NT == 0, "the cell scan gives every thread the same number of cells");
-          constexpr uint32_t PG = kGridCells / NT;
-          const float half = fabsf(oma) * coord_max * 1.01f + 1e-3f;
-          g_lo = -half;
-          g_inv = (float)kGridSide / (2.0f * half);
-          float2* gu = reinterpret_cast<float2*>(gsm);
-          uint32_t* goff = reinterpret_cast<uint32_t*>(gsm + kGridOffAt);
-          uint16_t* gid = reinterpret_cast<uint16_t*>(gsm + kGridIdAt);
-          for (uint32_t c = tid; c <= kGridCells; c += NT) goff[c] = 0u;
-          __syncthreads();
-          for (uint32_t i = tid; i < n2; i += NT) {  // counts of cell c at c + 1
-            const float4 h = hit[lo2 + i];
-            atomicAdd(goff + 1u + gcell(fm(oma, h.y)) * kGridSide + gcell(fm(oma, h.x)), 1u);
-          }
-          __syncthreads();
-          uint32_t cnt[PG], sum = 0;
-#pragma unroll
-          for (uint32_t k = 0; k < PG; ++k) {
-            cnt[k] = goff[tid * PG + k];
-            sum += cnt[k];
-          }
-          uint32_t total;
-          uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &total, S.tmp);
-#pragma unroll
-          for (uint32_t k = 0; k < PG; ++k) {  // goff[c + 1] = the first slot of cell c
-            goff[tid * PG + k] = run;
-            run += cnt[k];
-          }
-          if (tid == 0) goff[kGridCells] = total;
-          __syncthreads();
-          // (afterwards goff[c + 1] is the end of cell c, so cell c is [goff[c], goff[c + 1]))
-          for (uint32_t i = tid; i < n2; i += NT) {
-            const float4 h = hit[lo2 + i];
-            const float2 u = make_float2(fm(oma, h.x), fm(oma, h.y));
-            const uint32_t at = atomicAdd(goff + 1u + gcell(u.y) * kGridSide + gcell(u.x), 1u);
-            gu[at] = u;
-            gid[at] = (uint16_t)i;
-          }
-        }
-      }
-    }
-
     // ---- extension into module m (against the used flags of the step start);
     // a hit within the cut lies within sqrt(max_scatter_fwd) of the prediction
     const float fwd_reach = sqrtf(P.max_scatter_fwd) * 1.01f + 1e-3f;
@@ -358,23 +316,58 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
           const float tx = fd(fs(xa, xb), dzab), ty = fd(fs(ya, yb), dzab);
           const float dzm = fs(zm, za);
           const float xp = fa(xa, fm(tx, dzm)), yp = fa(ya, fm(ty, dzm));
-          const KeyIndex Im{mlo, S.ktab[m % 3]};
-          Ranges R = window_ranges(Im, ka, P.win_fwd);
-          if ((R.a1 - R.a0) + (R.b1 - R.b0) > kNarrowAbove) R = narrowed_ranges(Im, P.win_fwd, R, xp, yp, fwd_reach);
           unsigned long long best = ~0ull;
-          for (int part = 0; part < 2; ++part) {
-            const uint32_t s = part ? R.b0 : R.a0, en = part ? R.b1 : R.a1;
-            for (uint32_t pos = s; pos < en; ++pos) {  // the cut first: few candidates pass it
-              const float4 h = hit[pos];
-              const float dx = fs(xp, h.x), dy = fs(yp, h.y);
-              const float d2 = fa(fm(dx, dx), fm(dy, dy));
-              if (d2 > P.max_scatter_fwd) continue;
-              if (ldx<WIDE>(used + pos)) continue;
-              if (dmod4(h.z, ka) > P.win_fwd) continue;
-              const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | fbits(h.w);
-              if (cand < best) {
-                best = cand;
-                pk = pos;
+          bool searched = false;
+          if constexpr (WIDE) {
+            if (grid_m) {
+              // the hits of the grid cells around the prediction, scaled to the
+              // grid's plane: a hit within the cut lies within |1 - a'| fwd_reach
+              // of it there (+ the roundings of the two products, far below
+              // the margin of bx); the exact tests decide as below
+              const float ucx = fm(g_oma, xp), ucy = fm(g_oma, yp);
+              const float bx = fabsf(g_oma) * fwd_reach * 1.001f + 1e-4f, bx2 = bx * bx;
+              const uint32_t cx0 = gcell(fs(ucx, bx)), cx1 = gcell(fa(ucx, bx));
+              for (uint32_t cy = gcell(fs(ucy, bx)), cy1 = gcell(fa(ucy, bx)); cy <= cy1; ++cy) {
+                const uint32_t s1 = goff[cy * kGridSide + cx1 + 1u];  // cells cx0 .. cx1 of the row are adjacent
+                for (uint32_t sl = goff[cy * kGridSide + cx0]; sl < s1; ++sl) {
+                  const float2 u = gu[sl];
+                  const float ex = fs(u.x, ucx), ey = fs(u.y, ucy);
+                  if (fa(fm(ex, ex), fm(ey, ey)) > bx2) continue;
+                  const uint32_t pos = mlo + gid[sl];
+                  const float4 h = hit[pos];
+                  const float dx = fs(xp, h.x), dy = fs(yp, h.y);
+                  const float d2 = fa(fm(dx, dx), fm(dy, dy));
+                  if (d2 > P.max_scatter_fwd) continue;
+                  if (ldx<WIDE>(used + pos)) continue;
+                  if (dmod4(h.z, ka) > P.win_fwd) continue;
+                  const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | fbits(h.w);
+                  if (cand < best) {
+                    best = cand;
+                    pk = pos;
+                  }
+                }
+              }
+              searched = true;
+            }
+          }
+          if (!searched) {
+            const KeyIndex Im{mlo, S.ktab[m % 3]};
+            Ranges R = window_ranges(Im, ka, P.win_fwd);
+            if ((R.a1 - R.a0) + (R.b1 - R.b0) > kNarrowAbove) R = narrowed_ranges(Im, P.win_fwd, R, xp, yp, fwd_reach);
+            for (int part = 0; part < 2; ++part) {
+              const uint32_t s = part ? R.b0 : R.a0, en = part ? R.b1 : R.a1;
+              for (uint32_t pos = s; pos < en; ++pos) {  // the cut first: few candidates pass it
+                const float4 h = hit[pos];
+                const float dx = fs(xp, h.x), dy = fs(yp, h.y);
+                const float d2 = fa(fm(dx, dx), fm(dy, dy));
+                if (d2 > P.max_scatter_fwd) continue;
+                if (ldx<WIDE>(used + pos)) continue;
+                if (dmod4(h.z, ka) > P.win_fwd) continue;
+                const unsigned long long cand = (unsigned long long)fbits(d2) << 32 | fbits(h.w);
+                if (cand < best) {
+                  best = cand;
+                  pk = pos;
+                }
               }
             }
           }
@@ -442,6 +435,51 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     // the clustering's charge-sum scratch (dead after the clustering; the
     // first two hold the claims and the seed keys)
     float2* uxy = reinterpret_cast<float2*>(W.acc + 2 * L.n_pixels) + p0;
+    // (heavy events) the grid of module m - 1's hits by their u terms
+    bool grid = false;
+    if constexpr (WIDE) {
+      grid = hi2 - lo2 <= kGridCap && hi0 - lo0 <= kGridCap && mhi - mlo <= kGridCap && fabsf(oma) > 0.05f;
+      if (grid) {
+        static_assert(kGridCells % NT == 0, "the cell scan gives every thread the same number of cells");
+        constexpr uint32_t PG = kGridCells / NT;
+        const uint32_t n2 = hi2 - lo2;
+        const float half = fabsf(oma) * coord_max * 1.01f + 1e-3f;
+        g_oma = oma;
+        g_lo = -half;
+        g_inv = (float)kGridSide / (2.0f * half);
+        for (uint32_t c = tid; c <= kGridCells; c += NT) goff[c] = 0u;
+        __syncthreads();
+        for (uint32_t i = tid; i < n2; i += NT) {  // counts of cell c at c + 1
+          const float4 h = hit[lo2 + i];
+          atomicAdd(goff + 1u + gcell(fm(oma, h.y)) * kGridSide + gcell(fm(oma, h.x)), 1u);
+        }
+        __syncthreads();
+        uint32_t cnt[PG], sum = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < PG; ++k) {
+          cnt[k] = goff[tid * PG + k];
+          sum += cnt[k];
+        }
+        uint32_t total;
+        uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &total, S.tmp);
+#pragma unroll
+        for (uint32_t k = 0; k < PG; ++k) {  // goff[c + 1] = the first slot of cell c
+          goff[tid * PG + k] = run;
+          run += cnt[k];
+        }
+        if (tid == 0) goff[kGridCells] = total;
+        __syncthreads();
+        // (afterwards goff[c + 1] is the end of cell c, so cell c is [goff[c], goff[c + 1]))
+        for (uint32_t i = tid; i < n2; i += NT) {
+          const float4 h = hit[lo2 + i];
+          const float2 u = make_float2(fm(oma, h.x), fm(oma, h.y));
+          const uint32_t at = atomicAdd(goff + 1u + gcell(u.y) * kGridSide + gcell(u.x), 1u);
+          gu[at] = u;
+          gid[at] = (uint16_t)i;
+        }
+      }
+      grid_m = grid;  // module m - 1 is the next step's module m
+    }
     if (grid) {
       // (heavy events) one warp of the cluster per middle hit, its lanes over
       // the h0 window.  For an h0 the pre-test accepts only u terms within
@@ -450,23 +488,30 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
       // grid cells of that box; the exact chain then decides as above.  The
       // warp's smallest (bits(s), id0, id2) key is the seed of h1 (the same
       // minimum as a search over the whole window), claimed at once.
-      const float2* gu = reinterpret_cast<const float2*>(gsm);
-      const uint32_t* goff = reinterpret_cast<const uint32_t*>(gsm + kGridOffAt);
-      const uint16_t* gid = reinterpret_cast<const uint16_t*>(gsm + kGridIdAt);
-      uint32_t* sused = reinterpret_cast<uint32_t*>(gsm + kGridUsedAt);  // module m + 1, final since step m + 1
+      // used flags of module m + 1 (final since step m + 1) and of module m
+      // (final since the extension's)
+      uint32_t* sused = reinterpret_cast<uint32_t*>(gsm + kGridUsedAt);
+      uint32_t* s1used = reinterpret_cast<uint32_t*>(gsm + kGridUsed1At);
       for (uint32_t base = 0; base < hi0 - lo0; base += NT) {
         const uint32_t q = base + tid;
         const uint32_t bal = __ballot_sync(kFull, q < hi0 - lo0 && ldx<WIDE>(used + lo0 + q));
         if (lane_id() == 0 && base + warp_id() * 32u < hi0 - lo0) sused[(base >> 5) + warp_id()] = bal;
+      }
+      for (uint32_t base = 0; base < mhi - mlo; base += NT) {
+        const uint32_t q = base + tid;
+        const uint32_t bal = __ballot_sync(kFull, q < mhi - mlo && ldx<WIDE>(used + mlo + q));
+        if (lane_id() == 0 && base + warp_id() * 32u < mhi - mlo) s1used[(base >> 5) + warp_id()] = bal;
       }
       __syncthreads();
       const float box = sqrtf(pre_sc) * 1.001f + 1e-4f;
       const uint32_t lane = lane_id();
       const KeyIndex I0{lo0, S.ktab[(m + 1) % 3]};
       for (uint32_t p1 = mlo + (gt >> 5); p1 < mhi; p1 += GT >> 5) {  // (warp-uniform)
-        unsigned long long best = ~0ull;
-        if (!ldx<WIDE>(used + p1)) {
+        unsigned long long best = ~0ull, skey = ~0ull;
+        uint32_t b0 = 0, b2 = 0;
+        if (!((s1used[(p1 - mlo) >> 5] >> ((p1 - mlo) & 31u)) & 1u)) {
           const float4 H1 = hit[p1];
+          uint32_t bq = 0;  // (q0 - lo0) | (q2 - lo2) << 16 of this lane's best
           const float k1 = H1.z, x1 = H1.x, y1 = H1.y;
           const Ranges R0 = window_ranges(I0, k1, P.win_seed);
           const uint32_t na = R0.a1 - R0.a0, nw = na + (R0.b1 - R0.b0);
@@ -497,22 +542,30 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
                 if (sc > P.max_scatter_seed) continue;
                 const unsigned long long cand =
                     (unsigned long long)fbits(sc) << 32 | lid0 << 16 | (unsigned long long)(fbits(H2.w) - lo2);
-                best = cand < best ? cand : best;
+                if (cand < best) {
+                  best = cand;
+                  bq = (q0 - lo0) | (q2 - lo2) << 16;
+                }
               }
             }
           }
+          unsigned long long wbest = best;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(kFull, best, o);
-            best = v < best ? v : best;
+            const unsigned long long v = __shfl_xor_sync(kFull, wbest, o);
+            wbest = v < wbest ? v : wbest;
+          }
+          // the positions of h0 and h2 from the one lane that found the pair
+          const uint32_t own = __ballot_sync(kFull, best == wbest && wbest != ~0ull);
+          bq = __shfl_sync(kFull, bq, own ? __ffs(own) - 1 : 0);
+          if (own) {
+            b0 = lo0 + (bq & 0xFFFFu);
+            b2 = lo2 + (bq >> 16);
+            skey = step_key((uint32_t)m, (uint32_t)(wbest >> 32), fbits(H1.w));
           }
         }
         if (lane == 0) {
-          unsigned long long skey = ~0ull;
-          if (best != ~0ull) {
-            const uint32_t b0 = W.h_pos[p0 + lo0 + (uint32_t)((best >> 16) & 0xFFFFu)];
-            const uint32_t b2 = W.h_pos[p0 + lo2 + (uint32_t)(best & 0xFFFFu)];
-            skey = step_key((uint32_t)m, (uint32_t)(best >> 32), fbits(hit[p1].w));
+          if (skey != ~0ull) {
             seed_h0[p1] = b0;
             seed_h2[p1] = b2;
             atomicMin(claim + b0, skey);
