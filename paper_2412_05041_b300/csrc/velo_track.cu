@@ -65,7 +65,7 @@ constexpr uint32_t kWideClusterMax = 16, kWideClusterPortable = 8;
 constexpr uint32_t kGridSide = 64, kGridCells = kGridSide * kGridSide, kGridCap = 8192;
 constexpr uint32_t kGridOffAt = kGridCap * 8u, kGridIdAt = kGridOffAt + (kGridCells + 1u) * 4u,
                    kGridUsedAt = kGridIdAt + kGridCap * 2u, kGridUsed1At = kGridUsedAt + kGridCap / 8u,
-                   kGridBytes = kGridUsed1At + kGridCap / 8u;
+                   kGridNextAt = kGridUsed1At + kGridCap / 8u, kGridBytes = kGridNextAt + 16u;
 static_assert(kGridIdAt % 4 == 0 && kGridUsedAt % 4 == 0, "grid arrays aligned");
 
 template <uint32_t C>
@@ -502,11 +502,19 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
         const uint32_t bal = __ballot_sync(kFull, q < mhi - mlo && ldx<WIDE>(used + mlo + q));
         if (lane_id() == 0 && base + warp_id() * 32u < mhi - mlo) s1used[(base >> 5) + warp_id()] = bal;
       }
+      // the CTA of rank r takes the middle hits mlo + r + j CS, its warps the
+      // next j from a counter as they finish (the work per middle hit varies)
+      uint32_t* next = reinterpret_cast<uint32_t*>(gsm + kGridNextAt);
+      if (tid == 0) *next = 0u;
       __syncthreads();
       const float box = sqrtf(pre_sc) * 1.001f + 1e-4f;
       const uint32_t lane = lane_id();
       const KeyIndex I0{lo0, S.ktab[(m + 1) % 3]};
-      for (uint32_t p1 = mlo + (gt >> 5); p1 < mhi; p1 += GT >> 5) {  // (warp-uniform)
+      for (;;) {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(next, 1u);
+        const uint32_t p1 = mlo + rank + __shfl_sync(kFull, j, 0) * CS;  // (warp-uniform)
+        if (p1 >= mhi) break;
         unsigned long long best = ~0ull, skey = ~0ull;
         uint32_t b0 = 0, b2 = 0;
         if (!((s1used[(p1 - mlo) >> 5] >> ((p1 - mlo) & 31u)) & 1u)) {
