@@ -234,6 +234,51 @@ def fp32_peak_tflops():
 
 
 # ------------------------------------------------------------------ arms
+def link_rates(dev, nbytes: int = 256 << 20, reps: int = 5) -> dict:
+    """Pinned host <-> device copy rates (GB/s): each direction alone, and
+    each direction while the other runs (both at once)."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_b = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def h2d():
+        with torch.cuda.stream(s_in):
+            d_a.copy_(h_in, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s_out):
+            h_out.copy_(d_b, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    def rate(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return nbytes * reps / (time.perf_counter() - t0) / 1e9
+
+    return {"h2d_gbs": rate(h2d), "d2h_gbs": rate(d2h), "duplex_gbs_each": rate(both)}
+
+
+def link_bound_ms(bytes_in: int, bytes_out: int, link: dict) -> float:
+    """Shortest time the host link needs for a step's copies: both directions
+    at once while both have bytes left (each at the duplex rate), then the
+    rest alone -- or one direction after the other, if that is shorter."""
+    dup, r_in, r_out = link["duplex_gbs_each"], link["h2d_gbs"], link["d2h_gbs"]
+    both = min(bytes_in, bytes_out) / dup
+    rest = (bytes_out - bytes_in) / r_out if bytes_out > bytes_in else (bytes_in - bytes_out) / r_in
+    serial = bytes_in / r_in + bytes_out / r_out
+    return min(both + rest, serial) / 1e6
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: every step is a bounded sample of the workload."""
     rank, world, _ = dist_env()
@@ -620,15 +665,20 @@ def run_ours(args):
 
         el_serial = host_time(1)  # copy in, compute, copy out one after another
         el = host_time(0)         # chunked: copies overlap with the kernels
-        e2e = {"value": world * n_ev / el, "unit": UNIT, "h2d_bytes_per_step": int(8 * (n_ev + 1) + 4 * P),
-               "d2h_bytes_per_step": int(H.bytes_out()), "ms_per_step": 1000 * el, "pipeline": "auto chunks",
-               "serial_value": world * n_ev / el_serial}
+        b_in, b_out = int(8 * (n_ev + 1) + 4 * P), int(H.bytes_out())
+        link = link_rates(dev)
+        lb = link_bound_ms(b_in, b_out, link)
+        e2e = {"value": world * n_ev / el, "unit": UNIT, "h2d_bytes_per_step": b_in,
+               "d2h_bytes_per_step": b_out, "ms_per_step": 1000 * el, "pipeline": "auto chunks",
+               "serial_value": world * n_ev / el_serial,
+               "link": {k: round(v, 2) for k, v in link.items()}, "link_bound_ms": lb, "link_frac": lb / (1000 * el)}
         # the same with tracks-only results (no cluster coordinates copied back)
         del H
         H = velo.HostReconstructor(b.geometry, vp, max_events=n_ev, max_pixels=P, clusters=False)
         el_t = host_time(0)
+        lb_t = link_bound_ms(b_in, int(H.bytes_out()), link)
         e2e["tracks_only"] = {"value": world * n_ev / el_t, "d2h_bytes_per_step": int(H.bytes_out()),
-                              "ms_per_step": 1000 * el_t}
+                              "ms_per_step": 1000 * el_t, "link_bound_ms": lb_t, "link_frac": lb_t / (1000 * el_t)}
         del H
 
     serving = None

@@ -380,6 +380,30 @@ def test_heavy_ion_events_repeatedly_match_oracle():
         assert_labels(g["pixel_cluster"].cpu().numpy(), r["pixel_cluster"], b.offsets, b.offsets)
 
 
+@pytest.mark.slow
+def test_heavy_events_off_the_grid():
+    """Heavy-ion-like events where the grid search of their tracking does not
+    apply, next to steps where it does: a module 2 mm in front of the next one
+    (at that step the seeding's lever-arm ratio 1 - a' is below 0.05) and a
+    17000-track event (twelve modules of more than 8192 hits; the oracle takes
+    about 35 s on it).  The window search of those steps and modules, and the
+    grid in between, give results identical to the oracle."""
+    from dataclasses import replace
+    zs = [-300.0 + 42.0 * k for k in range(velogen.N_MODULES)]
+    zs[10] = zs[11] - 2.0
+    geo = velogen.Geometry(module_z=tuple(zs))
+    cfg = replace(velogen.C2, seed=11, n_events=2, fixed_pvs=1, fixed_tracks=10000)
+    b = velogen.generate(cfg, geometry=geo)
+    assert (np.diff(b.offsets.astype(np.int64)) > 300_000).all()
+    check_batch(b, cfg.ms_theta)
+    cfg = replace(velogen.C2, seed=12, n_events=1, fixed_pvs=1, fixed_tracks=17000)
+    b = velogen.generate(cfg)
+    g, r = check_batch(b, cfg.ms_theta, labels=False)
+    mod = np.asarray(r["cluster_z"])
+    assert max(np.unique(mod, return_counts=True)[1]) > 8192  # clusters of the fullest module
+    assert len(r["track_states"]) > 15000
+
+
 def test_fp32_peak_measurement():
     """The FP32 ceiling helper returns a rate in the range a B300-class GPU can
     reach (148 SMs x 128 FMA lanes x 2 flops at 1-2.1 GHz: 38-80 TFLOP/s)."""
