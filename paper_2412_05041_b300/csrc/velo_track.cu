@@ -58,12 +58,13 @@ constexpr uint32_t kWideClusterMax = 16, kWideClusterPortable = 8;
 // (x2, y2)): kGridSide^2 cells over the sensor, for modules of up to kGridCap
 // hits; the next step's extension into that module reads the same grid.
 // Every CTA of the cluster keeps its own copy in the dynamic shared memory of
-// k_track_wide: the u terms in cell order (2 f32), the cell starts (u32), the
+// k_track_wide: the u terms in cell order (2 f32), the cell starts (u16: a
+// module has at most kGridCap hits; counted two to a 32-bit word), the
 // hits' module-local indices in cell order (u16), and the used flags of the
 // h0 and h1 modules (1 bit each), so that the triplet loop reads none of them
 // from another SM through L2.
-constexpr uint32_t kGridSide = 64, kGridCells = kGridSide * kGridSide, kGridCap = 8192;
-constexpr uint32_t kGridOffAt = kGridCap * 8u, kGridIdAt = kGridOffAt + (kGridCells + 1u) * 4u,
+constexpr uint32_t kGridSide = 128, kGridCells = kGridSide * kGridSide, kGridCap = 8192;
+constexpr uint32_t kGridOffAt = kGridCap * 8u, kGridIdAt = kGridOffAt + (kGridCells + 2u) * 2u,
                    kGridUsedAt = kGridIdAt + kGridCap * 2u, kGridUsed1At = kGridUsedAt + kGridCap / 8u,
                    kGridNextAt = kGridUsed1At + kGridCap / 8u, kGridBytes = kGridNextAt + 16u;
 static_assert(kGridIdAt % 4 == 0 && kGridUsedAt % 4 == 0, "grid arrays aligned");
@@ -283,7 +284,13 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   // hit's cell and a query box's cells come from one monotone function of
   // the coordinate, so every u inside a box lies in the box's cells.
   float2* gu = WIDE ? reinterpret_cast<float2*>(gsm) : nullptr;
-  uint32_t* goff = WIDE ? reinterpret_cast<uint32_t*>(gsm + kGridOffAt) : nullptr;
+  uint16_t* goff = WIDE ? reinterpret_cast<uint16_t*>(gsm + kGridOffAt) : nullptr;
+  // adds 1 to goff[c] (two entries to a 32-bit word; no entry exceeds
+  // kGridCap, so no carry crosses) and returns its old value
+  auto goff_inc = [&](uint32_t c) -> uint32_t {
+    const uint32_t sh = (c & 1u) * 16u;
+    return (atomicAdd(reinterpret_cast<uint32_t*>(goff) + (c >> 1), 1u << sh) >> sh) & 0xFFFFu;
+  };
   uint16_t* gid = WIDE ? reinterpret_cast<uint16_t*>(gsm + kGridIdAt) : nullptr;
   bool grid_m = false;
   float g_lo = 0.0f, g_inv = 0.0f, g_oma = 0.0f;
@@ -440,40 +447,42 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
     if constexpr (WIDE) {
       grid = hi2 - lo2 <= kGridCap && hi0 - lo0 <= kGridCap && mhi - mlo <= kGridCap && fabsf(oma) > 0.05f;
       if (grid) {
-        static_assert(kGridCells % NT == 0, "the cell scan gives every thread the same number of cells");
-        constexpr uint32_t PG = kGridCells / NT;
+        static_assert(kGridCells % (2 * NT) == 0, "the cell scan gives every thread the same number of words");
+        constexpr uint32_t PG = kGridCells / NT;  // cells per thread in the scan (an even number)
         const uint32_t n2 = hi2 - lo2;
         const float half = fabsf(oma) * coord_max * 1.01f + 1e-3f;
         g_oma = oma;
         g_lo = -half;
         g_inv = (float)kGridSide / (2.0f * half);
-        for (uint32_t c = tid; c <= kGridCells; c += NT) goff[c] = 0u;
+        for (uint32_t w = tid; w < kGridCells / 2u + 1u; w += NT) reinterpret_cast<uint32_t*>(goff)[w] = 0u;
         __syncthreads();
         for (uint32_t i = tid; i < n2; i += NT) {  // counts of cell c at c + 1
           const float4 h = hit[lo2 + i];
-          atomicAdd(goff + 1u + gcell(fm(oma, h.y)) * kGridSide + gcell(fm(oma, h.x)), 1u);
+          goff_inc(1u + gcell(fm(oma, h.y)) * kGridSide + gcell(fm(oma, h.x)));
         }
         __syncthreads();
         uint32_t cnt[PG], sum = 0;
 #pragma unroll
-        for (uint32_t k = 0; k < PG; ++k) {
-          cnt[k] = goff[tid * PG + k];
-          sum += cnt[k];
+        for (uint32_t k = 0; k < PG; k += 2) {
+          const uint32_t w = reinterpret_cast<const uint32_t*>(goff)[(tid * PG + k) >> 1];
+          cnt[k] = w & 0xFFFFu;
+          cnt[k + 1] = w >> 16;
+          sum += cnt[k] + cnt[k + 1];
         }
         uint32_t total;
         uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, &total, S.tmp);
 #pragma unroll
         for (uint32_t k = 0; k < PG; ++k) {  // goff[c + 1] = the first slot of cell c
-          goff[tid * PG + k] = run;
+          goff[tid * PG + k] = (uint16_t)run;
           run += cnt[k];
         }
-        if (tid == 0) goff[kGridCells] = total;
+        if (tid == 0) goff[kGridCells] = (uint16_t)total;
         __syncthreads();
         // (afterwards goff[c + 1] is the end of cell c, so cell c is [goff[c], goff[c + 1]))
         for (uint32_t i = tid; i < n2; i += NT) {
           const float4 h = hit[lo2 + i];
           const float2 u = make_float2(fm(oma, h.x), fm(oma, h.y));
-          const uint32_t at = atomicAdd(goff + 1u + gcell(u.y) * kGridSide + gcell(u.x), 1u);
+          const uint32_t at = goff_inc(1u + gcell(u.y) * kGridSide + gcell(u.x));
           gu[at] = u;
           gid[at] = (uint16_t)i;
         }
