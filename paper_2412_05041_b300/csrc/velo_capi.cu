@@ -324,11 +324,13 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   const uint64_t E = L.n_events;
   const int sms = sm_count();
   if (sms <= 0) return VELO_ECUDA;
-  auto grid = [&](int per_sm) -> uint32_t {  // persistent grid, never more CTAs than events
+  // persistent grid, never more CTAs than work items (`items`: the events,
+  // unless stated)
+  auto grid = [&](int per_sm, uint64_t items = 0) -> uint32_t {
     if (tu.ctas_per_sm == VELO_CTAS_PER_EVENT) return (uint32_t)E;  // one CTA per event, hardware-scheduled
     if (tu.ctas_per_sm) per_sm = per_sm > 0 ? (int)std::min<uint32_t>((uint32_t)per_sm, tu.ctas_per_sm) : 0;
     const uint64_t g = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)sms;
-    return (uint32_t)std::min<uint64_t>(g, E);
+    return (uint32_t)std::min<uint64_t>(g, items ? items : E);
   };
   auto mark = [&](int i) {
     if (marks && marks[i]) cudaEventRecord(reinterpret_cast<cudaEvent_t>(marks[i]), s);
@@ -357,7 +359,8 @@ int velo_reconstruct_into_tuned(const velo_events_t* events, const velo_geometry
   mark(3);
   if (!fused) {
     k_scan<<<1, kScanThreads, 0, s>>>(L);
-    if (E) rc = launch_output(L, grid(output_blocks_per_sm(L.out.track_features != nullptr)), s);
+    // (up to kOutputParts work items per event: parts of heavy-ion-like events)
+    if (E) rc = launch_output(L, grid(output_blocks_per_sm(L.out.track_features != nullptr), E * kOutputParts), s);
     if (rc != VELO_OK) return rc;
   }
   mark(4);

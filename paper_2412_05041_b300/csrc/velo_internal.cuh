@@ -10,6 +10,9 @@ namespace velo {
 
 // Block shapes (the tunable ones are chosen per call, see velo_tuning_t).
 constexpr int kOutputThreads = 256;
+// CTAs of the output kernel that share one heavy-ion-like event (its work
+// queue holds that many parts of each listed event, then the other events)
+constexpr uint32_t kOutputParts = 32;
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kSmemPerSm = 228u * 1024u;    // shared memory of one SM
 constexpr uint32_t kSmemPerBlock = 227u * 1024u; // largest dynamic allocation of one CTA

@@ -102,7 +102,8 @@ static_assert(VELO_STATE_STRIDE % 4 == 0, "states move in 16-byte pieces");
 
 template <int NT>
 struct FitSmem {
-  uint32_t hit_fill;  // hit ids of the event's tracks staged so far
+  uint32_t hit_fill;  // hit ids of the event's tracks staged so far (on a cluster: rank 0's)
+  unsigned long long cta_counts;  // (on a cluster) this CTA's kept tracks << 32 | their hits
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   unsigned long long tmp64[64];
@@ -838,11 +839,22 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_track_wide(Launch L) {
 // chi2/ndf (or scored by the ghost-rejection network on tensor cores), and
 // the kept ones are ranked by their smallest cluster id.  A kernel of its
 // own, so that the module loop runs with fewer registers and more CTAs.
-template <int NT>
+// CL: a thread-block cluster shares the event (its CTAs take every CS-th
+// round of tracks and a CS-th of the ids; rank 0 holds the staging counter).
+template <int NT, bool CL = false>
 __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, FitSmem<NT>& S) {
   constexpr int kFitThreads = NT;
   const Workspace& W = L.ws;
   const uint32_t tid = threadIdx.x;
+  uint32_t CS = 1, crank = 0;
+  if constexpr (CL) {
+    CS = cooperative_groups::this_cluster().num_blocks();
+    crank = cooperative_groups::this_cluster().block_rank();
+  }
+  auto sync_event = [&]() {  // (CL: a cluster barrier also orders the CTAs' global writes)
+    if constexpr (CL) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+  };
   const Par P = L.par;
   const uint32_t M = L.geo.n_modules;
   if (P.use_mlp) mlp_load(P.mlp, S.mlp, tid, kFitThreads);  // network constants
@@ -860,7 +872,9 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
   if (tid < kModOffStride) S.mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
   if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
   if (tid == 0) S.hit_fill = 0;
-  __syncthreads();
+  sync_event();
+  uint32_t* fill = &S.hit_fill;
+  if constexpr (CL) fill = cooperative_groups::this_cluster().map_shared_rank(&S.hit_fill, 0);
   const float4* hit = W.hit + p0;
   uint32_t* first_of = W.sd + p0;
   // for k_output: every track's state and its hit ids (in z order) at a slot of
@@ -875,7 +889,7 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
   uint32_t* hoff = W.trk_hoff + tb;
   // every thread takes part in every round (the learned rule scores a warp's
   // 32 candidates with warp-wide tensor-core instructions)
-  for (uint32_t base = 0; base < n_tr; base += kFitThreads) {
+  for (uint32_t base = crank * kFitThreads; base < n_tr; base += CS * kFitThreads) {
     const uint32_t t = base + tid;
     const bool valid = t < n_tr;
     float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
@@ -908,36 +922,57 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
 #pragma unroll
         for (int k = 0; k < VELO_STATE_STRIDE / 4; ++k)
           so[k] = make_float4(st[4 * k], st[4 * k + 1], st[4 * k + 2], st[4 * k + 3]);
-        const uint32_t slot = atomicAdd(&S.hit_fill, n);
+        const uint32_t slot = atomicAdd(fill, n);
         W.trk_pick[tb + t] = slot;
         for (uint32_t j = 0; j < n; ++j) hit_stage[slot + j] = ids[j];
       }
     }
   }
-  __syncthreads();
+  sync_event();
   // Ranks: kept tracks in the order of their first cluster id.  Every warp
-  // takes a contiguous chunk of the ids, 32 at a time (coalesced): ballots
-  // and a warp scan count its tracks and their hits, one block scan over the
-  // warps gives each chunk its first rank and first hit.
+  // takes a contiguous chunk of the ids (of the CTA's CS-th of them), 32 at
+  // a time (coalesced): ballots and a warp scan count its tracks and their
+  // hits, one block scan over the warps gives each chunk its first rank and
+  // first hit (on a cluster, after the counts of the lower ranks' ids).
   constexpr uint32_t NW = kFitThreads / 32;
   const uint32_t lane = lane_id(), wid = warp_id();
-  const uint32_t cw = ((H + NW - 1) / NW + 31u) & ~31u;
-  const uint32_t wlo = min(H, wid * cw), whi = min(H, wlo + cw);
+  const uint32_t c_lo = (uint32_t)((uint64_t)H * crank / CS), c_hi = (uint32_t)((uint64_t)H * (crank + 1) / CS);
+  const uint32_t cw = ((c_hi - c_lo + NW - 1) / NW + 31u) & ~31u;
+  const uint32_t wlo = min(c_hi, c_lo + wid * cw), whi = min(c_hi, wlo + cw);
+  // (CL: first_of was written by other SMs; read past this SM's L1)
+  auto first_at = [&](uint32_t id) -> uint32_t {
+    if constexpr (CL) return __ldcg(first_of + id);
+    else return first_of[id];
+  };
   uint32_t wtr = 0, wht = 0;
   for (uint32_t b0 = wlo; b0 < whi; b0 += 32) {
     const uint32_t id = b0 + lane;
-    const uint32_t t = id < whi ? first_of[id] : kNone;
+    const uint32_t t = id < whi ? first_at(id) : kNone;
     wtr += __popc(__ballot_sync(kFull, t != kNone));
     wht += __reduce_add_sync(kFull, t != kNone ? meta[t] & 255u : 0u);
   }
   unsigned long long tot;
   const unsigned long long ex = block_exclusive_scan<kFitThreads, unsigned long long>(
       lane == 0 ? ((unsigned long long)wtr << 32) | wht : 0ull, &tot, S.tmp64);
-  uint32_t rr = (uint32_t)(__shfl_sync(kFull, ex, 0) >> 32), rh = (uint32_t)__shfl_sync(kFull, ex, 0);
+  unsigned long long below = 0;  // (CL) the counts of the lower ranks' ids
+  if constexpr (CL) {
+    if (tid == 0) S.cta_counts = tot;
+    cooperative_groups::this_cluster().sync();
+    if (wid == 0) {
+      unsigned long long v = lane < crank ? *cooperative_groups::this_cluster().map_shared_rank(&S.cta_counts, lane) : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      if (lane == 0) S.tmp64[NW] = v;  // (past the block scan's words)
+    }
+    __syncthreads();
+    below = S.tmp64[NW];
+  }
+  const unsigned long long ex0 = __shfl_sync(kFull, ex, 0) + below;
+  uint32_t rr = (uint32_t)(ex0 >> 32), rh = (uint32_t)ex0;
   const uint32_t lt = (1u << lane) - 1u;
   for (uint32_t b0 = wlo; b0 < whi; b0 += 32) {
     const uint32_t id = b0 + lane;
-    const uint32_t t = id < whi ? first_of[id] : kNone;
+    const uint32_t t = id < whi ? first_at(id) : kNone;
     const uint32_t nh = t != kNone ? meta[t] & 255u : 0u;
     uint32_t x = nh;  // inclusive warp scan of the hit counts
 #pragma unroll
@@ -953,9 +988,9 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
     rr += __popc(bal);
     rh += __shfl_sync(kFull, x, 31);
   }
-  if (tid == 0) {
-    W.ev_ntracks[e] = (uint32_t)(tot >> 32);
-    W.ev_nhits[e] = (uint32_t)tot;
+  if (tid == 0 && crank + 1 == CS) {
+    W.ev_ntracks[e] = (uint32_t)((below + tot) >> 32);
+    W.ev_nhits[e] = (uint32_t)(below + tot);
   }
 }
 
@@ -971,15 +1006,17 @@ __global__ void __launch_bounds__(kFitThreads, 6) k_fit(Launch L) {
   fit_event<kFitThreads>(L, e, S);
 }
 
-// The fit of the heavy-ion-like events: one 1024-thread CTA per listed event
-// (the CTAs take the events of the list in turn).
+// The fit of the heavy-ion-like events: one thread-block cluster of
+// 1024-thread CTAs per listed event (the clusters take the events of the list
+// in turn).
 __global__ void __launch_bounds__(kFitWideThreads, 1) k_fit_wide(Launch L) {
   extern __shared__ __align__(16) uint8_t fit_raw[];
   FitSmem<kFitWideThreads>& S = *reinterpret_cast<FitSmem<kFitWideThreads>*>(fit_raw);
   const uint32_t count = *(const volatile uint32_t*)(L.ws.queue + 3);
-  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
-    fit_event<kFitWideThreads>(L, L.ws.wide_list[i], S);
-    __syncthreads();  // the shared records are reused by the next event
+  const uint32_t cs = cooperative_groups::this_cluster().num_blocks();
+  for (uint32_t i = blockIdx.x / cs; i < count; i += gridDim.x / cs) {
+    fit_event<kFitWideThreads, true>(L, L.ws.wide_list[i], S);
+    cooperative_groups::this_cluster().sync();  // the shared records are reused by the next event
   }
 }
 
@@ -987,8 +1024,11 @@ __global__ void __launch_bounds__(kFitWideThreads, 1) k_fit_wide(Launch L) {
 // arrays (offsets from k_scan).  Without features the states and hit ids are
 // the ones k_fit staged; with them (FEAT) every kept track is gathered and
 // fitted again for its features.
+// Part `part` of `parts` of event e (its clusters and tracks in as many
+// equal ranges): a heavy-ion-like event is written by several CTAs.
 template <bool FEAT>
-__device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, uint32_t* mod_off, float* mz) {
+__device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, uint32_t* mod_off, float* mz,
+                                           uint32_t part, uint32_t parts) {
   constexpr int NT = kOutputThreads;
   constexpr int U = 4;  // cluster words in flight per thread
   const Workspace& W = L.ws;
@@ -1000,13 +1040,14 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   if (tid < kModOffStride) mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
   if (tid < VELO_MAX_MODULES) mz[tid] = L.geo.z[tid];
   __syncthreads();
-  const uint32_t H = W.ev_nclusters[e];
+  const uint32_t Hall = W.ev_nclusters[e];  // this part's clusters: [id_lo, H)
+  const uint32_t id_lo = (uint32_t)((uint64_t)Hall * part / parts), H = (uint32_t)((uint64_t)Hall * (part + 1) / parts);
   const uint64_t co = L.out.cluster_offsets[e];
   // clusters in id order (coalesced loads and stores): the clustering's
   // (x, y) by id, untouched by the tracking; the loads of U ids are issued
   // before their stores.  The module offsets hold for ids as for positions
   // (the hit sort keeps every module's clusters together).
-  for (uint32_t id0 = tid; id0 < H; id0 += U * NT) {
+  for (uint32_t id0 = id_lo + tid; id0 < H; id0 += U * NT) {
     float x[U], y[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -1027,14 +1068,15 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
       }
     }
   }
-  const uint32_t nt = W.ev_ntracks_all[e];
+  const uint32_t nt_all = W.ev_ntracks_all[e];  // this part's tracks: [t0, nt)
+  const uint32_t t0 = (uint32_t)((uint64_t)nt_all * part / parts), nt = (uint32_t)((uint64_t)nt_all * (part + 1) / parts);
   const uint64_t to = L.out.track_offsets[e];
   const uint64_t hb = W.ev_hitbase[e];
   if constexpr (!FEAT) {  // states and hit ids as k_fit staged them
     // states in 16-byte pieces when the caller's array allows it (the
     // workspace copy always does)
     const bool v4 = (reinterpret_cast<uintptr_t>(L.out.track_states) & 15u) == 0u;
-    for (uint32_t t = tid; t < nt; t += NT) {
+    for (uint32_t t = t0 + tid; t < nt; t += NT) {
       const uint32_t r = W.trk_rank[tb + t];
       if (r == kNone) continue;
       const uint32_t n = W.trk_meta[tb + t] & 255u, slot = W.trk_pick[tb + t];
@@ -1054,7 +1096,7 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
       }
     }
   } else {
-    for (uint32_t t = tid; t < nt; t += NT) {  // with the features: gathered and fitted again
+    for (uint32_t t = t0 + tid; t < nt; t += NT) {  // with the features: gathered and fitted again
       const uint32_t r = W.trk_rank[tb + t];
       if (r == kNone) continue;
       float xs[VELO_MAX_MODULES], ys[VELO_MAX_MODULES], zs[VELO_MAX_MODULES], st[VELO_STATE_STRIDE];
@@ -1078,9 +1120,10 @@ __device__ __forceinline__ void output_one(const Launch& L, const uint64_t e, ui
   }
 }
 
-// Persistent: events from the work queue.  The plain form is small (six
-// CTAs per SM keep more loads in flight); the form with features carries the
-// fit's arrays.
+// Persistent: work items from the queue -- first kOutputParts parts of each
+// heavy-ion-like event (those the clustering listed), then every other event
+// whole.  The plain form is small (six CTAs per SM keep more loads in
+// flight); the form with features carries the fit's arrays.
 template <bool FEAT>
 __global__ void __launch_bounds__(kOutputThreads, FEAT ? 1 : 6) k_output(Launch L) {
   __shared__ uint32_t mod_off[kModOffStride];
@@ -1088,13 +1131,26 @@ __global__ void __launch_bounds__(kOutputThreads, FEAT ? 1 : 6) k_output(Launch 
   __shared__ uint32_t next;
   // nothing is written when the batch does not fit the caller's buffers
   if (!output_fits(L.out, L.out.totals[0], L.out.totals[1], L.out.totals[2])) return;
+  const uint32_t n_parts = *(const volatile uint32_t*)(L.ws.queue + 3) * kOutputParts;
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(L.ws.queue + 2, 1u);
     __syncthreads();
-    const uint32_t e = next;
+    const uint32_t item = next;
     __syncthreads();
-    if (e >= L.n_events) break;
-    output_one<FEAT>(L, e, mod_off, mz);
+    uint32_t e, part = 0, parts = 1;
+    if (item < n_parts) {
+      e = L.ws.wide_list[item / kOutputParts];
+      part = item % kOutputParts;
+      parts = kOutputParts;
+    } else {
+      e = item - n_parts;
+      if (e >= L.n_events) break;
+      // (a listed event has this many clusters; one that failed writes nothing)
+      if (L.ws.ev_nclusters[e] >= kWideClusters && *(const volatile uint32_t*)L.ws.flag == 0u &&
+          L.out.status[e] == VELO_EVT_OK)
+        continue;
+    }
+    output_one<FEAT>(L, e, mod_off, mz, part, parts);
     __syncthreads();
   }
 }
@@ -1202,7 +1258,7 @@ __global__ void __launch_bounds__(kFitThreads, 4) k_fit_out(Launch L) {
     }
   }
   __syncthreads();
-  output_one<false>(L, e, S.mod_off, S.z);
+  output_one<false>(L, e, S.mod_off, S.z, 0, 1);
 }
 
 // One CTA: event offsets into the output CSR arrays and the batch totals.
@@ -1334,6 +1390,46 @@ int launch_track(const Launch& L, int nt, uint32_t grid, uint32_t wide_cluster, 
   return VELO_OK;
 }
 
+// Cluster size of k_fit_wide on the current device (once per device): the
+// largest of 16, 8, 4, 2 that the device can place, else 1; 0 if the
+// kernel's attributes cannot be set.
+uint32_t fit_wide_cluster_size() {
+  static std::mutex mu;
+  static uint32_t size[64] = {};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (size[d]) return size[d];
+  const void* f = reinterpret_cast<const void*>(k_fit_wide);
+  const uint32_t smem = (uint32_t)sizeof(FitSmem<kFitWideThreads>);
+  if (!set_max_smem_once(f, 7, smem)) return 0;
+  const bool large = allow_large_clusters_once(f, 2);
+  uint32_t cs = 1;
+  for (uint32_t c = kWideClusterMax; c > 1; c /= 2) {
+    if (c > kWideClusterPortable && !large) continue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kFitWideThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, k_fit_wide, &cfg) == cudaSuccess && n >= 1;
+    cudaGetLastError();
+    if (ok) {
+      cs = c;
+      break;
+    }
+  }
+  size[d] = cs;
+  return cs;
+}
+
 int launch_fit(const Launch& L, bool fused, cudaStream_t s) {
   const uint32_t grid = (uint32_t)L.n_events;  // one CTA per event
   if (fused) {
@@ -1341,9 +1437,22 @@ int launch_fit(const Launch& L, bool fused, cudaStream_t s) {
     return VELO_OK;
   }
   k_fit<<<grid, kFitThreads, 0, s>>>(L);
-  const uint32_t smem = (uint32_t)sizeof(FitSmem<kFitWideThreads>);
-  if (!set_max_smem_once(reinterpret_cast<const void*>(k_fit_wide), 7, smem)) return VELO_ECUDA;
-  k_fit_wide<<<(uint32_t)device_sm_count(), kFitWideThreads, smem, s>>>(L);
+  const uint32_t cs = fit_wide_cluster_size();
+  if (!cs) return VELO_ECUDA;
+  // one wave: a cluster per cs SMs (one 1024-thread CTA per SM)
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(std::max<uint32_t>(1u, (uint32_t)device_sm_count() / cs) * cs);
+  cfg.blockDim = dim3(kFitWideThreads);
+  cfg.dynamicSmemBytes = (uint32_t)sizeof(FitSmem<kFitWideThreads>);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_fit_wide, L) != cudaSuccess) return VELO_ECUDA;
   return VELO_OK;
 }
 
