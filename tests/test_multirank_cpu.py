@@ -57,3 +57,19 @@ def test_shard_rejects_bad_rank():
     import bench
     with pytest.raises(ValueError):
         bench.shard(2, 2, 10)
+
+
+def test_link_bound_schedules():
+    """The copy bound of the end-to-end step: both directions at once while
+    both have bytes left, then the rest alone -- or one after the other when
+    that is shorter (worked by hand)."""
+    import bench
+    link = {"h2d_gbs": 50.0, "d2h_gbs": 60.0, "duplex_gbs_each": 40.0}
+    # 1 GB in, 3 GB out: 1 GB each way at 40 GB/s (25 ms), then 2 GB out at 60 GB/s (33.3 ms)
+    assert abs(bench.link_bound_ms(1_000_000_000, 3_000_000_000, link) - (25.0 + 2000.0 / 60.0)) < 1e-9
+    # more in than out: the rest of the copy-in alone at 50 GB/s
+    assert abs(bench.link_bound_ms(2_000_000_000, 1_000_000_000, link) - (25.0 + 20.0)) < 1e-9
+    # a duplex rate below half of either direction: one after the other is shorter
+    slow = {"h2d_gbs": 50.0, "d2h_gbs": 60.0, "duplex_gbs_each": 20.0}
+    assert abs(bench.link_bound_ms(1_000_000_000, 1_000_000_000, slow) - (20.0 + 1000.0 / 60.0)) < 1e-9
+    assert bench.link_bound_ms(0, 0, link) == 0.0
