@@ -46,6 +46,29 @@ def test_candidate_features_bit_exact():
     np.testing.assert_array_equal(g["track_features"], r["track_features"])
 
 
+def test_features_of_a_heavy_event_in_a_mix():
+    """A heavy-ion-like event (its fit on a thread-block cluster, its output
+    written in parts by several CTAs) among ordinary events, with the candidate
+    features asked for: hit lists, states and features identical to the oracle."""
+    from dataclasses import replace
+    from _compare import assert_same
+    h = velogen.generate(replace(velogen.C2, seed=21, n_events=1, fixed_pvs=1, fixed_tracks=10000))
+    c = velogen.generate(velogen.C2, n_events=12, first_event=700)
+    assert h.offsets[-1] > 300_000
+    pixels = np.concatenate([c.pixels[: c.offsets[5]], h.pixels, c.pixels[c.offsets[5]:]])
+    sizes = np.concatenate([np.diff(c.offsets[:6].astype(np.int64)), [int(h.offsets[-1])],
+                            np.diff(c.offsets[5:].astype(np.int64))])
+    offsets = np.zeros(len(sizes) + 1, np.uint64)
+    offsets[1:] = np.cumsum(sizes)
+    off = torch.from_numpy(offsets.view(np.int64)).cuda()
+    pix = torch.from_numpy(pixels.view(np.int32)).cuda()
+    g = to_numpy(velo.reconstruct(off, pix, c.geometry, velo.default_params(), features=True))
+    r = oracle.reconstruct(offsets, pixels, c.geometry, oracle.Params())
+    assert_same(g, r)
+    np.testing.assert_array_equal(g["track_features"], r["track_features"])
+    assert int(r["track_offsets"][6]) - int(r["track_offsets"][5]) > 5000  # the heavy event's tracks
+
+
 def test_bf16_inference_matches_oracle_emulation():
     b = velogen.generate(velogen.C2, n_events=40, first_event=555)
     f = gpu(b, velo.default_params(), features=True)["track_features"]
