@@ -98,12 +98,20 @@ static_assert(offsetof(TrackSmem<256>, tmp) % 8 == 0 && offsetof(TrackSmem<128>,
 
 constexpr int kFitThreads = 256;
 constexpr int kFitWideThreads = 1024;  // the fit of the heavy-ion-like events (thousands of tracks)
+// Events of up to this many tracks have their kept tracks ranked in shared
+// memory by the fit (a count of smaller first ids); larger ones through the
+// id -> track map over all the event's ids.
+constexpr uint32_t kRankCap = 1024;
 static_assert(VELO_STATE_STRIDE % 4 == 0, "states move in 16-byte pieces");
 
 template <int NT>
 struct FitSmem {
   uint32_t hit_fill;  // hit ids of the event's tracks staged so far (on a cluster: rank 0's)
   unsigned long long cta_counts;  // (on a cluster) this CTA's kept tracks << 32 | their hits
+  uint32_t n_kept;                // (kRankCap tracks or fewer) kept tracks so far
+  uint32_t rkey[kRankCap];        // their first cluster id << 11 | track index
+  uint16_t rtrk[kRankCap];        // the track of each rank
+  uint8_t rnh[kRankCap];          // its hits
   uint32_t mod_off[kModOffStride];
   float z[VELO_MAX_MODULES];
   unsigned long long tmp64[64];
@@ -254,7 +262,7 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
 
   for (uint32_t i = gt; i < H; i += GT) {
     used[i] = 0;
-    first_of[i] = kNone;
+    if (WIDE) first_of[i] = kNone;  // (see the end: only events of many tracks need it)
     claim[i] = ~0ull;  // claims carry their step (step_key): no reset between steps
   }
   bar();  // mod_off
@@ -803,6 +811,10 @@ __device__ __forceinline__ void track_one(const Launch& L, const uint64_t e, Tra
   }
 
   if (rank == 0 && tid == 0) W.ev_ntracks_all[e] = n_tr;
+  // the fit ranks the kept tracks of an event of up to kRankCap tracks in
+  // shared memory; above that it reads the id -> track map, reset here
+  if (!WIDE && n_tr > kRankCap)
+    for (uint32_t i = tid; i < H; i += NT) first_of[i] = kNone;
 }
 
 
@@ -871,8 +883,13 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
   const uint32_t n_tr = W.ev_ntracks_all[e];
   if (tid < kModOffStride) S.mod_off[tid] = W.ev_modoff[e * kModOffStride + tid];
   if (tid < VELO_MAX_MODULES) S.z[tid] = L.geo.z[tid];
-  if (tid == 0) S.hit_fill = 0;
+  if (tid == 0) {
+    S.hit_fill = 0;
+    S.n_kept = 0;
+  }
   sync_event();
+  // (events of up to kRankCap tracks) ranks in shared memory
+  const bool ranks_here = !CL && n_tr <= kRankCap;
   uint32_t* fill = &S.hit_fill;
   if constexpr (CL) fill = cooperative_groups::this_cluster().map_shared_rank(&S.hit_fill, 0);
   const float4* hit = W.hit + p0;
@@ -916,7 +933,9 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
     if (valid) {
       rank[t] = kNone;
       if (keep) {
-        first_of[fbits(hit[ta[t]].w)] = t;
+        const uint32_t fid = fbits(hit[ta[t]].w);  // the track's smallest cluster id (< 2^21), t < 2^11
+        if (ranks_here) S.rkey[atomicAdd(&S.n_kept, 1u)] = fid << 11 | t;
+        else first_of[fid] = t;
         if (P.use_mlp) st[19] = W.trk_logit[tb + t];
         float4* so = reinterpret_cast<float4*>(W.trk_state + (tb + t) * VELO_STATE_STRIDE);  // 16-byte aligned
 #pragma unroll
@@ -929,6 +948,44 @@ __device__ __forceinline__ void fit_event(const Launch& L, const uint64_t e, Fit
     }
   }
   sync_event();
+  if (ranks_here) {
+    // Ranks: kept tracks in the order of their first cluster id (distinct:
+    // tracks share no hit), each the count of smaller keys; hit offsets by a
+    // block scan of the hit counts in rank order.
+    const uint32_t nk = S.n_kept;
+    for (uint32_t k = tid; k < nk; k += kFitThreads) {
+      const uint32_t key = S.rkey[k];
+      uint32_t r = 0;
+      for (uint32_t j = 0; j < nk; ++j) r += S.rkey[j] < key ? 1u : 0u;
+      const uint32_t t = key & 2047u;
+      rank[t] = r;
+      S.rtrk[r] = (uint16_t)t;
+      S.rnh[r] = (uint8_t)(meta[t] & 255u);
+    }
+    __syncthreads();
+    static_assert(kRankCap % kFitThreads == 0, "the rank scan gives every thread the same number of ranks");
+    constexpr uint32_t PR = kRankCap / kFitThreads;
+    uint32_t v[PR], sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < PR; ++k) {
+      const uint32_t r = tid * PR + k;
+      v[k] = r < nk ? S.rnh[r] : 0u;
+      sum += v[k];
+    }
+    uint32_t nh_all;
+    uint32_t run = block_exclusive_scan<kFitThreads, uint32_t>(sum, &nh_all, reinterpret_cast<uint32_t*>(S.tmp64));
+#pragma unroll
+    for (uint32_t k = 0; k < PR; ++k) {
+      const uint32_t r = tid * PR + k;
+      if (r < nk) hoff[S.rtrk[r]] = run;
+      run += v[k];
+    }
+    if (tid == 0) {
+      W.ev_ntracks[e] = nk;
+      W.ev_nhits[e] = nh_all;
+    }
+    return;
+  }
   // Ranks: kept tracks in the order of their first cluster id.  Every warp
   // takes a contiguous chunk of the ids (of the CTA's CS-th of them), 32 at
   // a time (coalesced): ballots and a warp scan count its tracks and their
