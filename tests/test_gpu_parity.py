@@ -404,6 +404,31 @@ def test_heavy_events_off_the_grid():
     assert len(r["track_states"]) > 15000
 
 
+def test_events_either_side_of_the_fit_rank_cap():
+    """The fit ranks the kept tracks of an event of up to 1024 tracks in shared
+    memory and those of a larger one through the id -> track map: events of
+    about 1220 tracks (one vertex of 1200 tracks, ~16.5k clusters: the
+    per-event tracking kernel) among pile-up 5.5 events, in the separate and the
+    fused form, equal the oracle."""
+    from dataclasses import replace
+    big = velogen.generate(replace(velogen.C2, seed=31, n_events=2, fixed_pvs=1, fixed_tracks=1200))
+    c2 = velogen.generate(velogen.C2, n_events=6, first_event=900)
+    pixels = np.concatenate([c2.pixels[: c2.offsets[3]], big.pixels, c2.pixels[c2.offsets[3]:]])
+    sizes = np.concatenate([np.diff(c2.offsets[:4].astype(np.int64)), np.diff(big.offsets.astype(np.int64)),
+                            np.diff(c2.offsets[3:].astype(np.int64))])
+    offsets = np.zeros(len(sizes) + 1, np.uint64)
+    offsets[1:] = np.cumsum(sizes)
+    vp, op = params(5e-4)
+    r = oracle.reconstruct(offsets, pixels, c2.geometry, op)
+    kept = np.diff(r["track_offsets"].astype(np.int64))
+    nclu = np.diff(r["cluster_offsets"].astype(np.int64))
+    assert (kept[3:5] > 1024).all() and (nclu[3:5] < 20000).all() and (kept[:3] < 1024).all()
+    o = torch.from_numpy(offsets.view(np.int64)).cuda()
+    p = torch.from_numpy(pixels.view(np.int32)).cuda()
+    for tuning in (None, velo.default_tuning(fused_output=1)):
+        assert_same(to_numpy(velo.reconstruct(o, p, c2.geometry, vp, tuning=tuning)), r)
+
+
 def test_fp32_peak_measurement():
     """The FP32 ceiling helper returns a rate in the range a B300-class GPU can
     reach (148 SMs x 128 FMA lanes x 2 flops at 1-2.1 GHz: 38-80 TFLOP/s)."""
