@@ -133,12 +133,12 @@ __device__ __forceinline__ uint32_t module_of(const uint32_t* mod_off, uint32_t 
 // failure only raises *fail (the heavy kernel then fails the event).
 struct Sub {
   bool on = false;
-  bool count_only = false;          // first pass: stop once the clusters are counted
   const uint32_t* words = nullptr;  // the module's words
   const uint32_t* index = nullptr;  // their positions in the event's input
   uint64_t ev_p0 = 0;               // the event's first word
   uint32_t id_base = 0;             // event-wide id of the module's first cluster
   uint32_t* fail = nullptr;         // VELO_EVT_* code of a failure, 0 if none
+  uint32_t* big = nullptr;          // set when the clusters are too many for the shared hit sort
 };
 
 __device__ void fail_event(const Launch& L, uint64_t e, int32_t code, bool offsets_ok, uint64_t p0, uint32_t n) {
@@ -545,7 +545,6 @@ __device__ __forceinline__ uint32_t pixel_phases(const Launch& L, const uint64_t
     fail_event(L, e, VELO_EVT_OVERFLOW, true, p0, n);
     return kNone;
   }
-  if (sub.count_only) return n_clusters;
 
   // optional per-word labels in input order (a sub-event's at its words' event positions)
   if (L.out.pixel_cluster) {
@@ -809,7 +808,11 @@ __device__ __forceinline__ uint32_t cluster_one(const Launch& L, const uint64_t 
   uint32_t* sums = nullptr;
   const uint32_t n_clusters = smem_tier ? pixel_phases<NT, true>(L, e, S, region, tier, p0, n, &sums, sub)
                                         : pixel_phases<NT, false>(L, e, S, region, tier, p0, n, &sums, sub);
-  if (n_clusters == kNone || sub.count_only) return n_clusters;
+  if (n_clusters == kNone) return n_clusters;
+  if (sub.on && 3u * n_clusters > 2u * tier) {  // (the heavy kernel then clusters the event on one CTA)
+    if (tid == 0) atomicOr(sub.big, 1u);
+    return n_clusters;
+  }
   if (3u * n_clusters <= 2u * tier) hit_phases<NT, true>(L, e, S, region, tier, p0, n, n_clusters, sums, sub);
   else hit_phases<NT, false>(L, e, S, region, tier, p0, n, n_clusters, sums, sub);
   return n_clusters;
@@ -852,10 +855,11 @@ struct WideShared {
   uint32_t n_jobs;                   // how many
   uint32_t next;                     // this CTA's current module job
   // rank 0 only:
-  uint32_t nclu[VELO_MAX_MODULES];   // clusters of each module (first pass)
-  uint32_t job[2];                   // the next module job of each pass
+  uint32_t nclu[VELO_MAX_MODULES];   // clusters of each module
+  uint32_t job;                      // the next module job
   uint32_t bad;                      // a word of the event is invalid
   uint32_t fail;                     // a module's failure (VELO_EVT_*), 0 if none
+  uint32_t big;                      // a module has too many clusters for the shared hit sort
 };
 
 // Heavy-ion-like events (kHeavyWords words or more), one thread-block
@@ -866,11 +870,13 @@ struct WideShared {
 //     by module; the module offsets follow, and every CTA scatters its words
 //     into a module-grouped copy of the event (words in sa, their input
 //     positions in sb);
-//  2. first pass: the CTAs take modules from a cluster-wide counter (most
-//     words first) and count each module's clusters;
-//  3. the module cluster offsets give every module its first event-wide
-//     id; second pass: every module is clustered again and writes its
-//     labels, centroids and hit records at their event-wide places;
+//  2. the CTAs take modules from a cluster-wide counter (most words first)
+//     and cluster each one, writing its labels, centroids and hit records at
+//     provisional event-wide places (ids and positions from its first word's
+//     place in the grouped copy);
+//  3. the module cluster offsets give every module its first event-wide id,
+//     and the records move down to their final places (ids and positions
+//     lowered; the labels in place);
 //  4. rank 0 writes the event's records (status, module offsets, counts,
 //     lists).
 // A module larger than the shared-memory tier, or with too many clusters
@@ -900,8 +906,8 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_wide(Launch L, uint32_t tie
     const uint32_t s0 = (uint32_t)((uint64_t)n * rank / CS), s1 = (uint32_t)((uint64_t)n * (rank + 1) / CS);
     S.cnt[tid] = 0u;  // 32 warps x 32 modules
     if (rank == 0 && tid == 0) {
-      X.job[0] = X.job[1] = 0u;
-      X.bad = X.fail = 0u;
+      X.job = 0u;
+      X.bad = X.fail = X.big = 0u;
     }
     __syncthreads();
     bool bad = false;
@@ -965,45 +971,93 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_wide(Launch L, uint32_t tie
     if (!ev_bad)
       for (uint32_t m = 0; m < M; ++m) big |= X.mo[m + 1] - X.mo[m] > tier;
     if (!ev_bad && !big) {
-      // ---- 2, 3. the two passes over the modules
-      for (int pass = 0; pass < 2; ++pass) {
-        for (;;) {
-          if (tid == 0) X.next = atomicAdd(&X0->job[pass], 1u);
-          __syncthreads();
-          const uint32_t j = X.next;
-          __syncthreads();
-          if (j >= X.n_jobs) break;
-          const uint32_t m = X.order[j];
-          Sub sub;
-          sub.on = true;
-          sub.count_only = pass == 0;
-          sub.words = W.sa + p0 + X.mo[m];
-          sub.index = W.sb + p0 + X.mo[m];
-          sub.ev_p0 = p0;
-          sub.id_base = pass == 0 ? 0u : X.cb[m];
-          sub.fail = &X0->fail;
-          const uint32_t nc = cluster_one<NT>(L, e, S, region, tier, sub, p0 + X.mo[m], X.mo[m + 1] - X.mo[m]);
-          if (pass == 0 && tid == 0) X0->nclu[m] = nc;
-          __syncthreads();
+      // ---- 2. one pass over the modules, each at provisional event-wide
+      // places: its first cluster id (and first hit position) is its first
+      // word's place in the grouped copy, mo[m] >= its final cb[m]
+      for (;;) {
+        if (tid == 0) X.next = atomicAdd(&X0->job, 1u);
+        __syncthreads();
+        const uint32_t j = X.next;
+        __syncthreads();
+        if (j >= X.n_jobs) break;
+        const uint32_t m = X.order[j];
+        Sub sub;
+        sub.on = true;
+        sub.words = W.sa + p0 + X.mo[m];
+        sub.index = W.sb + p0 + X.mo[m];
+        sub.ev_p0 = p0;
+        sub.id_base = X.mo[m];
+        sub.fail = &X0->fail;
+        sub.big = &X0->big;
+        const uint32_t nc = cluster_one<NT>(L, e, S, region, tier, sub, p0 + X.mo[m], X.mo[m + 1] - X.mo[m]);
+        if (tid == 0) X0->nclu[m] = nc;
+        __syncthreads();
+      }
+      cl.sync();  // every module's count and results
+      if (tid == 0) {  // module cluster offsets; too many clusters for the hit sort -> one CTA
+        uint32_t o = 0;
+        for (uint32_t m = 0; m < VELO_MAX_MODULES; ++m) {
+          const uint32_t c = m < M && X.mo[m + 1] > X.mo[m] ? X0->nclu[m] : 0u;
+          X.cb[m] = o;
+          if (c != kNone) o += c;
         }
-        cl.sync();  // every module's count (pass 0), every module's results (pass 1)
-        if (pass == 0) {
-          if (tid == 0) {  // module cluster offsets; too many clusters for the hit sort -> one CTA
-            uint32_t o = 0;
-            for (uint32_t m = 0; m < VELO_MAX_MODULES; ++m) {
-              const uint32_t c = m < M && X.mo[m + 1] > X.mo[m] ? X0->nclu[m] : 0u;
-              X.cb[m] = o;
-              if (c != kNone) {
-                o += c;
-                if (3u * c > 2u * tier) big = 1u;
-              }
-            }
-            X.cb[VELO_MAX_MODULES] = o;
-            X.next = big;
+        X.cb[VELO_MAX_MODULES] = o;
+        X.next = *(volatile uint32_t*)&X0->big;
+      }
+      __syncthreads();
+      big = X.next;
+      if (!big && !*(volatile uint32_t*)&X0->fail) {  // (every CTA sees the same)
+        // ---- 3. the records to their final places: the cluster (x, y) and
+        // the hit records and id -> position map of module m move from
+        // [mo[m], mo[m] + c) to [cb[m], cb[m] + c) with their ids and
+        // positions lowered by mo[m] - cb[m].  Every move goes down (cb[m] <=
+        // mo[m]), so in rounds of rising final places, each read before a
+        // cluster barrier and written after it, no write reaches a record
+        // that a later round still reads.  The labels are lowered in place.
+        const uint32_t nct = X.cb[VELO_MAX_MODULES];
+        auto module_of_final = [&](uint32_t f) {  // the last non-empty m with cb[m] <= f
+          uint32_t lo = 0, hi = M;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (X.cb[mid] <= f) lo = mid;
+            else hi = mid;
           }
-          __syncthreads();
-          big = X.next;
-          if (big || *(volatile uint32_t*)&X0->fail) break;  // (every CTA sees the same)
+          return lo;
+        };
+        for (uint32_t f0 = 0; f0 < nct; f0 += CS * NT) {
+          const uint32_t f = f0 + rank * NT + tid;
+          float2 xy = make_float2(0.0f, 0.0f);
+          float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          uint32_t hp = 0, d = 0;
+          if (f < nct) {
+            const uint32_t m = module_of_final(f);
+            d = X.mo[m] - X.cb[m];
+            xy = __ldcg(W.cl_xy + p0 + f + d);
+            h = __ldcg(W.hit + p0 + f + d);
+            hp = __ldcg(W.h_pos + p0 + f + d);
+          }
+          cl.sync();
+          if (f < nct) {
+            W.cl_xy[p0 + f] = xy;
+            W.hit[p0 + f] = make_float4(h.x, h.y, h.z, __uint_as_float(__float_as_uint(h.w) - d));
+            W.h_pos[p0 + f] = hp - d;
+          }
+        }
+        if (L.out.pixel_cluster) {
+          auto module_of_provisional = [&](uint32_t v) {  // the last m with mo[m] <= v
+            uint32_t lo = 0, hi = M;
+            while (hi - lo > 1) {
+              const uint32_t mid = (lo + hi) >> 1;
+              if (X.mo[mid] <= v) lo = mid;
+              else hi = mid;
+            }
+            return lo;
+          };
+          for (uint32_t i = rank * NT + tid; i < n; i += CS * NT) {
+            const uint32_t v = __ldcg(L.out.pixel_cluster + p0 + i);
+            const uint32_t m = module_of_provisional(v);
+            L.out.pixel_cluster[p0 + i] = v - (X.mo[m] - X.cb[m]);
+          }
         }
       }
     }
